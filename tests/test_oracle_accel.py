@@ -1,0 +1,130 @@
+"""Pins of the oracle's accelerated conduction-band summation (Eq. 3 with the
+quadrature of Eq. 4): count arithmetic, the N0 = N_c limit, the midpoint-rule
+convergence of the integral part, the nearest-state choice and the pair
+bookkeeping."""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.integrate import quad
+
+from oracle import (accelerated_pairs, chi0_from_pairs, dos, freq_factor, full_pairs,
+                    rel_fro, select_accelerated)
+from synth import HARTREE_EV, make_problem
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_A6000 = make_problem("c2").dos_A   # 6000 states on [0.17, 2.2] Ha
+
+
+def _speedup_rows():
+    rows = []
+    with open(os.path.join(HERE, "golden", "speedup_tables.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            t, label, nc, nsel, s = line.split()
+            rows.append((t, label, int(nc), int(nsel), float(s)))
+    return rows
+
+
+@pytest.mark.parametrize("row", _speedup_rows(), ids=lambda r: f"{r[0]}-{r[1]}")
+def test_printed_speedup_is_pair_count_ratio(row):
+    _, _, nc, nsel, printed = row
+    assert round(nc / nsel, 1) == pytest.approx(printed, abs=1e-9)
+
+
+@pytest.mark.parametrize("name,expect", [("c2", 535), ("c5", 2070)])
+def test_grid_point_count(name, expect):
+    # N_E = ceil((E_max - E_0) / dE) with E_0 the energy of band N0
+    prob = make_problem(name)
+    sel = select_accelerated(prob.E_c, prob.N0, prob.dE, prob.dos_A, prob.dos_V0, prob.E_max)
+    assert sel["explicit"].size + sel["rep"].size == expect
+    E0 = prob.E_c[prob.N0 - 1]
+    assert sel["rep"].size == math.ceil((prob.E_max - E0) / prob.dE)
+    # intervals tile (E_0, E_max] exactly; the last one is clipped
+    assert sel["edges"][0] == E0 and sel["edges"][-1] == prob.E_max
+    assert abs(sel["dE_i"].sum() - (prob.E_max - E0)) < 1e-14
+    assert np.all(sel["dE_i"][:-1] == pytest.approx(prob.dE, rel=1e-12))
+    assert 0 < sel["dE_i"][-1] <= prob.dE
+    assert np.allclose(sel["E_i"], 0.5 * (sel["edges"][:-1] + sel["edges"][1:]), rtol=0, atol=1e-15)
+
+
+def test_n0_equal_nc_is_full_sum():
+    prob = make_problem("c1", n_c=12, n_v=3)
+    sel = select_accelerated(prob.E_c, prob.n_c, 0.05, prob.dos_A, prob.dos_V0, prob.E_max)
+    c_idx, Ecol, wcol, dE, w = accelerated_pairs(prob.E_v, prob.E_c, sel)
+    c_f, E_f, w_f, dE_f, w_ff = full_pairs(prob.E_v, prob.E_c)
+    assert np.array_equal(c_idx, c_f) and np.array_equal(dE, dE_f) and np.array_equal(w, w_ff)
+
+
+def test_representative_is_nearest_state_above_n0():
+    rng = np.random.default_rng(3)
+    E_c = np.sort(rng.uniform(0.17, 2.2, 300))
+    E_c[150] = E_c[151]          # a degenerate pair to exercise the tie rule
+    sel = select_accelerated(E_c, 40, 0.037, 100.0, 0.17, 2.2)
+    for e, r in zip(sel["E_i"], sel["rep"]):
+        dist = np.abs(E_c - e)
+        dist[:40] = np.inf
+        best = np.flatnonzero(dist == dist.min())
+        assert r == best[0]
+
+
+@pytest.mark.parametrize("omega", [0.0, 0.4j])
+def test_integral_part_converges_as_midpoint_rule(omega):
+    # All states above E_0 share one matrix element (M = 1 on a 1x1 "sphere"),
+    # so Eq. 4 becomes sum_i g(E_i) dE_i h(E_i) and must converge to the
+    # integral of g(E) h(E) over (E_0, E_max] with an O(dE^2) error.
+    A, V0, Emax, Ev, delta = _A6000, 0.17, 2.2, -0.1, 1e-3
+    E_c = 0.17 + 2.03 * ((np.arange(1, 6001) - 0.5) / 6000) ** (2 / 3)
+    N0 = 512
+    E0 = E_c[N0 - 1]
+
+    def h(E, part):
+        z = 0.5 * (1 / (Ev - E - omega + 1j * delta) + 1 / (Ev - E + omega + 1j * delta))
+        return (z.real if part == 0 else z.imag) * A * math.sqrt(2 * (E - V0))
+
+    exact = quad(h, E0, Emax, args=(0,), epsabs=1e-12, epsrel=1e-13)[0] + \
+        1j * quad(h, E0, Emax, args=(1,), epsabs=1e-12, epsrel=1e-13)[0]
+    errs = []
+    for dE_eV in (2.0, 1.0, 0.5, 0.25):
+        sel = select_accelerated(E_c, N0, dE_eV / HARTREE_EV, A, V0, Emax)
+        f = freq_factor(Ev - sel["E_i"], sel["w_i"], [omega], delta)
+        got = chi0_from_pairs(np.ones((sel["rep"].size, 1)), f)[0, 0, 0]
+        errs.append(abs(got - exact) / abs(exact))
+    ratios = [errs[k] / errs[k + 1] for k in range(3)]
+    assert errs[0] < 2e-3
+    for r in ratios:
+        assert 3.0 < r < 5.0
+
+
+def test_weights_integrate_dos():
+    A, V0, Emax = _A6000, 0.17, 2.2
+    E_c = 0.17 + 2.03 * ((np.arange(1, 6001) - 0.5) / 6000) ** (2 / 3)
+    sel = select_accelerated(E_c, 512, 0.5 / HARTREE_EV, A, V0, Emax)
+    E0 = sel["E0"]
+    exact = A * math.sqrt(2) * (2 / 3) * ((Emax - V0) ** 1.5 - (E0 - V0) ** 1.5)
+    assert abs(sel["w_i"].sum() - exact) / exact < 1e-5
+    assert np.allclose(sel["w_i"], dos(sel["E_i"], A, V0) * sel["dE_i"], rtol=1e-15)
+    # the synthetic DOS counts N_c states up to E_max
+    assert abs(A * math.sqrt(2) * (2 / 3) * (Emax - V0) ** 1.5 - 6000) < 1e-9
+
+
+def test_explicit_part_is_eq1_restricted_at_static_limit():
+    rng = np.random.default_rng(5)
+    Ev = np.array([-0.2, -0.05])
+    E_c = np.sort(rng.uniform(0.2, 2.0, 40))
+    sel = select_accelerated(E_c, 10, 0.2, 50.0, 0.17, 2.2)
+    c_idx, Ecol, wcol, dE, w = accelerated_pairs(Ev, E_c, sel)
+    nsel = c_idx.size
+    M = (rng.standard_normal((2 * nsel, 4)) + 1j * rng.standard_normal((2 * nsel, 4)))
+    # explicit columns: dE = E_v - E_c, w = 1 ; grid columns: dE = E_v - E_i, w = g dE_i
+    dEm = dE.reshape(2, nsel)
+    assert np.allclose(dEm[:, :10], Ev[:, None] - E_c[None, :10], atol=0)
+    assert np.allclose(dEm[:, 10:], Ev[:, None] - sel["E_i"][None, :], atol=0)
+    assert np.all(w.reshape(2, nsel)[:, :10] == 1.0)
+    keep = (np.arange(2 * nsel) % nsel) < 10
+    f = freq_factor(dE[keep], w[keep], [0.0], 0.0)
+    expl = chi0_from_pairs(M[keep], f)[0]
+    direct = sum(M[p][:, None] * M[p].conj()[None, :] / dE[p] for p in np.flatnonzero(keep))
+    assert rel_fro(expl, direct) < 1e-14
