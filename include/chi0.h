@@ -1,0 +1,153 @@
+/*
+ * chi0.h - C ABI of libchi0: the RPA polarizability hot path of
+ * "Towards Fully Converged GW Calculations for Large Systems" on one GPU.
+ *
+ *   chi0_{G,G'}(q,w) = 1/2 sum_{v,c} M_vc(q,G) conj(M_vc(q,G'))
+ *                       x [1/(E_v - E_c - w + i d) + 1/(E_v - E_c + w + i d)]   (Eq. 1)
+ *
+ * with M_vc(q,G) = <v,k+q| exp(i(q+G).r) |c,k> (definition following Eq. 1),
+ * and its accelerated form (Eq. 3 with the energy quadrature of Eq. 4), in
+ * which the conduction bands above N0 are replaced by one state per energy
+ * grid point carrying the weight g(E_i) dE_i and the denominator E_v - E_i.
+ *
+ * Conventions used by every entry point
+ *   - Pointers marked (device) must point to memory of the device that was
+ *     current when the plan was created; (host) pointers are read before the
+ *     call returns and may be reused afterwards.  The caller owns every buffer.
+ *   - Complex numbers are interleaved (re, im).  "complex" below means
+ *     complex128 (double2) for a CHI0_FP64 plan and complex64 (float2) for the
+ *     split-precision plans; energies, weights and chi0 are always FP64.
+ *   - Real-space grids are [band][i1][i2][i3] with i3 fastest (n1*n2*n3
+ *     points, r = (i1/n1, i2/n2, i3/n3) in lattice coordinates).
+ *   - A pair index is p = iv * n_c + ic (valence-major) over the bands passed
+ *     to the call.  chi0 is [n_freq][N_G][N_G] complex128, row G, column G'.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Compute
+ *     calls only enqueue work; they return after host-side validation.
+ *   - Every call returns a chi0_status and never aborts.  Argument errors are
+ *     reported before any work is enqueued.  A device-side failure (a bounded
+ *     wait that ran out) is recorded in a device status word and reported as
+ *     CHI0_ERR_TIMEOUT by chi0_sync_status().
+ *   - A plan is not safe for concurrent use from several host threads.
+ */
+#ifndef CHI0_H
+#define CHI0_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CHI0_OK = 0,
+  CHI0_ERR_INVALID = 1,      /* bad argument; nothing was enqueued */
+  CHI0_ERR_OOM = 2,          /* device allocation failed */
+  CHI0_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+  CHI0_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out */
+  CHI0_ERR_UNSUPPORTED = 5   /* no kernel for this device / shape */
+} chi0_status;
+
+typedef enum {
+  CHI0_FP64 = 0,        /* FP64 end to end (CUDA-core DFMA contraction) */
+  CHI0_SPLIT_BF16 = 1,  /* FP32 pair stage; contraction on tcgen05 with hi+lo BF16 operands */
+  CHI0_SPLIT_FP16 = 2   /* FP32 pair stage; contraction on tcgen05 with hi+lo FP16 operands */
+} chi0_precision;
+
+typedef struct chi0_plan_s* chi0_plan;
+
+/* Plan description.  All arrays are (host) and are copied by chi0_plan_create. */
+typedef struct {
+  int n1, n2, n3;            /* real-space FFT grid */
+  int n_q;                   /* number of q-points */
+  const int32_t* n_G;        /* [n_q] dielectric-sphere size per q (>= 1) */
+  const int32_t* gvec;       /* [sum n_G][3] integer G vectors of each sphere, q after q;
+                                each sphere must span fewer than n_k points along axis k */
+  int npw;                   /* size of the wavefunction plane-wave sphere */
+  const int32_t* gw;         /* [npw][3] integer g of the wavefunction sphere */
+  int n_freq;                /* number of frequencies (>= 1) */
+  const double* freq_re;     /* [n_freq] Re(omega), Hartree */
+  const double* freq_im;     /* [n_freq] Im(omega), Hartree */
+  double delta;              /* broadening d of Eq. 1, Hartree */
+  chi0_precision precision;
+  int n_products;            /* split products per real product: 3 (hh+hl+lh) or 4 (+ll); 0 = 4 for
+                                BF16, 3 for FP16; ignored for FP64 */
+  int64_t max_pairs;         /* pairs per internal block of chi0_build / chi0_accumulate; 0 = default */
+  int chain_pairs;           /* pairs per tensor-core accumulation chain (multiple of 32); 0 = default */
+} chi0_plan_desc;
+
+/* Create a plan: validates the description, analyses each G sphere for the
+ * pruned transforms, uploads index maps and twiddle tables and allocates the
+ * plan's workspace on the current device.  *out is NULL on failure; the
+ * reason is available from chi0_last_error(NULL). */
+chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* desc);
+
+/* Release a plan and its workspace (synchronises the device first).  NULL is a no-op. */
+chi0_status chi0_plan_destroy(chi0_plan plan);
+
+/* Text of the last error of this plan (plan-owned, valid until the next call
+ * on the plan), or of the last failed plan creation when plan is NULL. */
+const char* chi0_last_error(chi0_plan plan);
+
+/* Bytes of device workspace held by the plan. */
+size_t chi0_workspace_bytes(chi0_plan plan);
+
+/* Synchronise `stream` and report device-side failures recorded since the
+ * last call (CHI0_ERR_TIMEOUT if a bounded wait ran out, CHI0_ERR_CUDA if the
+ * stream reports an error).  Clears the recorded status. */
+chi0_status chi0_sync_status(chi0_plan plan, void* stream);
+
+/* Wavefunctions on the grid (plane-wave expansion used by M after Eq. 1):
+ *   psi[b][r] = sum_{g in wavefunction sphere} coeff[b][g] exp(2 pi i g.r).
+ * coeff: (device) [nb][npw] complex128 in the order of desc.gw.
+ * psi:   (device) [nb][n1*n2*n3] complex (complex64 for split plans). */
+chi0_status chi0_wfn_to_grid(chi0_plan plan, const void* coeff, int nb, void* psi, void* stream);
+
+/* Pair matrix elements (definition following Eq. 1), pruned to sphere iq:
+ *   M[p][j] = (1/N_r) sum_r conj(psi_v[v(iv)][r]) psi_c[c(ic)][r] exp(2 pi i G_j.r)
+ * for iv < n_v, ic < n_c, p = iv*n_c + ic.
+ * psi_v, psi_c: (device) grids as written by chi0_wfn_to_grid.
+ * v_idx, c_idx: (device) int32 [n_v] / [n_c] band rows to use, or NULL for 0..n-1.
+ * M: (device) [n_v*n_c][n_G[iq]] complex. */
+chi0_status chi0_pairs(chi0_plan plan, int iq, const void* psi_v, const int32_t* v_idx, int n_v,
+                       const void* psi_c, const int32_t* c_idx, int n_c, void* M, void* stream);
+
+/* Contraction of Eq. 1 / Eq. 3-4 for one set of pairs, added into chi0:
+ *   chi0[w][G][G'] += sum_p f_p(w) M[p][G] conj(M[p][G'])
+ *   f_p(w) = (w_p/2) [1/(dE_p - w + i d) + 1/(dE_p + w + i d)],
+ *   dE_p = E_v[iv] - E_col[ic],  w_p = w_col[ic] (1 when w_col is NULL).
+ * For the explicit bands E_col = E_c and w_col = 1; for an energy-grid state
+ * of Eq. 4, E_col = E_i and w_col = g(E_i) dE_i.
+ * M: (device) [n_v*n_c][n_G[iq]] complex; E_v (device) [n_v]; E_col, w_col (device) [n_c];
+ * chi0: (device) [n_freq][n_G[iq]][n_G[iq]] complex128, accumulated in place (caller zeroes it). */
+chi0_status chi0_accumulate(chi0_plan plan, int iq, const void* M, int n_v, int n_c,
+                            const double* E_v, const double* E_col, const double* w_col,
+                            void* chi0, void* stream);
+
+/* The whole hot path for one q-point: for blocks of conduction columns,
+ * chi0_pairs into plan workspace followed by chi0_accumulate, so M is never
+ * held for all pairs at once.  Arguments as for chi0_pairs/chi0_accumulate
+ * (valence rows 0..n_v-1 of psi_v; conduction rows c_idx[ic] of psi_c). */
+chi0_status chi0_build(chi0_plan plan, int iq, const void* psi_v, int n_v, const double* E_v,
+                       const void* psi_c, const int32_t* c_idx, int n_c,
+                       const double* E_col, const double* w_col, void* chi0, void* stream);
+
+/* Band selection of Eq. 3 / Eq. 4 (host arrays, host computation).
+ * E_c (host) [n_c] sorted ascending.  Columns 0..N0-1 are bands 0..N0-1 with
+ * their own energy and weight 1.  E_0 = E_c[N0-1]; the interval (E_0, E_max]
+ * is cut into N_E = ceil((E_max-E_0)/dE) steps of width dE (the last one
+ * clipped at E_max); grid point E_i is the midpoint of step i, dE_i its width,
+ * its state is the band above N0 nearest in energy to E_i (ties to the lower
+ * index), its energy E_i and its weight g(E_i) dE_i with
+ * g(E) = dos_A * sqrt(2 (E - dos_V0)) (zero below dos_V0).
+ * Writes up to cap columns to c_sel (host int32), E_sel, w_sel (host double).
+ * Returns the number of columns N0 + N_E, or -1 on invalid input or when cap is too small. */
+int chi0_select_accelerated(const double* E_c, int n_c, int N0, double dE, double dos_A,
+                            double dos_V0, double E_max, int32_t* c_sel, double* E_sel,
+                            double* w_sel, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHI0_H */

@@ -1,0 +1,173 @@
+"""Thin PyTorch binding of libchi0 (argument marshalling only).
+
+Every step of the hot path runs in the library's CUDA kernels; PyTorch only
+provides device memory and the current stream.  Names follow include/chi0.h.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class Chi0Plan:
+    """A chi0 plan on the current CUDA device (see chi0_plan_create)."""
+
+    def __init__(self, n, gvecs, omega, delta: float, precision: str = "fp64", gw=None,
+                 n_products: int = 0, max_pairs: int = 0, chain_pairs: int = 0):
+        lib = L.lib()
+        n1, n2, n3 = (n, n, n) if np.isscalar(n) else tuple(int(x) for x in n)
+        self.n = (n1, n2, n3)
+        self.nr = n1 * n2 * n3
+        self.precision = precision
+        if precision not in L.PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(L.PRECISIONS)}")
+        gl = [_i32(g).reshape(-1, 3) for g in gvecs]
+        self.n_G = [int(g.shape[0]) for g in gl]
+        om = np.atleast_1d(np.asarray(omega, dtype=np.complex128))
+        self.n_freq = int(om.size)
+        keep = dict(nG=_i32(self.n_G), g=np.ascontiguousarray(np.concatenate(gl, 0)),
+                    re=_f64(om.real), im=_f64(om.imag),
+                    gw=None if gw is None else _i32(gw).reshape(-1, 3))
+        d = L.Chi0PlanDesc()
+        d.n1, d.n2, d.n3 = n1, n2, n3
+        d.n_q = len(gl)
+        d.n_G = keep["nG"].ctypes.data_as(C.POINTER(C.c_int32))
+        d.gvec = keep["g"].ctypes.data_as(C.POINTER(C.c_int32))
+        d.npw = 0 if gw is None else int(keep["gw"].shape[0])
+        d.gw = None if gw is None else keep["gw"].ctypes.data_as(C.POINTER(C.c_int32))
+        d.n_freq = self.n_freq
+        d.freq_re = keep["re"].ctypes.data_as(C.POINTER(C.c_double))
+        d.freq_im = keep["im"].ctypes.data_as(C.POINTER(C.c_double))
+        d.delta = float(delta)
+        d.precision = L.PRECISIONS[precision]
+        d.n_products = int(n_products)
+        d.max_pairs = int(max_pairs)
+        d.chain_pairs = int(chain_pairs)
+        h = C.c_void_p()
+        L.check(lib.chi0_plan_create(C.byref(h), C.byref(d)), None)
+        self._h = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.cdtype = torch.complex128 if precision == "fp64" else torch.complex64
+
+    # -- lifetime --------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            L.lib().chi0_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(L.lib().chi0_workspace_bytes(self._h))
+
+    def _check(self, st):
+        L.check(st, self._h)
+
+    def _c(self, t, name, dtype=None):
+        dtype = dtype or self.cdtype
+        if t.dtype != dtype or t.device != self.device or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {dtype} tensor on {self.device}")
+        return t
+
+    # -- entry points ----------------------------------------------------
+    def sync_status(self):
+        self._check(L.lib().chi0_sync_status(self._h, _stream()))
+
+    def wfn_to_grid(self, coeff: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        coeff = self._c(coeff, "coeff", torch.complex128)
+        nb = coeff.shape[0]
+        if out is None:
+            out = torch.empty((nb,) + self.n, dtype=self.cdtype, device=self.device)
+        self._c(out, "out")
+        self._check(L.lib().chi0_wfn_to_grid(self._h, _ptr(coeff), nb, _ptr(out), _stream()))
+        return out
+
+    def pairs(self, iq: int, psi_v, psi_c, v_idx=None, c_idx=None, out=None) -> torch.Tensor:
+        self._c(psi_v, "psi_v")
+        self._c(psi_c, "psi_c")
+        n_v = psi_v.shape[0] if v_idx is None else int(v_idx.numel())
+        n_c = psi_c.shape[0] if c_idx is None else int(c_idx.numel())
+        for t in (v_idx, c_idx):
+            if t is not None:
+                self._c(t, "index", torch.int32)
+        if out is None:
+            out = torch.empty((n_v * n_c, self.n_G[iq]), dtype=self.cdtype, device=self.device)
+        self._c(out, "out")
+        self._check(L.lib().chi0_pairs(self._h, iq, _ptr(psi_v), _ptr(v_idx), n_v, _ptr(psi_c),
+                                       _ptr(c_idx), n_c, _ptr(out), _stream()))
+        return out
+
+    def new_chi(self, iq: int) -> torch.Tensor:
+        nG = self.n_G[iq]
+        return torch.zeros((self.n_freq, nG, nG), dtype=torch.complex128, device=self.device)
+
+    def accumulate(self, iq: int, M, n_v: int, n_c: int, E_v, E_col, w_col=None, chi=None):
+        self._c(M, "M")
+        for t, nm in ((E_v, "E_v"), (E_col, "E_col"), (w_col, "w_col")):
+            if t is not None:
+                self._c(t, nm, torch.float64)
+        chi = self.new_chi(iq) if chi is None else self._c(chi, "chi", torch.complex128)
+        self._check(L.lib().chi0_accumulate(self._h, iq, _ptr(M), n_v, n_c, _ptr(E_v), _ptr(E_col),
+                                            _ptr(w_col), _ptr(chi), _stream()))
+        return chi
+
+    def build(self, iq: int, psi_v, E_v, psi_c, E_col, w_col=None, c_idx=None, chi=None):
+        self._c(psi_v, "psi_v")
+        self._c(psi_c, "psi_c")
+        n_v = psi_v.shape[0]
+        n_c = psi_c.shape[0] if c_idx is None else int(c_idx.numel())
+        if c_idx is not None:
+            self._c(c_idx, "c_idx", torch.int32)
+        for t, nm in ((E_v, "E_v"), (E_col, "E_col"), (w_col, "w_col")):
+            if t is not None:
+                self._c(t, nm, torch.float64)
+        chi = self.new_chi(iq) if chi is None else self._c(chi, "chi", torch.complex128)
+        self._check(L.lib().chi0_build(self._h, iq, _ptr(psi_v), n_v, _ptr(E_v), _ptr(psi_c), _ptr(c_idx),
+                                       n_c, _ptr(E_col), _ptr(w_col), _ptr(chi), _stream()))
+        return chi
+
+
+def select_accelerated(E_c, N0: int, dE: float, dos_A: float, dos_V0: float, E_max: float):
+    """Columns of Eq. 3/4 from chi0_select_accelerated: (band index, energy, weight)."""
+    E_c = _f64(E_c)
+    cap = int(N0) + int(np.ceil(max(E_max - E_c[min(max(N0, 1), E_c.size) - 1], 0) / dE)) + 2 if E_c.size else 1
+    c_sel = np.empty(cap, np.int32)
+    E_sel = np.empty(cap, np.float64)
+    w_sel = np.empty(cap, np.float64)
+    n = L.lib().chi0_select_accelerated(E_c.ctypes.data, E_c.size, int(N0), float(dE), float(dos_A),
+                                        float(dos_V0), float(E_max), c_sel.ctypes.data, E_sel.ctypes.data,
+                                        w_sel.ctypes.data, cap)
+    if n < 0:
+        raise L.Chi0Error(L.CHI0_ERR_INVALID, "chi0_select_accelerated rejected its input")
+    return c_sel[:n].copy(), E_sel[:n].copy(), w_sel[:n].copy()

@@ -1,0 +1,101 @@
+// Internal declarations shared by the translation units of libchi0.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/chi0.h"
+
+namespace chi0 {
+
+// Pruned-transform structure of one dielectric sphere (one q-point).
+// Stage 1 runs along i3 and keeps k3 in [k3min, k3min+nk3); stage 2 along i2
+// keeps k2 in [k2min, k2min+nk2); the kept (k2,k3) box of every plane i1 is
+// stored; stage 3 runs along i1 for every sphere point.
+struct SphereQ {
+  int nG = 0;
+  int k1min = 0, k2min = 0, k3min = 0;
+  int nk1 = 0, nk2 = 0, nk3 = 0;      // kept extents
+  int nk2p = 0, nk3p = 0;             // padded to a multiple of 4 (twiddle tables)
+  int64_t goff = 0;                   // offset of this sphere in the concatenated list
+  // device tables, sphere points sorted by (k2, k3, k1) ("column order")
+  int* ent_box = nullptr;             // [nG] (k2-k2min)*nk3 + (k3-k3min)
+  int* ent_k1 = nullptr;              // [nG] k1 - k1min
+  int* ent_j = nullptr;               // [nG] index of the point in the caller's order
+  double2* T1d = nullptr; float2* T1f = nullptr;   // [n1][nk1]   exp(+2 pi i k1 i1/n1)
+  double2* T2d = nullptr; float2* T2f = nullptr;   // [n2][nk2p]  exp(+2 pi i k2 i2/n2)
+  double2* T3d = nullptr; float2* T3f = nullptr;   // [n3][nk3p]  exp(+2 pi i k3 i3/n3)
+};
+
+// Structure of the wavefunction sphere for chi0_wfn_to_grid.
+struct WfnSphere {
+  int npw = 0;
+  int w1min = 0, w2min = 0, w3min = 0, nw1 = 0, nw2 = 0, nw3 = 0;
+  int* col_start = nullptr;           // [nw2*nw3 + 1] start of each (g2,g3) column
+  int* col_pw = nullptr;              // [npw] plane-wave index, column order
+  int* col_g1 = nullptr;              // [npw] g1 - w1min, column order
+  double2* T1d = nullptr; float2* T1f = nullptr;   // [n1][nw1]
+  double2* T2d = nullptr; float2* T2f = nullptr;   // [n2][nw2]
+  double2* T3d = nullptr; float2* T3f = nullptr;   // [nw3][n3] (transposed)
+};
+
+}  // namespace chi0
+
+struct chi0_plan_s {
+  int device = 0;
+  int n1 = 0, n2 = 0, n3 = 0;
+  int64_t nr = 0;
+  chi0_precision prec = CHI0_FP64;
+  int n_products = 4;
+  int64_t max_pairs = 0;     // pairs per accumulate block
+  int chain_pairs = 0;       // pairs per TMEM accumulation chain
+  int n_freq = 0;
+  double delta = 0.0;
+  std::vector<double> om_re, om_im;
+  double2* d_omega = nullptr;
+  std::vector<chi0::SphereQ> q;
+  int max_nG = 0;
+  chi0::WfnSphere w;
+  // workspace
+  void* d_D = nullptr;       // per-plane pruned transforms, [pairs][n1][nk2][nk3] complex
+  int64_t D_pairs = 0;       // capacity in pairs
+  void* d_M = nullptr;       // M block used by chi0_build, [max_pairs][max_nG] complex
+  double2* d_f = nullptr;    // frequency factors, [n_freq][max_pairs]
+  void* d_pack = nullptr;    // split operands of the tensor-core contraction
+  size_t pack_bytes = 0;
+  int* d_status = nullptr;   // device status word (bit 0: a bounded wait ran out)
+  size_t ws_bytes = 0;
+  std::string err;
+  bool tc_ready = false;     // tensor-map encoder resolved
+};
+
+namespace chi0 {
+
+bool is_split(const chi0_plan_s* p);
+size_t cbytes(const chi0_plan_s* p);   // bytes of one complex element of psi / M
+
+// ---- kernels (launchers return cudaGetLastError()) ----
+cudaError_t launch_wfn_to_grid(const chi0_plan_s* p, const double2* coeff, int nb, void* psi,
+                               cudaStream_t s);
+// stages 1+2 for pairs (v0..v0+nv) x (c0..c0+nc) into D (local pair index iv*nc + ic)
+cudaError_t launch_pair_planes(const chi0_plan_s* p, int iq, const void* psi_v, const int32_t* v_idx,
+                               int v0, int nv, const void* psi_c, const int32_t* c_idx, int c0,
+                               int nc, void* D, cudaStream_t s);
+// stage 3: D -> M rows (v0+iv)*ldc + (c0+ic)
+cudaError_t launch_pair_gather(const chi0_plan_s* p, int iq, const void* D, int nv, int nc,
+                               int64_t row0, int64_t ldv, void* M, cudaStream_t s);
+// frequency factors f[w][k] for pairs p0..p0+K of an (n_v x n_c) set
+cudaError_t launch_weights(const chi0_plan_s* p, int64_t p0, int64_t K, int n_c, const double* E_v,
+                           const double* E_col, const double* w_col, double2* f, cudaStream_t s);
+cudaError_t launch_contract_f64(const chi0_plan_s* p, int nG, const double2* M, int64_t K,
+                                const double2* f, double2* chi, cudaStream_t s);
+// split-precision tensor-core path for K pairs of M (float2) with factors f
+cudaError_t launch_contract_tc(chi0_plan_s* p, int nG, const float2* M, int64_t K,
+                               const double2* f, double2* chi, cudaStream_t s, std::string* why);
+size_t tc_pack_bytes(const chi0_plan_s* p, int64_t max_pairs, int max_nG);
+bool tc_supported(std::string* why);
+
+}  // namespace chi0

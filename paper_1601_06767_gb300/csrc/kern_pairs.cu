@@ -1,0 +1,299 @@
+// Wavefunctions on the grid and pair matrix elements M_vc(q,G) (definition
+// following Eq. 1): pointwise products conj(psi_v) psi_c on each grid plane,
+// pruned forward transforms along i3 and i2 inside the plane (stages 1-2),
+// then the transform along i1 evaluated only on the G sphere (stage 3).
+//
+// All transforms are direct sums with exact twiddle tables, restricted to the
+// frequencies the sphere needs; the three stages together equal
+// M(G) = (1/N_r) sum_r conj(psi_v(r)) psi_c(r) exp(2 pi i G.r).
+#include <algorithm>
+#include <type_traits>
+
+#include "cplx.cuh"
+#include "internal.h"
+
+namespace chi0 {
+namespace {
+
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------
+// psi[b][i1][i2][i3] = sum_g c_b(g) exp(2 pi i g.r): one CTA per (plane i1, band b)
+// stage A: along g1 for every (g2,g3) column of the sphere (sparse)
+// stage B: along g2 for every (i2, g3); stage C: along g3 for every (i2, i3)
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_wfn_to_grid(const double2* __restrict__ coeff, int npw, int n1, int n2, int n3, int nw1, int nw2,
+              int nw3, const int* __restrict__ col_start, const int* __restrict__ col_pw,
+              const int* __restrict__ col_g1, const typename Cx<R>::T* __restrict__ T1,
+              const typename Cx<R>::T* __restrict__ T2, const typename Cx<R>::T* __restrict__ T3t,
+              typename Cx<R>::T* __restrict__ psi) {
+  using C = typename Cx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* A = reinterpret_cast<C*>(smem_raw);   // [nw2][nw3]
+  C* B = A + nw2 * nw3;                    // [n2][nw3]
+  const int i1 = blockIdx.x;
+  const int64_t b = blockIdx.y;
+  const double2* cb = coeff + b * npw;
+  const C* T1r = T1 + (size_t)i1 * nw1;
+  for (int e = threadIdx.x; e < nw2 * nw3; e += blockDim.x) {
+    C acc = cz(C());
+    const int k1 = col_start[e + 1];
+    for (int k = col_start[e]; k < k1; ++k) cfma(acc, to_c(cb[col_pw[k]], C()), T1r[col_g1[k]]);
+    A[e] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n2 * nw3; e += blockDim.x) {
+    const int i2 = e / nw3, g3 = e - i2 * nw3;
+    const C* t = T2 + (size_t)i2 * nw2;
+    C acc = cz(C());
+    for (int g2 = 0; g2 < nw2; ++g2) cfma(acc, A[g2 * nw3 + g3], t[g2]);
+    B[e] = acc;
+  }
+  __syncthreads();
+  C* out = psi + ((size_t)b * n1 + i1) * (size_t)n2 * n3;
+  for (int e = threadIdx.x; e < n2 * n3; e += blockDim.x) {
+    const int i2 = e / n3, i3 = e - i2 * n3;
+    const C* brow = B + i2 * nw3;
+    C acc = cz(C());
+    for (int g3 = 0; g3 < nw3; ++g3) cfma(acc, brow[g3], T3t[(size_t)g3 * n3 + i3]);
+    out[e] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stages 1+2 for one plane i1, a tile of TV valence bands and a run of
+// conduction bands.  Shared memory: Uv[TV][n2][ld3], Uc[n2][ld3], X[TV][n2][nk3p].
+//   stage 1: X_j(i2,k3) = sum_i3 conj(u_vj(i1,i2,i3)) u_c(i1,i2,i3) e^{2 pi i k3 i3/n3}
+//   stage 2: D_p(i1,k2,k3) = sum_i2 X_j(i2,k3) e^{2 pi i k2 i2/n2}
+// D is [pair][i1][nk2][nk3], pair = jv*nc + jc local to the chunk.
+// ---------------------------------------------------------------------------
+template <typename R, int TV>
+__global__ void __launch_bounds__(kThreads)
+k_pair_planes(const typename Cx<R>::T* __restrict__ psi_v, const int32_t* __restrict__ v_idx, int v0,
+              int nv, const typename Cx<R>::T* __restrict__ psi_c, const int32_t* __restrict__ c_idx,
+              int c0, int nc, int c_per_cta, int n1, int n2, int n3, int ld3, int nk2, int nk3, int nk2p,
+              int nk3p, const typename Cx<R>::T* __restrict__ T2, const typename Cx<R>::T* __restrict__ T3,
+              typename Cx<R>::T* __restrict__ D) {
+  using C = typename Cx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* Uv = reinterpret_cast<C*>(smem_raw);
+  C* Uc = Uv + (size_t)TV * n2 * ld3;
+  C* X = Uc + (size_t)n2 * ld3;
+  const int i1 = blockIdx.x;
+  const int jv0 = blockIdx.y * TV;
+  const int jc_begin = blockIdx.z * c_per_cta;
+  const int jc_end = min(nc, jc_begin + c_per_cta);
+  const int64_t nr = (int64_t)n1 * n2 * n3;
+  const int plane = n2 * n3;
+  const int64_t box = (int64_t)nk2 * nk3;
+
+  for (int j = 0; j < TV; ++j) {
+    const int jv = jv0 + j;
+    const bool ok = jv < nv;
+    const int64_t band = ok ? (v_idx ? v_idx[v0 + jv] : v0 + jv) : 0;
+    const C* src = psi_v + band * nr + (int64_t)i1 * plane;
+    for (int e = threadIdx.x; e < plane; e += blockDim.x) {
+      const int i2 = e / n3, i3 = e - i2 * n3;
+      Uv[((size_t)j * n2 + i2) * ld3 + i3] = ok ? src[e] : cz(C());
+    }
+  }
+  const int items1 = n2 * (nk3p >> 2);
+  const int items2 = nk3 * (nk2p >> 2);
+  for (int jc = jc_begin; jc < jc_end; ++jc) {
+    const int64_t band = c_idx ? c_idx[c0 + jc] : c0 + jc;
+    const C* src = psi_c + band * nr + (int64_t)i1 * plane;
+    for (int e = threadIdx.x; e < plane; e += blockDim.x) {
+      const int i2 = e / n3, i3 = e - i2 * n3;
+      Uc[(size_t)i2 * ld3 + i3] = src[e];
+    }
+    __syncthreads();
+    // stage 1 (along i3)
+    for (int it = threadIdx.x; it < items1; it += blockDim.x) {
+      const int i2 = it % n2, kb = (it / n2) << 2;
+      C acc[TV][4];
+#pragma unroll
+      for (int j = 0; j < TV; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[j][q] = cz(C());
+      const C* uc = Uc + (size_t)i2 * ld3;
+      for (int i3 = 0; i3 < n3; ++i3) {
+        const C c = uc[i3];
+        const C* t = T3 + (size_t)i3 * nk3p + kb;
+        C tw[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tw[q] = __ldg(t + q);
+#pragma unroll
+        for (int j = 0; j < TV; ++j) {
+          const C rho = cconjmul(Uv[((size_t)j * n2 + i2) * ld3 + i3], c);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cfma(acc[j][q], rho, tw[q]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < TV; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) X[((size_t)j * n2 + i2) * nk3p + kb + q] = acc[j][q];
+    }
+    __syncthreads();
+    // stage 2 (along i2)
+    for (int it = threadIdx.x; it < items2; it += blockDim.x) {
+      const int k3 = it % nk3, kb = (it / nk3) << 2;
+      C acc[TV][4];
+#pragma unroll
+      for (int j = 0; j < TV; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[j][q] = cz(C());
+      for (int i2 = 0; i2 < n2; ++i2) {
+        const C* t = T2 + (size_t)i2 * nk2p + kb;
+        C tw[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tw[q] = __ldg(t + q);
+#pragma unroll
+        for (int j = 0; j < TV; ++j) {
+          const C x = X[((size_t)j * n2 + i2) * nk3p + k3];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cfma(acc[j][q], x, tw[q]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < TV; ++j) {
+        const int jv = jv0 + j;
+        if (jv >= nv) continue;
+        C* dst = D + ((int64_t)(jv * nc + jc) * n1 + i1) * box + k3;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (kb + q < nk2) dst[(int64_t)(kb + q) * nk3] = acc[j][q];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 3: M[row][j] = (1/N_r) sum_i1 D_p(i1, k2_j, k3_j) e^{2 pi i k1_j i1/n1}
+// one CTA per local pair; sphere points visited in column order.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_pair_gather(const typename Cx<R>::T* __restrict__ D, int nc, int64_t row0, int64_t ldv, int n1,
+              int64_t box, int nG, int nk1, const int* __restrict__ ent_box, const int* __restrict__ ent_k1,
+              const int* __restrict__ ent_j, const typename Cx<R>::T* __restrict__ T1, R scale,
+              typename Cx<R>::T* __restrict__ M) {
+  using C = typename Cx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* T1s = reinterpret_cast<C*>(smem_raw);
+  for (int e = threadIdx.x; e < n1 * nk1; e += blockDim.x) T1s[e] = T1[e];
+  __syncthreads();
+  const int pl = blockIdx.x;
+  const int jv = pl / nc, jc = pl - jv * nc;
+  const int64_t row = row0 + (int64_t)jv * ldv + jc;
+  const C* Dp = D + (int64_t)pl * n1 * box;
+  C* out = M + row * nG;
+  for (int t = threadIdx.x; t < nG; t += blockDim.x) {
+    const int off = ent_box[t], k1 = ent_k1[t];
+    C acc = cz(C());
+    for (int i1 = 0; i1 < n1; ++i1) cfma(acc, Dp[(int64_t)i1 * box + off], T1s[i1 * nk1 + k1]);
+    acc.x *= scale;
+    acc.y *= scale;
+    out[ent_j[t]] = acc;
+  }
+}
+
+size_t planes_smem(int tv, int n2, int ld3, int nk3p, size_t cb) {
+  return ((size_t)tv * n2 * ld3 + (size_t)n2 * ld3 + (size_t)tv * n2 * nk3p) * cb;
+}
+
+template <typename R, int TV>
+cudaError_t launch_planes_tv(const chi0_plan_s* p, const SphereQ& s, const void* psi_v, const int32_t* v_idx,
+                             int v0, int nv, const void* psi_c, const int32_t* c_idx, int c0, int nc,
+                             void* D, cudaStream_t st) {
+  using C = typename Cx<R>::T;
+  const int ld3 = p->n3 | 1;
+  const size_t sm = planes_smem(TV, p->n2, ld3, s.nk3p, sizeof(C));
+  auto kern = k_pair_planes<R, TV>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const int vt = (nv + TV - 1) / TV;
+  // enough CTAs to fill the machine several times over, but long c runs per CTA
+  int cpc = 16;
+  while (cpc > 1 && (int64_t)p->n1 * vt * ((nc + cpc - 1) / cpc) < 4 * 152) cpc >>= 1;
+  dim3 grid(p->n1, vt, (nc + cpc - 1) / cpc);
+  const C* T2 = std::is_same<R, float>::value ? (const C*)s.T2f : (const C*)s.T2d;
+  const C* T3 = std::is_same<R, float>::value ? (const C*)s.T3f : (const C*)s.T3d;
+  kern<<<grid, kThreads, sm, st>>>((const C*)psi_v, v_idx, v0, nv, (const C*)psi_c, c_idx, c0, nc, cpc,
+                                   p->n1, p->n2, p->n3, ld3, s.nk2, s.nk3, s.nk2p, s.nk3p, T2, T3, (C*)D);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_planes_r(const chi0_plan_s* p, const SphereQ& s, const void* psi_v, const int32_t* v_idx,
+                            int v0, int nv, const void* psi_c, const int32_t* c_idx, int c0, int nc, void* D,
+                            cudaStream_t st) {
+  const int ld3 = p->n3 | 1;
+  const size_t cb = sizeof(typename Cx<R>::T);
+  // prefer two resident CTAs per SM; fall back to one
+  for (size_t cap : {(size_t)110 * 1024, (size_t)220 * 1024}) {
+    if (planes_smem(4, p->n2, ld3, s.nk3p, cb) <= cap)
+      return launch_planes_tv<R, 4>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
+    if (planes_smem(2, p->n2, ld3, s.nk3p, cb) <= cap)
+      return launch_planes_tv<R, 2>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
+    if (planes_smem(1, p->n2, ld3, s.nk3p, cb) <= cap)
+      return launch_planes_tv<R, 1>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
+  }
+  return cudaErrorInvalidConfiguration;
+}
+
+}  // namespace
+
+cudaError_t launch_wfn_to_grid(const chi0_plan_s* p, const double2* coeff, int nb, void* psi, cudaStream_t s) {
+  const WfnSphere& w = p->w;
+  dim3 grid(p->n1, nb);
+  if (is_split(p)) {
+    size_t sm = ((size_t)w.nw2 * w.nw3 + (size_t)p->n2 * w.nw3) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_wfn_to_grid<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_wfn_to_grid<float><<<grid, kThreads, sm, s>>>(coeff, w.npw, p->n1, p->n2, p->n3, w.nw1, w.nw2, w.nw3,
+                                                    w.col_start, w.col_pw, w.col_g1, w.T1f, w.T2f, w.T3f,
+                                                    (float2*)psi);
+  } else {
+    size_t sm = ((size_t)w.nw2 * w.nw3 + (size_t)p->n2 * w.nw3) * sizeof(double2);
+    cudaError_t e = cudaFuncSetAttribute(k_wfn_to_grid<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_wfn_to_grid<double><<<grid, kThreads, sm, s>>>(coeff, w.npw, p->n1, p->n2, p->n3, w.nw1, w.nw2, w.nw3,
+                                                     w.col_start, w.col_pw, w.col_g1, w.T1d, w.T2d, w.T3d,
+                                                     (double2*)psi);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_planes(const chi0_plan_s* p, int iq, const void* psi_v, const int32_t* v_idx, int v0,
+                               int nv, const void* psi_c, const int32_t* c_idx, int c0, int nc, void* D,
+                               cudaStream_t s) {
+  const SphereQ& sq = p->q[iq];
+  if (is_split(p)) return launch_planes_r<float>(p, sq, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, s);
+  return launch_planes_r<double>(p, sq, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, s);
+}
+
+cudaError_t launch_pair_gather(const chi0_plan_s* p, int iq, const void* D, int nv, int nc, int64_t row0,
+                               int64_t ldv, void* M, cudaStream_t s) {
+  const SphereQ& sq = p->q[iq];
+  const int64_t box = (int64_t)sq.nk2 * sq.nk3;
+  const int npl = nv * nc;
+  if (npl == 0) return cudaSuccess;
+  if (is_split(p)) {
+    size_t sm = (size_t)p->n1 * sq.nk1 * sizeof(float2);
+    k_pair_gather<float><<<npl, kThreads, sm, s>>>((const float2*)D, nc, row0, ldv, p->n1, box, sq.nG, sq.nk1,
+                                                   sq.ent_box, sq.ent_k1, sq.ent_j, sq.T1f,
+                                                   (float)(1.0 / (double)p->nr), (float2*)M);
+  } else {
+    size_t sm = (size_t)p->n1 * sq.nk1 * sizeof(double2);
+    k_pair_gather<double><<<npl, kThreads, sm, s>>>((const double2*)D, nc, row0, ldv, p->n1, box, sq.nG,
+                                                    sq.nk1, sq.ent_box, sq.ent_k1, sq.ent_j, sq.T1d,
+                                                    1.0 / (double)p->nr, (double2*)M);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace chi0

@@ -1,0 +1,455 @@
+// Plan object, argument validation, workspace and the public entry points of
+// libchi0 (host side).  The arithmetic of the hot path lives in the kernels of
+// the other translation units.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using chi0::SphereQ;
+
+namespace {
+
+thread_local std::string g_create_err;
+
+chi0_status fail(chi0_plan_s* p, chi0_status st, const std::string& msg) {
+  if (p) p->err = msg; else g_create_err = msg;
+  return st;
+}
+
+#define CK(p, call)                                                                     \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      return fail((p), e_ == cudaErrorMemoryAllocation ? CHI0_ERR_OOM : CHI0_ERR_CUDA,  \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    }                                                                                   \
+  } while (0)
+
+// exp(+2 pi i k j / n) with the phase reduced exactly in integers first.
+void twiddle(int k, int j, int n, double* re, double* im) {
+  long long m = ((long long)k * (long long)j) % n;
+  if (m < 0) m += n;
+  double ang = 2.0 * M_PI * (double)m / (double)n;
+  *re = cos(ang);
+  *im = sin(ang);
+}
+
+template <typename T>
+cudaError_t upload(T** dst, const std::vector<T>& src) {
+  *dst = nullptr;
+  if (src.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)dst, src.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// table[j][k - kmin] = exp(2 pi i k j / n), padded columns are zero
+cudaError_t make_table(int n, int kmin, int nk, int nkp, double2** dd, float2** df) {
+  std::vector<double2> td((size_t)n * nkp);
+  std::vector<float2> tf((size_t)n * nkp);
+  for (int j = 0; j < n; ++j)
+    for (int c = 0; c < nkp; ++c) {
+      double re = 0.0, im = 0.0;
+      if (c < nk) twiddle(kmin + c, j, n, &re, &im);
+      td[(size_t)j * nkp + c] = make_double2(re, im);
+      tf[(size_t)j * nkp + c] = make_float2((float)re, (float)im);
+    }
+  cudaError_t e = upload(dd, td);
+  if (e != cudaSuccess) return e;
+  return upload(df, tf);
+}
+
+// transposed table[k - kmin][j] = exp(2 pi i k j / n)
+cudaError_t make_table_t(int n, int kmin, int nk, double2** dd, float2** df) {
+  std::vector<double2> td((size_t)n * nk);
+  std::vector<float2> tf((size_t)n * nk);
+  for (int c = 0; c < nk; ++c)
+    for (int j = 0; j < n; ++j) {
+      double re, im;
+      twiddle(kmin + c, j, n, &re, &im);
+      td[(size_t)c * n + j] = make_double2(re, im);
+      tf[(size_t)c * n + j] = make_float2((float)re, (float)im);
+    }
+  cudaError_t e = upload(dd, td);
+  if (e != cudaSuccess) return e;
+  return upload(df, tf);
+}
+
+void free_sphere(SphereQ& s) {
+  cudaFree(s.ent_box); cudaFree(s.ent_k1); cudaFree(s.ent_j);
+  cudaFree(s.T1d); cudaFree(s.T1f); cudaFree(s.T2d); cudaFree(s.T2f);
+  cudaFree(s.T3d); cudaFree(s.T3f);
+  s = SphereQ();
+}
+
+void free_plan(chi0_plan_s* p) {
+  for (auto& s : p->q) free_sphere(s);
+  chi0::WfnSphere& w = p->w;
+  cudaFree(w.col_start); cudaFree(w.col_pw); cudaFree(w.col_g1);
+  cudaFree(w.T1d); cudaFree(w.T1f); cudaFree(w.T2d); cudaFree(w.T2f);
+  cudaFree(w.T3d); cudaFree(w.T3f);
+  cudaFree(p->d_omega); cudaFree(p->d_D); cudaFree(p->d_M); cudaFree(p->d_f);
+  cudaFree(p->d_pack); cudaFree(p->d_status);
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+chi0_status analyse_sphere(chi0_plan_s* p, const int32_t* g, int nG, SphereQ* s) {
+  int lo[3] = {g[0], g[1], g[2]}, hi[3] = {g[0], g[1], g[2]};
+  for (int j = 0; j < nG; ++j)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], g[3 * j + a]);
+      hi[a] = std::max(hi[a], g[3 * j + a]);
+    }
+  const int n[3] = {p->n1, p->n2, p->n3};
+  for (int a = 0; a < 3; ++a)
+    if (hi[a] - lo[a] + 1 > n[a])
+      return fail(p, CHI0_ERR_INVALID, "a G sphere spans more grid points than the grid along axis " +
+                                           std::to_string(a + 1));
+  s->nG = nG;
+  s->k1min = lo[0]; s->k2min = lo[1]; s->k3min = lo[2];
+  s->nk1 = hi[0] - lo[0] + 1; s->nk2 = hi[1] - lo[1] + 1; s->nk3 = hi[2] - lo[2] + 1;
+  s->nk2p = round_up(s->nk2, 4); s->nk3p = round_up(s->nk3, 4);
+  std::vector<int> order(nG);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    for (int k : {1, 2, 0}) {
+      if (g[3 * a + k] != g[3 * b + k]) return g[3 * a + k] < g[3 * b + k];
+    }
+    return false;
+  });
+  std::vector<int> box(nG), k1(nG), jj(nG);
+  for (int t = 0; t < nG; ++t) {
+    int j = order[t];
+    box[t] = (g[3 * j + 1] - s->k2min) * s->nk3 + (g[3 * j + 2] - s->k3min);
+    k1[t] = g[3 * j] - s->k1min;
+    jj[t] = j;
+  }
+  CK(p, upload(&s->ent_box, box));
+  CK(p, upload(&s->ent_k1, k1));
+  CK(p, upload(&s->ent_j, jj));
+  CK(p, make_table(p->n1, s->k1min, s->nk1, s->nk1, &s->T1d, &s->T1f));
+  CK(p, make_table(p->n2, s->k2min, s->nk2, s->nk2p, &s->T2d, &s->T2f));
+  CK(p, make_table(p->n3, s->k3min, s->nk3, s->nk3p, &s->T3d, &s->T3f));
+  return CHI0_OK;
+}
+
+chi0_status analyse_wfn(chi0_plan_s* p, const int32_t* g, int npw) {
+  chi0::WfnSphere& w = p->w;
+  w.npw = npw;
+  if (npw <= 0 || !g) return CHI0_OK;  // wavefunction transform not configured
+  int lo[3] = {g[0], g[1], g[2]}, hi[3] = {g[0], g[1], g[2]};
+  for (int j = 0; j < npw; ++j)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], g[3 * j + a]);
+      hi[a] = std::max(hi[a], g[3 * j + a]);
+    }
+  const int n[3] = {p->n1, p->n2, p->n3};
+  for (int a = 0; a < 3; ++a)
+    if (hi[a] - lo[a] + 1 > n[a])
+      return fail(p, CHI0_ERR_INVALID, "the wavefunction sphere does not fit the grid");
+  w.w1min = lo[0]; w.w2min = lo[1]; w.w3min = lo[2];
+  w.nw1 = hi[0] - lo[0] + 1; w.nw2 = hi[1] - lo[1] + 1; w.nw3 = hi[2] - lo[2] + 1;
+  const int ncol = w.nw2 * w.nw3;
+  std::vector<int> cnt(ncol + 1, 0), start(ncol + 1, 0);
+  for (int j = 0; j < npw; ++j) cnt[(g[3 * j + 1] - lo[1]) * w.nw3 + (g[3 * j + 2] - lo[2])]++;
+  for (int c = 0; c < ncol; ++c) start[c + 1] = start[c] + cnt[c];
+  std::vector<int> fill(start.begin(), start.end() - 1), pw(npw), g1(npw);
+  for (int j = 0; j < npw; ++j) {
+    int c = (g[3 * j + 1] - lo[1]) * w.nw3 + (g[3 * j + 2] - lo[2]);
+    int t = fill[c]++;
+    pw[t] = j;
+    g1[t] = g[3 * j] - lo[0];
+  }
+  CK(p, upload(&w.col_start, start));
+  CK(p, upload(&w.col_pw, pw));
+  CK(p, upload(&w.col_g1, g1));
+  CK(p, make_table(p->n1, w.w1min, w.nw1, w.nw1, &w.T1d, &w.T1f));
+  CK(p, make_table(p->n2, w.w2min, w.nw2, w.nw2, &w.T2d, &w.T2f));
+  CK(p, make_table_t(p->n3, w.w3min, w.nw3, &w.T3d, &w.T3f));
+  return CHI0_OK;
+}
+
+bool env_fault(const char* what) {
+  const char* e = getenv("CHI0_FAULT");
+  return e && strcmp(e, what) == 0;
+}
+
+chi0_status check_plan(chi0_plan_s* p) {
+  if (!p) return CHI0_ERR_INVALID;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device)
+    return fail(p, CHI0_ERR_INVALID, "the current device is not the plan's device");
+  return CHI0_OK;
+}
+
+}  // namespace
+
+namespace chi0 {
+bool is_split(const chi0_plan_s* p) { return p->prec != CHI0_FP64; }
+size_t cbytes(const chi0_plan_s* p) { return is_split(p) ? sizeof(float2) : sizeof(double2); }
+}  // namespace chi0
+
+extern "C" {
+
+const char* chi0_last_error(chi0_plan plan) {
+  return plan ? plan->err.c_str() : g_create_err.c_str();
+}
+
+size_t chi0_workspace_bytes(chi0_plan plan) { return plan ? plan->ws_bytes : 0; }
+
+chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* d) {
+  if (!out) return fail(nullptr, CHI0_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!d) return fail(nullptr, CHI0_ERR_INVALID, "desc is NULL");
+  if (d->n1 < 2 || d->n2 < 2 || d->n3 < 2 || d->n1 > 512 || d->n2 > 512 || d->n3 > 512)
+    return fail(nullptr, CHI0_ERR_INVALID, "grid extents must be in [2, 512]");
+  if (d->n_q < 1 || !d->n_G || !d->gvec) return fail(nullptr, CHI0_ERR_INVALID, "need n_q >= 1, n_G and gvec");
+  if (d->n_freq < 1 || !d->freq_re || !d->freq_im)
+    return fail(nullptr, CHI0_ERR_INVALID, "need n_freq >= 1 and frequency arrays");
+  if (d->precision != CHI0_FP64 && d->precision != CHI0_SPLIT_BF16 && d->precision != CHI0_SPLIT_FP16)
+    return fail(nullptr, CHI0_ERR_INVALID, "unknown precision");
+  if (d->npw < 0 || (d->npw > 0 && !d->gw)) return fail(nullptr, CHI0_ERR_INVALID, "bad wavefunction sphere");
+  if (d->chain_pairs < 0 || d->chain_pairs % 32 != 0)
+    return fail(nullptr, CHI0_ERR_INVALID, "chain_pairs must be a non-negative multiple of 32");
+  if (d->max_pairs < 0) return fail(nullptr, CHI0_ERR_INVALID, "max_pairs must be >= 0");
+  if (d->n_products != 0 && d->n_products != 3 && d->n_products != 4)
+    return fail(nullptr, CHI0_ERR_INVALID, "n_products must be 0, 3 or 4");
+  for (int i = 0; i < d->n_q; ++i)
+    if (d->n_G[i] < 1 || d->n_G[i] > 65536) return fail(nullptr, CHI0_ERR_INVALID, "n_G must be in [1, 65536]");
+  if (env_fault("bad_shape")) return fail(nullptr, CHI0_ERR_INVALID, "injected fault: bad_shape");
+
+  chi0_plan_s* p = new chi0_plan_s();
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return fail(nullptr, CHI0_ERR_CUDA, "no CUDA device");
+  }
+  p->n1 = d->n1; p->n2 = d->n2; p->n3 = d->n3;
+  p->nr = (int64_t)d->n1 * d->n2 * d->n3;
+  p->prec = d->precision;
+  p->n_products = d->n_products ? d->n_products : (d->precision == CHI0_SPLIT_FP16 ? 3 : 4);
+  p->delta = d->delta;
+  p->n_freq = d->n_freq;
+  p->om_re.assign(d->freq_re, d->freq_re + d->n_freq);
+  p->om_im.assign(d->freq_im, d->freq_im + d->n_freq);
+  p->chain_pairs = d->chain_pairs ? d->chain_pairs : 128;
+
+  chi0_status st = CHI0_OK;
+  auto bail = [&](chi0_status s) {
+    g_create_err = p->err;
+    free_plan(p);
+    delete p;
+    return s;
+  };
+  if (chi0::is_split(p)) {
+    std::string why;
+    if (!chi0::tc_supported(&why)) {
+      p->err = "split precision needs the tcgen05 tensor cores of sm_103a: " + why;
+      return bail(CHI0_ERR_UNSUPPORTED);
+    }
+  }
+  {
+    std::vector<double2> om(p->n_freq);
+    for (int i = 0; i < p->n_freq; ++i) om[i] = make_double2(p->om_re[i], p->om_im[i]);
+    cudaError_t e = upload(&p->d_omega, om);
+    if (e != cudaSuccess) { p->err = cudaGetErrorString(e); return bail(CHI0_ERR_CUDA); }
+  }
+  int64_t off = 0;
+  p->q.resize(d->n_q);
+  for (int i = 0; i < d->n_q; ++i) {
+    st = analyse_sphere(p, d->gvec + 3 * off, d->n_G[i], &p->q[i]);
+    if (st != CHI0_OK) return bail(st);
+    p->q[i].goff = off;
+    off += d->n_G[i];
+    p->max_nG = std::max(p->max_nG, d->n_G[i]);
+  }
+  st = analyse_wfn(p, d->gw, d->npw);
+  if (st != CHI0_OK) return bail(st);
+
+  // workspace
+  const size_t cb = chi0::cbytes(p);
+  int64_t box = 0;
+  for (auto& s : p->q) box = std::max<int64_t>(box, (int64_t)p->n1 * s.nk2 * s.nk3);
+  int64_t mp = d->max_pairs ? d->max_pairs : (chi0::is_split(p) ? 8192 : 4096);
+  mp = std::max<int64_t>(64, (mp + 63) / 64 * 64);
+  p->max_pairs = mp;
+  // D holds the per-plane transforms of up to D_pairs pairs (about 1 GiB)
+  p->D_pairs = std::max<int64_t>(64, std::min<int64_t>(mp, ((int64_t)1 << 30) / (box * (int64_t)cb)));
+  size_t bytes_D = (size_t)p->D_pairs * box * cb;
+  size_t bytes_M = (size_t)mp * p->max_nG * cb;
+  size_t bytes_f = (size_t)p->n_freq * mp * sizeof(double2);
+  p->pack_bytes = chi0::is_split(p) ? chi0::tc_pack_bytes(p, mp, p->max_nG) : 0;
+  if (env_fault("oom")) { p->err = "injected fault: oom"; return bail(CHI0_ERR_OOM); }
+  cudaError_t e;
+  if ((e = cudaMalloc(&p->d_D, bytes_D)) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_M, bytes_M)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&p->d_f, bytes_f)) != cudaSuccess ||
+      (p->pack_bytes && (e = cudaMalloc(&p->d_pack, p->pack_bytes)) != cudaSuccess) ||
+      (e = cudaMalloc((void**)&p->d_status, sizeof(int))) != cudaSuccess ||
+      (e = cudaMemset(p->d_status, 0, sizeof(int))) != cudaSuccess) {
+    p->err = std::string("workspace allocation: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    return bail(e == cudaErrorMemoryAllocation ? CHI0_ERR_OOM : CHI0_ERR_CUDA);
+  }
+  p->ws_bytes = bytes_D + bytes_M + bytes_f + p->pack_bytes + sizeof(int);
+  *out = p;
+  return CHI0_OK;
+}
+
+chi0_status chi0_plan_destroy(chi0_plan p) {
+  if (!p) return CHI0_OK;
+  cudaDeviceSynchronize();
+  free_plan(p);
+  delete p;
+  return CHI0_OK;
+}
+
+chi0_status chi0_sync_status(chi0_plan p, void* stream) {
+  chi0_status st = check_plan(p);
+  if (st != CHI0_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(p, cudaStreamSynchronize(s));
+  int h = 0;
+  CK(p, cudaMemcpy(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(p, cudaMemset(p->d_status, 0, sizeof(int)));
+  if (h) return fail(p, CHI0_ERR_TIMEOUT, "a bounded device-side wait ran out (status " + std::to_string(h) + ")");
+  return CHI0_OK;
+}
+
+chi0_status chi0_wfn_to_grid(chi0_plan p, const void* coeff, int nb, void* psi, void* stream) {
+  chi0_status st = check_plan(p);
+  if (st != CHI0_OK) return st;
+  if (p->w.npw <= 0) return fail(p, CHI0_ERR_INVALID, "the plan has no wavefunction sphere");
+  if (nb < 0 || (nb > 0 && (!coeff || !psi))) return fail(p, CHI0_ERR_INVALID, "bad band count or NULL buffer");
+  if (nb == 0) return CHI0_OK;
+  CK(p, chi0::launch_wfn_to_grid(p, (const double2*)coeff, nb, psi, (cudaStream_t)stream));
+  return CHI0_OK;
+}
+
+// Pairs of valence rows 0..n_v and conduction columns c_base..c_base+n_c (column ic of the
+// index space is band c_idx[ic], or ic when c_idx is NULL); M row = iv*ld_pairs_c + (ic - c_base).
+static chi0_status pairs_impl(chi0_plan p, int iq, const void* psi_v, const int32_t* v_idx, int n_v,
+                              const void* psi_c, const int32_t* c_idx, int c_base, int n_c, void* M,
+                              int64_t ld_pairs_c, cudaStream_t s) {
+  // chunk over (v, c) so one chunk's per-plane transforms fit the D buffer
+  int vchunk = (int)std::min<int64_t>(n_v, p->D_pairs);
+  int cchunk = (int)std::max<int64_t>(1, std::min<int64_t>(n_c, p->D_pairs / vchunk));
+  for (int v0 = 0; v0 < n_v; v0 += vchunk) {
+    int nv = std::min(vchunk, n_v - v0);
+    for (int c0 = 0; c0 < n_c; c0 += cchunk) {
+      int nc = std::min(cchunk, n_c - c0);
+      CK(p, chi0::launch_pair_planes(p, iq, psi_v, v_idx, v0, nv, psi_c, c_idx, c_base + c0, nc, p->d_D, s));
+      CK(p, chi0::launch_pair_gather(p, iq, p->d_D, nv, nc, (int64_t)v0 * ld_pairs_c + c0, ld_pairs_c, M, s));
+    }
+  }
+  return CHI0_OK;
+}
+
+chi0_status chi0_pairs(chi0_plan p, int iq, const void* psi_v, const int32_t* v_idx, int n_v,
+                       const void* psi_c, const int32_t* c_idx, int n_c, void* M, void* stream) {
+  chi0_status st = check_plan(p);
+  if (st != CHI0_OK) return st;
+  if (iq < 0 || iq >= (int)p->q.size()) return fail(p, CHI0_ERR_INVALID, "iq out of range");
+  if (n_v < 0 || n_c < 0) return fail(p, CHI0_ERR_INVALID, "negative band count");
+  if ((int64_t)n_v * n_c == 0) return CHI0_OK;
+  if (!psi_v || !psi_c || !M) return fail(p, CHI0_ERR_INVALID, "NULL buffer");
+  return pairs_impl(p, iq, psi_v, v_idx, n_v, psi_c, c_idx, 0, n_c, M, n_c, (cudaStream_t)stream);
+}
+
+static chi0_status accumulate_impl(chi0_plan p, int iq, const void* M, int n_v, int n_c,
+                                   const double* E_v, const double* E_col, const double* w_col,
+                                   void* chi, cudaStream_t s) {
+  const int nG = p->q[iq].nG;
+  const int64_t np = (int64_t)n_v * n_c;
+  for (int64_t p0 = 0; p0 < np; p0 += p->max_pairs) {
+    int64_t K = std::min<int64_t>(p->max_pairs, np - p0);
+    CK(p, chi0::launch_weights(p, p0, K, n_c, E_v, E_col, w_col, p->d_f, s));
+    if (chi0::is_split(p)) {
+      std::string why;
+      cudaError_t e = chi0::launch_contract_tc(p, nG, (const float2*)M + p0 * nG, K, p->d_f,
+                                               (double2*)chi, s, &why);
+      if (e != cudaSuccess)
+        return fail(p, CHI0_ERR_CUDA, "tensor-core contraction: " + why + " " + cudaGetErrorString(e));
+    } else {
+      CK(p, chi0::launch_contract_f64(p, nG, (const double2*)M + p0 * nG, K, p->d_f, (double2*)chi, s));
+    }
+  }
+  return CHI0_OK;
+}
+
+chi0_status chi0_accumulate(chi0_plan p, int iq, const void* M, int n_v, int n_c, const double* E_v,
+                            const double* E_col, const double* w_col, void* chi0, void* stream) {
+  chi0_status st = check_plan(p);
+  if (st != CHI0_OK) return st;
+  if (iq < 0 || iq >= (int)p->q.size()) return fail(p, CHI0_ERR_INVALID, "iq out of range");
+  if (n_v < 0 || n_c < 0) return fail(p, CHI0_ERR_INVALID, "negative band count");
+  if ((int64_t)n_v * n_c == 0) return CHI0_OK;
+  if (!M || !E_v || !E_col || !chi0) return fail(p, CHI0_ERR_INVALID, "NULL buffer");
+  return accumulate_impl(p, iq, M, n_v, n_c, E_v, E_col, w_col, chi0, (cudaStream_t)stream);
+}
+
+chi0_status chi0_build(chi0_plan p, int iq, const void* psi_v, int n_v, const double* E_v,
+                       const void* psi_c, const int32_t* c_idx, int n_c, const double* E_col,
+                       const double* w_col, void* chi0, void* stream) {
+  chi0_status st = check_plan(p);
+  if (st != CHI0_OK) return st;
+  if (iq < 0 || iq >= (int)p->q.size()) return fail(p, CHI0_ERR_INVALID, "iq out of range");
+  if (n_v < 0 || n_c < 0) return fail(p, CHI0_ERR_INVALID, "negative band count");
+  if ((int64_t)n_v * n_c == 0) return CHI0_OK;
+  if (!psi_v || !psi_c || !E_v || !E_col || !chi0) return fail(p, CHI0_ERR_INVALID, "NULL buffer");
+  if (n_v > p->max_pairs)
+    return fail(p, CHI0_ERR_INVALID, "n_v exceeds the plan's pair block; raise max_pairs");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int cb = (int)std::max<int64_t>(1, p->max_pairs / n_v);
+  for (int c0 = 0; c0 < n_c; c0 += cb) {
+    int nc = std::min(cb, n_c - c0);
+    st = pairs_impl(p, iq, psi_v, nullptr, n_v, psi_c, c_idx, c0, nc, p->d_M, nc, s);
+    if (st != CHI0_OK) return st;
+    st = accumulate_impl(p, iq, p->d_M, n_v, nc, E_v, E_col + c0, w_col ? w_col + c0 : nullptr, chi0, s);
+    if (st != CHI0_OK) return st;
+  }
+  return CHI0_OK;
+}
+
+int chi0_select_accelerated(const double* E_c, int n_c, int N0, double dE, double dos_A, double dos_V0,
+                            double E_max, int32_t* c_sel, double* E_sel, double* w_sel, int cap) {
+  if (!E_c || n_c < 0 || N0 < 0 || !(dE > 0.0) || !c_sel || !E_sel || !w_sel || cap < 0) return -1;
+  for (int i = 1; i < n_c; ++i)
+    if (E_c[i] < E_c[i - 1]) return -1;
+  N0 = std::min(N0, n_c);
+  int n = 0;
+  for (int c = 0; c < N0; ++c) {            // explicit part of Eq. 3
+    if (n >= cap) return -1;
+    c_sel[n] = c; E_sel[n] = E_c[c]; w_sel[n] = 1.0; ++n;
+  }
+  if (N0 == 0 || N0 >= n_c) return n;
+  const double E0 = E_c[N0 - 1];
+  const double span = E_max - E0;
+  int NE = (int)ceil(span / dE - 1e-12);
+  if (NE < 0) NE = 0;
+  for (int i = 0; i < NE; ++i) {            // grid points of Eq. 4
+    double lo = std::min(E0 + dE * i, E_max), hi = std::min(E0 + dE * (i + 1), E_max);
+    double Ei = 0.5 * (lo + hi), dEi = hi - lo;
+    // nearest band above N0; E_c is sorted, so bisect then compare neighbours
+    int a = N0, b = n_c;                     // first index with E_c >= Ei
+    while (a < b) { int m = (a + b) / 2; if (E_c[m] < Ei) a = m + 1; else b = m; }
+    int best = a < n_c ? a : n_c - 1;
+    if (a > N0 && (a == n_c || fabs(E_c[a - 1] - Ei) <= fabs(E_c[a] - Ei))) best = a - 1;
+    // ties go to the lowest index among equal energies
+    while (best > N0 && E_c[best - 1] == E_c[best]) --best;
+    double g = (Ei > dos_V0) ? dos_A * sqrt(2.0 * (Ei - dos_V0)) : 0.0;
+    if (n >= cap) return -1;
+    c_sel[n] = best; E_sel[n] = Ei; w_sel[n] = g * dEi; ++n;
+  }
+  return n;
+}
+
+}  // extern "C"

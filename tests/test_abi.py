@@ -1,0 +1,85 @@
+"""Host-side checks of the C ABI: the library loads without a GPU, exports
+every function include/chi0.h declares, and its host-only band selection
+(Eq. 3/4) equals the oracle's."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1601_06767_gb300 as P
+from paper_1601_06767_gb300 import _lib as L
+from oracle import select_accelerated as oracle_select
+from synth import HARTREE_EV, make_problem
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "chi0.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(chi0_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported_and_bound():
+    names = _declared()
+    assert len(names) >= 10
+    h = C.CDLL(L.LIB_PATH)
+    for n in names:
+        assert hasattr(h, n), n
+    bound = {s[0] for s in L.SIGNATURES}
+    assert set(names) <= bound, set(names) - bound
+
+
+def test_create_rejects_bad_descriptions_without_a_device():
+    lib = P.lib()
+    h = C.c_void_p()
+    assert lib.chi0_plan_create(C.byref(h), None) == L.CHI0_ERR_INVALID
+    assert b"desc" in lib.chi0_last_error(None)
+    d = L.Chi0PlanDesc()
+    d.n1 = d.n2 = d.n3 = 1
+    assert lib.chi0_plan_create(C.byref(h), C.byref(d)) == L.CHI0_ERR_INVALID
+    assert h.value is None
+
+
+def _oracle_columns(E_c, N0, dE, A, V0, Emax):
+    o = oracle_select(E_c, N0, dE, A, V0, Emax)
+    c = np.concatenate([o["explicit"], o["rep"]])
+    E = np.concatenate([np.asarray(E_c)[o["explicit"]], o["E_i"]])
+    w = np.concatenate([np.ones(o["explicit"].size), o["w_i"]])
+    return c, E, w
+
+
+@pytest.mark.parametrize("name", ["c2", "c5"])
+@pytest.mark.parametrize("dE_eV", [1.5, 2.0, 2.5, 3.0, 3.5, 4.0])
+def test_select_matches_oracle(name, dE_eV):
+    pr = make_problem(name)
+    dE = dE_eV / HARTREE_EV
+    c, E, w = P.select_accelerated(pr.E_c, pr.N0, dE, pr.dos_A, pr.dos_V0, pr.E_max)
+    oc, oE, ow = _oracle_columns(pr.E_c, pr.N0, dE, pr.dos_A, pr.dos_V0, pr.E_max)
+    assert np.array_equal(c, oc)
+    assert np.array_equal(E, oE)
+    assert np.allclose(w, ow, rtol=1e-15, atol=0)
+
+
+def test_select_ties_and_degenerate_bands():
+    rng = np.random.default_rng(0)
+    E_c = np.sort(np.round(rng.uniform(0.17, 2.2, 400), 2))   # many exact degeneracies
+    for N0 in (0, 1, 37, 399, 400, 500):
+        c, E, w = P.select_accelerated(E_c, N0, 0.031, 80.0, 0.17, 2.2)
+        oc, oE, ow = _oracle_columns(E_c, N0, 0.031, 80.0, 0.17, 2.2)
+        assert np.array_equal(c, oc) and np.array_equal(E, oE) and np.allclose(w, ow, rtol=1e-15)
+
+
+def test_select_rejects_unsorted_and_small_capacity():
+    lib = P.lib()
+    E = np.array([0.3, 0.2, 0.5])
+    out_c = np.empty(8, np.int32)
+    out_e = np.empty(8)
+    out_w = np.empty(8)
+    assert lib.chi0_select_accelerated(E.ctypes.data, 3, 1, 0.1, 1.0, 0.17, 2.2, out_c.ctypes.data,
+                                       out_e.ctypes.data, out_w.ctypes.data, 8) == -1
+    E = np.sort(E)
+    assert lib.chi0_select_accelerated(E.ctypes.data, 3, 1, 0.1, 1.0, 0.17, 2.2, out_c.ctypes.data,
+                                       out_e.ctypes.data, out_w.ctypes.data, 2) == -1
