@@ -70,10 +70,14 @@ typedef struct {
   const double* freq_im;     /* [n_freq] Im(omega), Hartree */
   double delta;              /* broadening d of Eq. 1, Hartree */
   chi0_precision precision;
-  int n_products;            /* split products per real product: 3 (hh+hl+lh) or 4 (+ll); 0 = 4 for
-                                BF16, 3 for FP16; ignored for FP64 */
+  int n_products;            /* 16-bit terms and products per real product: 3 = two terms t0+t1,
+                                products t0t0+t0t1+t1t0; 4 = two terms, adds t1t1; 6 = three terms
+                                t0+t1+t2, products t_i t_j with i+j <= 2.  0 = 6 for BF16 (three
+                                BF16 terms carry 24 bits), 3 for FP16; ignored for FP64 */
   int64_t max_pairs;         /* pairs per internal block of chi0_build / chi0_accumulate; 0 = default */
-  int chain_pairs;           /* pairs per tensor-core accumulation chain (multiple of 32); 0 = default */
+  int chain_pairs;           /* pairs accumulated in tensor memory before they are added into FP32
+                                registers (multiple of 32).  The tensor cores round each MMA result
+                                toward zero, so the bias grows with this length; 0 = 32 (default) */
 } chi0_plan_desc;
 
 /* Create a plan: validates the description, analyses each G sphere for the

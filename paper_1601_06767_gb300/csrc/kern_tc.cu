@@ -1,20 +1,480 @@
-// Split-precision tensor-core contraction (tcgen05) - placeholder until the
-// kernel lands; split plans are refused at plan creation.
+// Split-precision tensor-core contraction of Eq. 1 on sm_103a:
+//   chi0[w][G][H] += sum_p f_p(w) M_p(G) conj(M_p(H))
+//
+// Real form:   Re chi = sum_p Wr Mr + Wi Mi,   Im chi = sum_p Wi Mr - Wr Mi,
+// with W = f_p(w) M_p (FP32).  Every real operand x is split into NT 16-bit
+// terms x = t0 + t1 (+ t2), t0 = rn(x), t1 = rn(x - t0), t2 = rn(x - t0 - t1);
+// a real product keeps the term products t_i t_j with i + j < NT (plus t1 t1
+// for the four-product two-term variant).  Operands are first scaled by exact
+// powers of two so that the largest magnitude of the block sits near 2^14
+// (keeps FP16 terms normal; harmless for BF16) and the scale is undone in FP64.
+//
+// pack:     M block [K][nG] (FP32 complex) and f -> K-major 16-bit planes
+//           B = {Mr_t..., Mi_t...}[nGp][Kp], A_w = {Wr_t..., Wi_t...}[nGp][Kp].
+// contract: one CTA per (128 x 128 output tile, frequency).  Warp 0 issues TMA
+//           loads into a 3-stage ring, warp 1 issues tcgen05.mma into two
+//           double-buffered TMEM accumulator pairs (Re, Im), warps 2..9 drain
+//           finished accumulation chains into FP32 registers and finally add
+//           the tile into chi0 in FP64.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <string>
+
 #include "internal.h"
+#include "tc_ptx.cuh"
 
 namespace chi0 {
+namespace {
 
-bool tc_supported(std::string* why) {
-  if (why) *why = "tensor-core contraction not built";
-  return false;
+constexpr int BM = 128, BN = 128, BK = 32;
+constexpr int TILE_BYTES = BM * BK * 2;           // 8 KB per plane tile
+constexpr int RING_BYTES = 6 * 32768;              // operand ring in shared memory
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 64 + EPI_WARPS * 32;
+constexpr int TMEM_COLS = 512;                     // 2 buffers x (Re, Im) x 128 columns
+constexpr uint64_t WAIT_BUDGET_NS = 2000000000ull; // 2 s per wait
+constexpr size_t SMEM_BYTES = (size_t)RING_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int MAX_STAGES = 3;
+
+template <int NT> struct Ring {
+  static constexpr int PLANES = 2 * NT;                       // per operand: Re terms, Im terms
+  static constexpr int STAGE_BYTES = 2 * PLANES * TILE_BYTES; // A and B
+  static constexpr int STAGES = RING_BYTES / STAGE_BYTES;     // 3 for NT = 2, 2 for NT = 3
+};
+
+int round_up_i(int x, int m) { return (x + m - 1) / m * m; }
+
+// ---------------------------------------------------------------------------
+// pack: tile of 64 pairs x 32 sphere points, transposed through shared memory
+// ---------------------------------------------------------------------------
+template <bool BF16>
+__device__ __forceinline__ float rn16(float x, uint16_t* bits) {
+  if constexpr (BF16) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    *bits = __bfloat16_as_ushort(h);
+    return __bfloat162float(h);
+  } else {
+    const __half h = __float2half_rn(x);
+    *bits = __half_as_ushort(h);
+    return __half2float(h);
+  }
 }
 
-size_t tc_pack_bytes(const chi0_plan_s*, int64_t, int) { return 0; }
+// split a and b (two consecutive K elements) into NT terms; word t packs term t of (a, b)
+template <bool BF16, int NT>
+__device__ __forceinline__ void splitn(float a, float b, uint32_t (&w)[NT]) {
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    uint16_t ua, ub;
+    const float ta = rn16<BF16>(a, &ua), tb = rn16<BF16>(b, &ub);
+    a -= ta;   // exact: the remainder of a rounding to 8 or 11 bits fits FP32
+    b -= tb;
+    w[t] = (uint32_t)ua | ((uint32_t)ub << 16);
+  }
+}
 
-cudaError_t launch_contract_tc(chi0_plan_s*, int, const float2*, int64_t, const double2*, double2*, cudaStream_t,
-                               std::string* why) {
-  if (why) *why = "not built";
-  return cudaErrorNotSupported;
+// largest |component| of the M block -> amax[0]; of f(w) -> amax[1 + w]
+__global__ void k_absmax(const float2* __restrict__ M, int64_t n, const double2* __restrict__ f, int64_t K,
+                         int n_freq, unsigned int* __restrict__ amax) {
+  float m = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = M[i];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(amax, __float_as_uint(m));
+  for (int iw = 0; iw < n_freq; ++iw) {
+    float g = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x) {
+      const double2 v = f[(int64_t)iw * K + i];
+      g = fmaxf(g, (float)fmax(fabs(v.x), fabs(v.y)));
+    }
+    for (int o = 16; o; o >>= 1) g = fmaxf(g, __shfl_xor_sync(0xffffffffu, g, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(amax + 1 + iw, __float_as_uint(g));
+  }
+}
+
+// power of two 2^(14 - e) with x < 2^e (1 when x is zero or not finite)
+__device__ __forceinline__ float pow2_scale(float x) {
+  if (!(x > 0.f) || !isfinite(x)) return 1.f;
+  int e;
+  frexpf(x, &e);
+  return ldexpf(1.f, 14 - e);
+}
+
+// scale[0] = sM; scale[1 + w] = sW(w); inv[w] = 1 / (sM sW(w))
+__global__ void k_scales(const unsigned int* __restrict__ amax, int n_freq, float* __restrict__ scale,
+                         double* __restrict__ inv) {
+  const float mM = __uint_as_float(amax[0]);
+  const float sM = pow2_scale(mM);
+  if (threadIdx.x == 0) scale[0] = sM;
+  for (int iw = threadIdx.x; iw < n_freq; iw += blockDim.x) {
+    // |Re W|, |Im W| <= 2 max|f| max|M|
+    const float sW = pow2_scale(2.f * __uint_as_float(amax[1 + iw]) * mM);
+    scale[1 + iw] = sW;
+    inv[iw] = 1.0 / ((double)sM * (double)sW);
+  }
+}
+
+// tile of 64 pairs x 32 sphere points, transposed through shared memory
+template <bool BF16, int NT>
+__global__ void __launch_bounds__(256)
+k_pack(const float2* __restrict__ M, int nG, int64_t K, int nGp, int Kp, const double2* __restrict__ f,
+       int n_freq, const float* __restrict__ scale, uint32_t* __restrict__ Bp, uint32_t* __restrict__ Ap) {
+  extern __shared__ __align__(16) unsigned char smem_pack[];
+  float2* tile = reinterpret_cast<float2*>(smem_pack);          // [64][33]
+  float2* fs = tile + 64 * 33;                                 // [n_freq][64]
+  const int G0 = blockIdx.x * 32;
+  const int64_t p0 = (int64_t)blockIdx.y * 64;
+  const float sM = scale[0];
+  for (int e = threadIdx.x; e < 64 * 32; e += blockDim.x) {
+    const int pp = e >> 5, g = e & 31;
+    const int64_t p = p0 + pp;
+    float2 v = make_float2(0.f, 0.f);
+    if (p < K && G0 + g < nG) v = M[p * nG + G0 + g];
+    tile[pp * 33 + g] = v;
+  }
+  for (int e = threadIdx.x; e < n_freq * 64; e += blockDim.x) {
+    const int iw = e >> 6, pp = e & 63;
+    const int64_t p = p0 + pp;
+    float2 v = make_float2(0.f, 0.f);
+    if (p < K) {
+      const double2 d = f[(int64_t)iw * K + p];
+      const float sW = scale[1 + iw];
+      v = make_float2((float)d.x * sW, (float)d.y * sW);
+    }
+    fs[e] = v;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t plane = (size_t)nGp * (Kp / 2);                 // uint32 words per plane
+  const int64_t kw = p0 / 2 + lane;                            // word index along K
+  for (int g = warp; g < 32; g += 8) {
+    const int G = G0 + g;
+    const float2 m0 = tile[(2 * lane) * 33 + g], m1 = tile[(2 * lane + 1) * 33 + g];
+    const size_t row = (size_t)G * (Kp / 2) + kw;
+    uint32_t w[NT];
+    splitn<BF16, NT>(m0.x * sM, m1.x * sM, w);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) Bp[t * plane + row] = w[t];
+    splitn<BF16, NT>(m0.y * sM, m1.y * sM, w);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) Bp[(NT + t) * plane + row] = w[t];
+    for (int iw = 0; iw < n_freq; ++iw) {
+      const float2 f0 = fs[iw * 64 + 2 * lane], f1 = fs[iw * 64 + 2 * lane + 1];
+      const float wr0 = f0.x * m0.x - f0.y * m0.y, wi0 = f0.x * m0.y + f0.y * m0.x;
+      const float wr1 = f1.x * m1.x - f1.y * m1.y, wi1 = f1.x * m1.y + f1.y * m1.x;
+      uint32_t* a = Ap + (size_t)iw * 2 * NT * plane + row;
+      splitn<BF16, NT>(wr0, wr1, w);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) a[t * plane] = w[t];
+      splitn<BF16, NT>(wi0, wi1, w);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) a[(NT + t) * plane] = w[t];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// contraction
+// ---------------------------------------------------------------------------
+struct Barriers {
+  uint64_t full[MAX_STAGES];
+  uint64_t empty[MAX_STAGES];
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint64_t done;
+  uint32_t tmem_base;
+};
+
+// Issue the MMAs of one stage (BK pairs) into the (Re, Im) accumulator pair.
+// The tensor cores round the FP32 accumulator toward zero after every MMA, so
+// each MMA loses about one ulp of the running sum.  Chains are therefore kept
+// to one stage and ordered smallest-first: every term product t_i t_j with
+// i + j > 0 goes in while the accumulator is still small, and the t0 t0
+// products (the only large ones) come last.
+template <bool BF16, int NT>
+__device__ __forceinline__ void issue_stage(const unsigned char* st, uint32_t d_re, uint32_t d_im, bool first,
+                                            int n_products) {
+  constexpr int P = 2 * NT;
+  const uint32_t id_pos = tc::idesc_f16(BF16, false, BM, BN);
+  const uint32_t id_neg = tc::idesc_f16(BF16, true, BM, BN);
+  uint32_t acc_re = first ? 0u : 1u, acc_im = acc_re;
+#pragma unroll
+  for (int order = 2 * NT - 2; order >= 0; --order) {
+#pragma unroll
+    for (int ks = 0; ks < BK / 16; ++ks) {
+#pragma unroll
+      for (int i = 0; i < NT; ++i) {
+        const int j = order - i;
+        if (j < 0 || j >= NT) continue;
+        const bool keep = (i + j < NT) || (NT == 2 && n_products == 4 && i == 1 && j == 1);
+        if (!keep) continue;
+        // planes: Re terms 0..NT-1, Im terms NT..2NT-1; K step ks is +32 bytes
+        const uint64_t ar = tc::sdesc_kmajor_sw64(st + i * TILE_BYTES) + (uint64_t)(ks * 2);
+        const uint64_t ai = tc::sdesc_kmajor_sw64(st + (NT + i) * TILE_BYTES) + (uint64_t)(ks * 2);
+        const uint64_t br = tc::sdesc_kmajor_sw64(st + (P + j) * TILE_BYTES) + (uint64_t)(ks * 2);
+        const uint64_t bi = tc::sdesc_kmajor_sw64(st + (P + NT + j) * TILE_BYTES) + (uint64_t)(ks * 2);
+        // Re += Wr Mr + Wi Mi
+        tc::mma_f16(d_re, ar, br, id_pos, acc_re);
+        acc_re = 1u;
+        tc::mma_f16(d_re, ai, bi, id_pos, 1u);
+        // Im += Wi Mr - Wr Mi
+        tc::mma_f16(d_im, ai, br, id_pos, acc_im);
+        acc_im = 1u;
+        tc::mma_f16(d_im, ar, bi, id_neg, 1u);
+      }
+    }
+  }
+}
+
+template <bool BF16, int NT>
+__global__ void __launch_bounds__(THREADS, 1)
+k_contract_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int nG, int nK,
+              int chain_k, int n_products, const double* __restrict__ inv_scale, double2* __restrict__ chi,
+              int* __restrict__ status) {
+  using RG = Ring<NT>;
+  constexpr int STAGES = RG::STAGES, STAGE_BYTES = RG::STAGE_BYTES, P = RG::PLANES;
+  extern __shared__ __align__(1024) unsigned char smem_tc[];
+  unsigned char* tiles = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_tc) + 1023) & ~uintptr_t(1023));
+  Barriers* bar = reinterpret_cast<Barriers*>(tiles + RING_BYTES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int H0 = blockIdx.x * BN, G0 = blockIdx.y * BM, iw = blockIdx.z;
+  const int nchains = (nK + chain_k - 1) / chain_k;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&bar->full[s], 1);
+      tc::mbar_init(&bar->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&bar->tfull[b], 1);
+      tc::mbar_init(&bar->tempty[b], EPI_WARPS);
+    }
+    tc::mbar_init(&bar->done, 1);
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&tmA);
+    tc::prefetch_tmap(&tmB);
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(&bar->tmem_base, TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = bar->tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      int issued = 0;
+      for (int kc = 0; kc < nK; ++kc) {
+        const int s = kc % STAGES, u = kc / STAGES;
+        if (!tc::mbar_wait(&bar->empty[s], (u & 1) ^ 1, status, 1, WAIT_BUDGET_NS)) break;
+        tc::mbar_arrive_expect_tx(&bar->full[s], STAGE_BYTES);
+        unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+          tc::tma_load_3d(st + j * TILE_BYTES, &tmA, &bar->full[s], kc * BK, G0, iw * P + j);
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+          tc::tma_load_3d(st + (P + j) * TILE_BYTES, &tmB, &bar->full[s], kc * BK, H0, j);
+        issued = kc + 1;
+      }
+      // copies still in flight must land before the CTA may exit
+      for (int kc = max(0, issued - STAGES); kc < issued; ++kc)
+        tc::mbar_wait(&bar->full[kc % STAGES], (kc / STAGES) & 1, status, 1, WAIT_BUDGET_NS);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      for (int kc = 0; kc < nK; ++kc) {
+        const int c = kc / chain_k, buf = c & 1;
+        const bool first = (kc % chain_k) == 0;
+        if (first) {
+          if (!tc::mbar_wait(&bar->tempty[buf], ((c >> 1) & 1) ^ 1, status, 1, WAIT_BUDGET_NS)) break;
+          tc::fence_after();
+        }
+        const int s = kc % STAGES;
+        if (!tc::mbar_wait(&bar->full[s], (kc / STAGES) & 1, status, 1, WAIT_BUDGET_NS)) break;
+        tc::fence_after();
+        const unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
+        const uint32_t d_re = tbase + buf * 256, d_im = d_re + 128;
+        issue_stage<BF16, NT>(st, d_re, d_im, first, n_products);
+        tc::mma_commit(&bar->empty[s]);
+        if ((kc % chain_k) == chain_k - 1 || kc == nK - 1) tc::mma_commit(&bar->tfull[buf]);
+      }
+      tc::mma_commit(&bar->done);
+      tc::mbar_wait(&bar->done, 0, status, 1, WAIT_BUDGET_NS);
+    }
+  } else {
+    // ---------------- epilogue: drain chains, then FP64 merge ----------------
+    const int ew = warp - 2, quad = warp & 3, half = ew >> 2;
+    const int row = quad * 32 + lane;
+    float sre[64], sim[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) { sre[i] = 0.f; sim[i] = 0.f; }
+    bool ok = true;
+    for (int c = 0; c < nchains; ++c) {
+      const int buf = c & 1;
+      if (!tc::mbar_wait(&bar->tfull[buf], (c >> 1) & 1, status, 1, WAIT_BUDGET_NS)) { ok = false; break; }
+      tc::fence_after();
+      const uint32_t ta = tbase + ((uint32_t)(quad * 32) << 16) + buf * 256 + half * 64;
+      float v[32];
+      tc::tmem_ld32(ta, v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < 32; ++i) sre[i] += v[i];
+      tc::tmem_ld32(ta + 32, v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < 32; ++i) sre[32 + i] += v[i];
+      tc::tmem_ld32(ta + 128, v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < 32; ++i) sim[i] += v[i];
+      tc::tmem_ld32(ta + 160, v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < 32; ++i) sim[32 + i] += v[i];
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bar->tempty[buf]);
+    }
+    const int G = G0 + row;
+    if (ok && G < nG) {
+      const double sc = inv_scale[iw];
+      const int Hb = H0 + half * 64;
+      double2* out = chi + ((size_t)iw * nG + G) * nG + Hb;
+#pragma unroll
+      for (int i = 0; i < 64; ++i) {
+        if (Hb + i < nG) {
+          double2 o = out[i];
+          o.x += (double)sre[i] * sc;
+          o.y += (double)sim[i] * sc;
+          out[i] = o;
+        }
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 1) tc::tmem_dealloc(tbase, TMEM_COLS);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool resolve_encoder(std::string* why) {
+  if (g_encode) return true;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+    if (why) *why = "cuTensorMapEncodeTiled is not available from the driver";
+    cudaGetLastError();
+    return false;
+  }
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return true;
+}
+
+bool encode_planes(CUtensorMap* tm, void* base, bool bf16, int Kp, int nGp, int planes, std::string* why) {
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)nGp, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * nGp};
+  cuuint32_t box[3] = {BK, BM, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    if (why) *why = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+bool tc_supported(std::string* why) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    if (why) *why = "no CUDA device";
+    return false;
+  }
+  if (!(prop.major == 10 && prop.minor == 3)) {
+    if (why) *why = "device is sm_" + std::to_string(prop.major) + std::to_string(prop.minor) + ", kernels are built for sm_103a";
+    return false;
+  }
+  return resolve_encoder(why);
+}
+
+int n_terms(const chi0_plan_s* p) { return p->n_products == 6 ? 3 : 2; }
+
+size_t tc_pack_bytes(const chi0_plan_s* p, int64_t max_pairs, int max_nG) {
+  const size_t nGp = (size_t)round_up_i(max_nG, BM);
+  const size_t Kp = (size_t)((max_pairs + 63) / 64 * 64);
+  const size_t planes = 2 * (size_t)n_terms(p) * (1 + (size_t)p->n_freq);
+  const size_t scal = 256 + 32 * (size_t)(p->n_freq + 1);   // amax, scales, inverse scales
+  return planes * nGp * Kp * 2 + scal;
+}
+
+template <bool BF16, int NT>
+cudaError_t run_tc(chi0_plan_s* p, int nG, const float2* M, int64_t K, const double2* f, double2* chi,
+                   cudaStream_t s, std::string* why) {
+  const int nGp = round_up_i(nG, BM);
+  const int Kp = (int)((K + 63) / 64 * 64);
+  const size_t planes_ws = 2 * (size_t)n_terms(p) * (1 + (size_t)p->n_freq) * (size_t)round_up_i(p->max_nG, BM) *
+                           (size_t)((p->max_pairs + 63) / 64 * 64) * 2;
+  uint16_t* Bp = reinterpret_cast<uint16_t*>(p->d_pack);
+  uint16_t* Ap = Bp + (size_t)2 * NT * nGp * Kp;
+  unsigned char* tail = reinterpret_cast<unsigned char*>(p->d_pack) + planes_ws;
+  unsigned int* amax = reinterpret_cast<unsigned int*>(tail);                     // [1 + n_freq]
+  float* scale = reinterpret_cast<float*>(tail + 8 * (size_t)(p->n_freq + 1));   // [1 + n_freq]
+  double* inv = reinterpret_cast<double*>(tail + 16 * (size_t)(p->n_freq + 1));              // [n_freq]
+  cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(unsigned int) * (p->n_freq + 1), s);
+  if (e != cudaSuccess) return e;
+  k_absmax<<<2 * 152, 256, 0, s>>>(M, K * nG, f, K, p->n_freq, amax);
+  k_scales<<<1, 128, 0, s>>>(amax, p->n_freq, scale, inv);
+  dim3 gpk(nGp / 32, Kp / 64);
+  const size_t smp = (size_t)(64 * 33 + 64 * p->n_freq) * sizeof(float2);
+  e = cudaFuncSetAttribute(k_pack<BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+  if (e != cudaSuccess) return e;
+  k_pack<BF16, NT><<<gpk, 256, smp, s>>>(M, nG, K, nGp, Kp, f, p->n_freq, scale, (uint32_t*)Bp, (uint32_t*)Ap);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap tmA, tmB;
+  if (!encode_planes(&tmB, Bp, BF16, Kp, nGp, 2 * NT, why)) return cudaErrorInvalidValue;
+  if (!encode_planes(&tmA, Ap, BF16, Kp, nGp, 2 * NT * p->n_freq, why)) return cudaErrorInvalidValue;
+  const int nK = Kp / BK;
+  const int chain_k = std::max(1, p->chain_pairs / BK);
+  dim3 grid(nGp / BN, nGp / BM, p->n_freq);
+  e = cudaFuncSetAttribute(k_contract_tc<BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  k_contract_tc<BF16, NT><<<grid, THREADS, SMEM_BYTES, s>>>(tmA, tmB, nG, nK, chain_k, p->n_products, inv, chi,
+                                                           p->d_status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contract_tc(chi0_plan_s* p, int nG, const float2* M, int64_t K, const double2* f, double2* chi,
+                               cudaStream_t s, std::string* why) {
+  if (K <= 0) return cudaSuccess;
+  if (!resolve_encoder(why)) return cudaErrorNotSupported;
+  const bool bf16 = p->prec == CHI0_SPLIT_BF16;
+  if (n_terms(p) == 3) {
+    if (bf16) return run_tc<true, 3>(p, nG, M, K, f, chi, s, why);
+    return run_tc<false, 3>(p, nG, M, K, f, chi, s, why);
+  }
+  if (bf16) return run_tc<true, 2>(p, nG, M, K, f, chi, s, why);
+  return run_tc<false, 2>(p, nG, M, K, f, chi, s, why);
 }
 
 }  // namespace chi0

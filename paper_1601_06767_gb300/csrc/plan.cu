@@ -221,8 +221,8 @@ chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* d) {
   if (d->chain_pairs < 0 || d->chain_pairs % 32 != 0)
     return fail(nullptr, CHI0_ERR_INVALID, "chain_pairs must be a non-negative multiple of 32");
   if (d->max_pairs < 0) return fail(nullptr, CHI0_ERR_INVALID, "max_pairs must be >= 0");
-  if (d->n_products != 0 && d->n_products != 3 && d->n_products != 4)
-    return fail(nullptr, CHI0_ERR_INVALID, "n_products must be 0, 3 or 4");
+  if (d->n_products != 0 && d->n_products != 3 && d->n_products != 4 && d->n_products != 6)
+    return fail(nullptr, CHI0_ERR_INVALID, "n_products must be 0, 3, 4 or 6");
   for (int i = 0; i < d->n_q; ++i)
     if (d->n_G[i] < 1 || d->n_G[i] > 65536) return fail(nullptr, CHI0_ERR_INVALID, "n_G must be in [1, 65536]");
   if (env_fault("bad_shape")) return fail(nullptr, CHI0_ERR_INVALID, "injected fault: bad_shape");
@@ -235,12 +235,12 @@ chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* d) {
   p->n1 = d->n1; p->n2 = d->n2; p->n3 = d->n3;
   p->nr = (int64_t)d->n1 * d->n2 * d->n3;
   p->prec = d->precision;
-  p->n_products = d->n_products ? d->n_products : (d->precision == CHI0_SPLIT_FP16 ? 3 : 4);
+  p->n_products = d->n_products ? d->n_products : (d->precision == CHI0_SPLIT_FP16 ? 3 : 6);
   p->delta = d->delta;
   p->n_freq = d->n_freq;
   p->om_re.assign(d->freq_re, d->freq_re + d->n_freq);
   p->om_im.assign(d->freq_im, d->freq_im + d->n_freq);
-  p->chain_pairs = d->chain_pairs ? d->chain_pairs : 128;
+  p->chain_pairs = d->chain_pairs ? d->chain_pairs : 32;
 
   chi0_status st = CHI0_OK;
   auto bail = [&](chi0_status s) {
