@@ -1,0 +1,474 @@
+#!/usr/bin/env python
+"""Benchmark of the chi0 hot path on the 64-atom-MgO-sized workload.
+
+One step = one complete build of chi0_{G,G'}(q, omega) by the full band sum of
+Eq. 1 from plane-wave coefficients resident in HBM: wavefunctions on the 48^3
+grid for 128 valence + 6000 conduction bands, 768,000 pair matrix elements on
+the 2500-vector sphere, FP64 frequency factors for omega = 0 and 8 imaginary
+frequencies, split-precision tcgen05 contraction and FP64 merge into chi0.
+
+Metric: effective TFLOP/s = 8 N_G^2 N_pairs n_omega / build time (the
+algorithmic work of the contraction only).  Inputs (6.6 GB of coefficients and
+grids) exceed L2, so no explicit flush is done between steps.
+
+Legs:
+  --impl ours (default): the CUDA path through the C ABI, plus
+      e2e (host buffers, copies inside the timed region), the accelerated
+      sum of Eq. 3/4 on the same workload, the plain FP64 GPU path timed on a
+      sample of pairs and extrapolated, per-kernel device times (roofline)
+      and the FP64 oracle on host cores (cpu_baseline, rank 0 only).
+  --impl reference: the FP64 oracle on host cores, one bounded sample per step.
+Multi-GPU: N independent replicas (the build of one q-point is one unit of
+work; there is no data-path collective), max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "chi0 build time + effective TFLOP/s, mixed vs FP64 GPU path at ≤1e-6 rel error"
+WORKLOAD = ("64-atom-MgO-sized chi0, full band sum (Eq. 1): N_v=128, N_c=6000, grid 48^3, "
+            "N_G=2500, one q=(0.001,0,0) bohr^-1, omega = 0 + 8 imaginary (0.01-2 Ha), delta=1e-3 Ha")
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas); also exercised by the gloo tests on CPU
+# ---------------------------------------------------------------------------
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def dist_init(backend: str):
+    import torch.distributed as dist
+    rank, world, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29531")
+        dist.init_process_group(backend, rank=rank, world_size=world)
+    return rank, world
+
+
+def barrier(device=None):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        if device is not None and device.type == "cuda":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job throughput: units processed by all ranks / slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"chi0_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def profiled_traffic(kernel_src: str, summary: str):
+    """Per-launch DRAM bytes from a committed ncu summary, or None if the kernel
+    source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(path):
+        return None
+    want = hashlib.sha256(open(os.path.join(ROOT, kernel_src), "rb").read()).hexdigest()[:16]
+    src_hash, traffic = None, None
+    for line in open(path):
+        if line.startswith("source_sha256_16:"):
+            src_hash = line.split(":", 1)[1].strip()
+        if line.startswith("traffic_bytes_per_full_launch:"):
+            traffic = float(line.split(":", 1)[1].strip())
+    return traffic if src_hash == want else None
+
+
+def algorithmic_flops(nG: int, n_pairs: int, n_freq: int) -> float:
+    return 8.0 * nG * nG * n_pairs * n_freq
+
+
+# ---------------------------------------------------------------------------
+# the oracle on host cores (cpu_baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(prob, nv: int, nc: int, seed_offset: int = 0):
+    """Time the FP64 oracle on nv x nc pairs of the workload (wavefunctions,
+    pair elements, factors, contraction).  Returns (seconds, flops, chi, bands)."""
+    import numpy as np
+    from oracle import chi0_from_pairs, freq_factor, pair_elements, wfn_to_grid
+    vb = (np.arange(nv) + seed_offset * nv) % prob.n_v
+    cb = (np.arange(nc) * 37 + seed_offset * 11) % prob.n_c
+    cv, cc = prob.coeff_v(0, vb), prob.coeff_c(cb)
+    t0 = time.perf_counter()
+    uv, uc = wfn_to_grid(cv, prob.gw, prob.n), wfn_to_grid(cc, prob.gw, prob.n)
+    M = pair_elements(uv, uc, prob.gvec[0], prob.n)
+    dE = (prob.E_v[vb][:, None] - prob.E_c[cb][None, :]).reshape(-1)
+    chi = chi0_from_pairs(M, freq_factor(dE, np.ones_like(dE), prob.omega, prob.delta))
+    dt = time.perf_counter() - t0
+    nG = prob.gvec[0].shape[0]
+    return dt, algorithmic_flops(nG, nv * nc, prob.omega.size), chi, (vb, cb, cv, cc)
+
+
+def run_reference(args):
+    from synth import make_problem
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    prob = make_problem("c2")
+    nv, nc = 2, 32
+    for w in range(args.warmup):
+        oracle_sample(prob, nv, nc, w)
+    secs, flops = 0.0, 0.0
+    for k in range(args.steps):
+        dt, fl, _, _ = oracle_sample(prob, nv, nc, args.warmup + k)
+        secs += dt
+        flops += fl
+    value = flops / secs / 1e12
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_per_step": f"{nv}x{nc} pairs"},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{nv} valence x {nc} conduction bands per step (of 128 x 6000)"},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1601_06767_gb300 as pkg
+    from synth import make_problem
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist_init("nccl")
+    prob = make_problem("c2")
+    nG, nf = prob.gvec[0].shape[0], prob.omega.size
+    n_pairs = prob.n_v * prob.n_c
+    F = algorithmic_flops(nG, n_pairs, nf)
+
+    t0 = time.time()
+    cv_h = torch.from_numpy(prob.coeff_v(0)).pin_memory()
+    cc_h = torch.from_numpy(prob.coeff_c()).pin_memory()
+    gen_s = time.time() - t0
+    Ev_h = torch.from_numpy(prob.E_v).pin_memory()
+    Ec_h = torch.from_numpy(prob.E_c).pin_memory()
+    cv, cc = cv_h.to(dev), cc_h.to(dev)
+    Ev, Ec = Ev_h.to(dev), Ec_h.to(dev)
+
+    plan = pkg.Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision=args.precision, gw=prob.gw,
+                        n_products=args.n_products)
+    psi_v = torch.empty((prob.n_v,) + plan.n, dtype=plan.cdtype, device=dev)
+    psi_c = torch.empty((prob.n_c,) + plan.n, dtype=plan.cdtype, device=dev)
+    chi = plan.new_chi(0)
+
+    def step():
+        plan.wfn_to_grid(cv, out=psi_v)
+        plan.wfn_to_grid(cc, out=psi_c)
+        chi.zero_()
+        plan.build(0, psi_v, Ev, psi_c, Ec, chi=chi)
+
+    for _ in range(args.warmup):
+        step()
+    plan.sync_status()
+    torch.cuda.synchronize()
+    plan.profile(True)
+    plan.profile_reset()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(dev)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            step()
+        ev1.record()
+        torch.cuda.synchronize()
+    barrier(dev)
+    ms_step = ev0.elapsed_time(ev1) / args.steps
+    plan.sync_status()
+    prof = plan.profile_read()
+    plan.profile(False)
+    secs_max = max_over_ranks(ms_step / 1e3, dev)
+    value = replica_value(F, world, secs_max) / 1e12
+    launches = sum(c for _, c in prof.values())
+
+    # ---- e2e: host buffers, copies inside the timed region ----
+    chi_h = torch.empty(chi.shape, dtype=chi.dtype).pin_memory()
+
+    def step_e2e():
+        cv.copy_(cv_h, non_blocking=True)
+        cc.copy_(cc_h, non_blocking=True)
+        Ev.copy_(Ev_h, non_blocking=True)
+        Ec.copy_(Ec_h, non_blocking=True)
+        step()
+        chi_h.copy_(chi, non_blocking=True)
+
+    step_e2e()
+    torch.cuda.synchronize()
+    barrier(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_e2e = max(1, min(args.steps, 3))
+    e0.record()
+    for _ in range(n_e2e):
+        step_e2e()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(e0.elapsed_time(e1) / n_e2e / 1e3, dev)
+    h2d = cv_h.nbytes + cc_h.nbytes + Ev_h.nbytes + Ec_h.nbytes
+    d2h = chi_h.nbytes
+
+    # ---- accelerated sum (Eq. 3/4) on the same workload ----
+    c_sel, E_sel, w_sel = pkg.select_accelerated(prob.E_c, prob.N0, prob.dE, prob.dos_A, prob.dos_V0, prob.E_max)
+    c_idx = torch.from_numpy(c_sel).to(dev)
+    Ecol, wcol = torch.from_numpy(E_sel).to(dev), torch.from_numpy(w_sel).to(dev)
+    chi_a = plan.new_chi(0)
+
+    def step_acc():
+        plan.wfn_to_grid(cv, out=psi_v)
+        plan.wfn_to_grid(cc, out=psi_c)
+        chi_a.zero_()
+        plan.build(0, psi_v, Ev, psi_c, Ecol, w_col=wcol, c_idx=c_idx, chi=chi_a)
+
+    step_acc()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(3):
+        step_acc()
+    e1.record()
+    torch.cuda.synchronize()
+    acc_ms = e0.elapsed_time(e1) / 3
+    plan.sync_status()
+    acc_pairs = prob.n_v * len(c_sel)
+    del chi_a
+
+    # ---- plain FP64 GPU path on a sample of conduction bands, extrapolated ----
+    fp64 = None
+    if not args.no_fp64:
+        plan64 = pkg.Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision="fp64", gw=prob.gw)
+        nc_s = args.fp64_sample
+        idx = torch.arange(nc_s, dtype=torch.int32, device=dev)
+        psi_v64 = plan64.wfn_to_grid(cv)
+        psi_c64 = plan64.wfn_to_grid(cc[:nc_s].contiguous())
+        chi64 = plan64.new_chi(0)
+        plan64.build(0, psi_v64, Ev, psi_c64, Ec[:nc_s].contiguous(), c_idx=idx, chi=chi64)
+        torch.cuda.synchronize()
+        e0.record()
+        plan64.wfn_to_grid(cc[:nc_s].contiguous(), out=psi_c64)
+        chi64.zero_()
+        plan64.build(0, psi_v64, Ev, psi_c64, Ec[:nc_s].contiguous(), c_idx=idx, chi=chi64)
+        e1.record()
+        torch.cuda.synchronize()
+        plan64.sync_status()
+        s_ms = e0.elapsed_time(e1)
+        wfn_v0, wfn_v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        wfn_v0.record()
+        plan64.wfn_to_grid(cv, out=psi_v64)
+        wfn_v1.record()
+        torch.cuda.synchronize()
+        full_s = (s_ms * prob.n_c / nc_s + wfn_v0.elapsed_time(wfn_v1)) / 1e3
+        fp64 = {"build_s_extrapolated": full_s, "value_tflops": F / full_s / 1e12,
+                "sample": f"all 128 valence x {nc_s} conduction bands timed, scaled linearly to 6000 "
+                          "(cost is linear in the pair count)",
+                "mixed_speedup": full_s / (ms_step / 1e3)}
+        del plan64, psi_v64, psi_c64, chi64
+
+    # ---- roofline of the dominant kernel (tensor-core contraction) ----
+    pk, pk_kind = peaks()
+    n_prod = {"fp16": 3, "bf16": 6}[args.precision] if args.n_products == 0 else args.n_products
+    tc_ms, tc_n = prof["contract_tc"]
+    # every launch contracts one block of pairs; summed over the timed steps this is
+    # (tensor flops per launch x launches) / (average launch time x launches)
+    tensor_flops_total = n_prod * F * args.steps
+    avg_launch_s = tc_ms / 1e3 / max(tc_n, 1)
+    tensor_flops_launch = tensor_flops_total / max(tc_n, 1)
+    ach = tensor_flops_launch / avg_launch_s / 1e12
+    peak = pk.get("bf16_tflops_sustained", 1700.0)
+    traffic = profiled_traffic("paper_1601_06767_gb300/csrc/kern_tc.cu", f"contract_tc_c2_{args.precision}.md")
+    roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": traffic, "kernel": "k_contract_tc", "peak_source": f"{pk_kind} bf16_tflops_sustained",
+            "flops_per_launch": tensor_flops_launch, "launches": tc_n,
+            "algorithmic_tflops": ach / n_prod}
+    kernel_ms = {k: round(v[0] / args.steps, 3) for k, v in prof.items()}
+
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pairs": n_pairs, "n_freq": nf,
+                       "precision": f"{args.precision} split x{n_prod} products, FP32 TMEM chains of "
+                                    f"32 pairs, FP64 factors and merge",
+                       "l2": "no flush: resident inputs (6.6 GB) exceed the 129 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "kernel_ms_per_step": kernel_ms, "gpu_launches": launches,
+            "e2e": {"value": replica_value(F, world, e2e_s) / 1e12, "unit": "TFLOP/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
+            "accelerated": {"ms": acc_ms, "pairs": acc_pairs, "columns": len(c_sel),
+                            "pair_ratio": n_pairs / acc_pairs, "speedup_vs_full": ms_step / acc_ms,
+                            "N0": prob.N0, "dE_eV": 2.0},
+            "fp64_gpu": fp64, "clocks": clk.summary(), "input_gen_s": gen_s}
+
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(prob, plan, psi_v, psi_c, Ev, Ec)
+    del plan
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def cpu_baseline(prob, plan, psi_v, psi_c, Ev, Ec):
+    """The oracle on host cores on a bounded sample (8 x 64 pairs), plus the
+    GPU result on the same sample for a parity figure."""
+    import numpy as np
+    import torch
+    from oracle import rel_fro
+    nv, nc = 8, 64
+    dt, fl, chi_ref, (vb, cb, cv, cc) = oracle_sample(prob, nv, nc)
+    dev = psi_v.device
+    vi = torch.from_numpy(vb.astype(np.int32)).to(dev)
+    ci = torch.from_numpy(cb.astype(np.int32)).to(dev)
+    M = plan.pairs(0, psi_v, psi_c, v_idx=vi, c_idx=ci)
+    chi = plan.accumulate(0, M, nv, nc, Ev[vi.long()].contiguous(), Ec[ci.long()].contiguous())
+    torch.cuda.synchronize()
+    err = max(rel_fro(chi[i].cpu().numpy(), chi_ref[i]) for i in range(chi.shape[0]))
+    return {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{nv} valence x {nc} conduction bands ({nv * nc} of 768000 pairs), all 9 frequencies",
+            "seconds": dt, "parity_rel_fro_max_over_omega": err}
+
+
+def run_case(args):
+    """Small fixed cases for ncu captures (no JSON line): 'contract' = two
+    accumulate calls of 8192 pairs on the 2500-vector sphere with 9
+    frequencies; 'pairs' = two pair-element calls of 128 x 64 pairs on 48^3."""
+    import torch
+    import paper_1601_06767_gb300 as pkg
+    from synth import make_problem
+    prob = make_problem("c2")
+    nG = prob.gvec[0].shape[0]
+    K, nv, nc = 8192, 128, 64
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    with pkg.Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision=args.precision, max_pairs=K,
+                      gw=prob.gw, n_products=args.n_products) as plan:
+        M = torch.randn(K, nG, dtype=torch.complex64, device="cuda", generator=g) * 4e-3
+        if args.case == "contract":
+            Ev = torch.tensor(prob.E_v[:nv], device="cuda")
+            Ec = torch.tensor(prob.E_c[:nc], device="cuda")
+            chi = plan.new_chi(0)
+            for _ in range(2):
+                plan.accumulate(0, M, nv, nc, Ev, Ec, chi=chi)
+        else:
+            psi_v = torch.randn(nv, *plan.n, dtype=torch.complex64, device="cuda", generator=g)
+            psi_c = torch.randn(nc, *plan.n, dtype=torch.complex64, device="cuda", generator=g)
+            for _ in range(2):
+                plan.pairs(0, psi_v, psi_c, out=M)
+        plan.sync_status()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["bf16", "fp16"], default="bf16")
+    ap.add_argument("--n-products", type=int, default=0)
+    ap.add_argument("--fp64-sample", type=int, default=32)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--case", choices=["contract", "pairs"], default=None,
+                    help="run a small fixed case for profiling instead of the benchmark")
+    args = ap.parse_args(argv)
+    if args.case:
+        return run_case(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -136,6 +136,28 @@ chi0_status chi0_build(chi0_plan plan, int iq, const void* psi_v, int n_v, const
                        const void* psi_c, const int32_t* c_idx, int n_c,
                        const double* E_col, const double* w_col, void* chi0, void* stream);
 
+/* Kernel families counted and timed by the plan's instrumentation. */
+typedef enum {
+  CHI0_K_WFN = 0,        /* wavefunctions on the grid */
+  CHI0_K_PAIR_PLANES,    /* pair products + transforms along i3, i2 */
+  CHI0_K_PAIR_GATHER,    /* transform along i1 on the G sphere */
+  CHI0_K_WEIGHTS,        /* FP64 frequency factors */
+  CHI0_K_PACK,           /* operand scaling + 16-bit split (split plans) */
+  CHI0_K_CONTRACT_TC,    /* tcgen05 contraction + FP64 merge (split plans) */
+  CHI0_K_CONTRACT_F64,   /* DFMA contraction (FP64 plans) */
+  CHI0_K_COUNT
+} chi0_kernel;
+
+/* Instrumentation (not part of the method).  With timing enabled, every
+ * launch of a family is bracketed by CUDA events recorded on the launching
+ * stream.  chi0_profile_read synchronises the recorded events and returns,
+ * per family, the summed device time (ms, may be NULL) and the number of
+ * kernel launches since the last reset (launches are always counted).
+ * total_ms and launches are (host) arrays of CHI0_K_COUNT entries. */
+chi0_status chi0_profile_enable(chi0_plan plan, int timing_on);
+chi0_status chi0_profile_reset(chi0_plan plan);
+chi0_status chi0_profile_read(chi0_plan plan, double* total_ms, int64_t* launches);
+
 /* Band selection of Eq. 3 / Eq. 4 (host arrays, host computation).
  * E_c (host) [n_c] sorted ascending.  Columns 0..N0-1 are bands 0..N0-1 with
  * their own energy and weight 1.  E_0 = E_c[N0-1]; the interval (E_0, E_max]

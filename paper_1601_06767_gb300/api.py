@@ -100,6 +100,20 @@ class Chi0Plan:
             raise ValueError(f"{name} must be a contiguous {dtype} tensor on {self.device}")
         return t
 
+    # -- instrumentation -------------------------------------------------
+    def profile(self, timing: bool = True):
+        self._check(L.lib().chi0_profile_enable(self._h, int(timing)))
+
+    def profile_reset(self):
+        self._check(L.lib().chi0_profile_reset(self._h))
+
+    def profile_read(self) -> dict:
+        n = len(L.KERNELS)
+        ms = np.zeros(n, np.float64)
+        cnt = np.zeros(n, np.int64)
+        self._check(L.lib().chi0_profile_read(self._h, ms.ctypes.data, cnt.ctypes.data))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(L.KERNELS)}
+
     # -- entry points ----------------------------------------------------
     def sync_status(self):
         self._check(L.lib().chi0_sync_status(self._h, _stream()))

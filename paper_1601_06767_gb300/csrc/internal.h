@@ -70,11 +70,27 @@ struct chi0_plan_s {
   size_t ws_bytes = 0;
   std::string err;
   bool tc_ready = false;     // tensor-map encoder resolved
+  // instrumentation
+  bool prof_timing = false;
+  int64_t prof_launches[CHI0_K_COUNT] = {};
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events[CHI0_K_COUNT];
+  std::vector<cudaEvent_t> prof_pool;
 };
 
 namespace chi0 {
 
 bool is_split(const chi0_plan_s* p);
+
+// Brackets the launches of one kernel family: counts them and, when timing
+// is on, records events on the stream before and after.
+struct ProfScope {
+  chi0_plan_s* p;
+  int k;
+  cudaStream_t s;
+  cudaEvent_t e1 = nullptr;
+  ProfScope(chi0_plan_s* plan, int kernel, cudaStream_t st, int launches);
+  ~ProfScope();
+};
 size_t cbytes(const chi0_plan_s* p);   // bytes of one complex element of psi / M
 
 // ---- kernels (launchers return cudaGetLastError()) ----

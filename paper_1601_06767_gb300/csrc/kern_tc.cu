@@ -440,17 +440,21 @@ cudaError_t run_tc(chi0_plan_s* p, int nG, const float2* M, int64_t K, const dou
   unsigned int* amax = reinterpret_cast<unsigned int*>(tail);                     // [1 + n_freq]
   float* scale = reinterpret_cast<float*>(tail + 8 * (size_t)(p->n_freq + 1));   // [1 + n_freq]
   double* inv = reinterpret_cast<double*>(tail + 16 * (size_t)(p->n_freq + 1));              // [n_freq]
-  cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(unsigned int) * (p->n_freq + 1), s);
-  if (e != cudaSuccess) return e;
-  k_absmax<<<2 * 152, 256, 0, s>>>(M, K * nG, f, K, p->n_freq, amax);
-  k_scales<<<1, 128, 0, s>>>(amax, p->n_freq, scale, inv);
-  dim3 gpk(nGp / 32, Kp / 64);
-  const size_t smp = (size_t)(64 * 33 + 64 * p->n_freq) * sizeof(float2);
-  e = cudaFuncSetAttribute(k_pack<BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
-  if (e != cudaSuccess) return e;
-  k_pack<BF16, NT><<<gpk, 256, smp, s>>>(M, nG, K, nGp, Kp, f, p->n_freq, scale, (uint32_t*)Bp, (uint32_t*)Ap);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  {
+    ProfScope ps(p, CHI0_K_PACK, s, 3);
+    e = cudaMemsetAsync(amax, 0, sizeof(unsigned int) * (p->n_freq + 1), s);
+    if (e != cudaSuccess) return e;
+    k_absmax<<<2 * 152, 256, 0, s>>>(M, K * nG, f, K, p->n_freq, amax);
+    k_scales<<<1, 128, 0, s>>>(amax, p->n_freq, scale, inv);
+    dim3 gpk(nGp / 32, Kp / 64);
+    const size_t smp = (size_t)(64 * 33 + 64 * p->n_freq) * sizeof(float2);
+    e = cudaFuncSetAttribute(k_pack<BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+    if (e != cudaSuccess) return e;
+    k_pack<BF16, NT><<<gpk, 256, smp, s>>>(M, nG, K, nGp, Kp, f, p->n_freq, scale, (uint32_t*)Bp, (uint32_t*)Ap);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   CUtensorMap tmA, tmB;
   if (!encode_planes(&tmB, Bp, BF16, Kp, nGp, 2 * NT, why)) return cudaErrorInvalidValue;
   if (!encode_planes(&tmA, Ap, BF16, Kp, nGp, 2 * NT * p->n_freq, why)) return cudaErrorInvalidValue;
@@ -459,6 +463,7 @@ cudaError_t run_tc(chi0_plan_s* p, int nG, const float2* M, int64_t K, const dou
   dim3 grid(nGp / BN, nGp / BM, p->n_freq);
   e = cudaFuncSetAttribute(k_contract_tc<BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
   if (e != cudaSuccess) return e;
+  ProfScope ps(p, CHI0_K_CONTRACT_TC, s, 1);
   k_contract_tc<BF16, NT><<<grid, THREADS, SMEM_BYTES, s>>>(tmA, tmB, nG, nK, chain_k, p->n_products, inv, chi,
                                                            p->d_status);
   return cudaGetLastError();

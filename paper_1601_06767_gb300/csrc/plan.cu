@@ -91,6 +91,9 @@ void free_sphere(SphereQ& s) {
 }
 
 void free_plan(chi0_plan_s* p) {
+  for (auto& v : p->prof_events)
+    for (auto& e : v) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+  for (auto e : p->prof_pool) cudaEventDestroy(e);
   for (auto& s : p->q) free_sphere(s);
   chi0::WfnSphere& w = p->w;
   cudaFree(w.col_start); cudaFree(w.col_pw); cudaFree(w.col_g1);
@@ -194,6 +197,40 @@ chi0_status check_plan(chi0_plan_s* p) {
 }  // namespace
 
 namespace chi0 {
+
+static cudaEvent_t pool_get(chi0_plan_s* p) {
+  if (!p->prof_pool.empty()) {
+    cudaEvent_t e = p->prof_pool.back();
+    p->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+ProfScope::ProfScope(chi0_plan_s* plan, int kernel, cudaStream_t st, int launches) : p(plan), k(kernel), s(st) {
+  p->prof_launches[k] += launches;
+  if (p->prof_timing) {
+    e1 = pool_get(p);
+    if (e1) cudaEventRecord(e1, s);
+  }
+}
+
+ProfScope::~ProfScope() {
+  if (!e1) return;
+  cudaEvent_t e2 = pool_get(p);
+  if (!e2) {
+    p->prof_pool.push_back(e1);
+    return;
+  }
+  cudaEventRecord(e2, s);
+  p->prof_events[k].emplace_back(e1, e2);
+}
+
 bool is_split(const chi0_plan_s* p) { return p->prec != CHI0_FP64; }
 size_t cbytes(const chi0_plan_s* p) { return is_split(p) ? sizeof(float2) : sizeof(double2); }
 }  // namespace chi0
@@ -330,6 +367,7 @@ chi0_status chi0_wfn_to_grid(chi0_plan p, const void* coeff, int nb, void* psi, 
   if (p->w.npw <= 0) return fail(p, CHI0_ERR_INVALID, "the plan has no wavefunction sphere");
   if (nb < 0 || (nb > 0 && (!coeff || !psi))) return fail(p, CHI0_ERR_INVALID, "bad band count or NULL buffer");
   if (nb == 0) return CHI0_OK;
+  chi0::ProfScope ps(p, CHI0_K_WFN, (cudaStream_t)stream, 1);
   CK(p, chi0::launch_wfn_to_grid(p, (const double2*)coeff, nb, psi, (cudaStream_t)stream));
   return CHI0_OK;
 }
@@ -346,8 +384,14 @@ static chi0_status pairs_impl(chi0_plan p, int iq, const void* psi_v, const int3
     int nv = std::min(vchunk, n_v - v0);
     for (int c0 = 0; c0 < n_c; c0 += cchunk) {
       int nc = std::min(cchunk, n_c - c0);
-      CK(p, chi0::launch_pair_planes(p, iq, psi_v, v_idx, v0, nv, psi_c, c_idx, c_base + c0, nc, p->d_D, s));
-      CK(p, chi0::launch_pair_gather(p, iq, p->d_D, nv, nc, (int64_t)v0 * ld_pairs_c + c0, ld_pairs_c, M, s));
+      {
+        chi0::ProfScope ps(p, CHI0_K_PAIR_PLANES, s, 1);
+        CK(p, chi0::launch_pair_planes(p, iq, psi_v, v_idx, v0, nv, psi_c, c_idx, c_base + c0, nc, p->d_D, s));
+      }
+      {
+        chi0::ProfScope ps(p, CHI0_K_PAIR_GATHER, s, 1);
+        CK(p, chi0::launch_pair_gather(p, iq, p->d_D, nv, nc, (int64_t)v0 * ld_pairs_c + c0, ld_pairs_c, M, s));
+      }
     }
   }
   return CHI0_OK;
@@ -371,7 +415,10 @@ static chi0_status accumulate_impl(chi0_plan p, int iq, const void* M, int n_v, 
   const int64_t np = (int64_t)n_v * n_c;
   for (int64_t p0 = 0; p0 < np; p0 += p->max_pairs) {
     int64_t K = std::min<int64_t>(p->max_pairs, np - p0);
-    CK(p, chi0::launch_weights(p, p0, K, n_c, E_v, E_col, w_col, p->d_f, s));
+    {
+      chi0::ProfScope ps(p, CHI0_K_WEIGHTS, s, 1);
+      CK(p, chi0::launch_weights(p, p0, K, n_c, E_v, E_col, w_col, p->d_f, s));
+    }
     if (chi0::is_split(p)) {
       std::string why;
       cudaError_t e = chi0::launch_contract_tc(p, nG, (const float2*)M + p0 * nG, K, p->d_f,
@@ -379,6 +426,7 @@ static chi0_status accumulate_impl(chi0_plan p, int iq, const void* M, int n_v, 
       if (e != cudaSuccess)
         return fail(p, CHI0_ERR_CUDA, "tensor-core contraction: " + why + " " + cudaGetErrorString(e));
     } else {
+      chi0::ProfScope ps(p, CHI0_K_CONTRACT_F64, s, 1);
       CK(p, chi0::launch_contract_f64(p, nG, (const double2*)M + p0 * nG, K, p->d_f, (double2*)chi, s));
     }
   }
@@ -415,6 +463,43 @@ chi0_status chi0_build(chi0_plan p, int iq, const void* psi_v, int n_v, const do
     if (st != CHI0_OK) return st;
     st = accumulate_impl(p, iq, p->d_M, n_v, nc, E_v, E_col + c0, w_col ? w_col + c0 : nullptr, chi0, s);
     if (st != CHI0_OK) return st;
+  }
+  return CHI0_OK;
+}
+
+chi0_status chi0_profile_enable(chi0_plan p, int timing_on) {
+  if (!p) return CHI0_ERR_INVALID;
+  p->prof_timing = timing_on != 0;
+  return CHI0_OK;
+}
+
+chi0_status chi0_profile_reset(chi0_plan p) {
+  if (!p) return CHI0_ERR_INVALID;
+  for (int k = 0; k < CHI0_K_COUNT; ++k) {
+    for (auto& e : p->prof_events[k]) {
+      cudaEventSynchronize(e.second);
+      p->prof_pool.push_back(e.first);
+      p->prof_pool.push_back(e.second);
+    }
+    p->prof_events[k].clear();
+    p->prof_launches[k] = 0;
+  }
+  return CHI0_OK;
+}
+
+chi0_status chi0_profile_read(chi0_plan p, double* total_ms, int64_t* launches) {
+  if (!p) return CHI0_ERR_INVALID;
+  for (int k = 0; k < CHI0_K_COUNT; ++k) {
+    double t = 0.0;
+    for (auto& e : p->prof_events[k]) {
+      if (cudaEventSynchronize(e.second) != cudaSuccess)
+        return fail(p, CHI0_ERR_CUDA, "profiling event failed");
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) t += ms;
+      cudaGetLastError();
+    }
+    if (total_ms) total_ms[k] = t;
+    if (launches) launches[k] = p->prof_launches[k];
   }
   return CHI0_OK;
 }
