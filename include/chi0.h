@@ -158,6 +158,32 @@ chi0_status chi0_profile_enable(chi0_plan plan, int timing_on);
 chi0_status chi0_profile_reset(chi0_plan plan);
 chi0_status chi0_profile_read(chi0_plan plan, double* total_ms, int64_t* launches);
 
+/* Allocation-free FP64 accumulate.  The paper has no counterpart: this entry
+ * exists for callers that cannot allocate device memory when they need chi0
+ * (code embedded in a framework that owns all device memory through its own
+ * pool, or a loop that must not risk the device-wide synchronisation and
+ * out-of-memory failures of cudaMalloc).  It needs no plan and allocates
+ * nothing; it computes what chi0_accumulate computes for a CHI0_FP64 plan:
+ *   chi0[w][G][G'] += sum_p f_p(w) M[p][G] conj(M[p][G']),  p = iv*n_c + ic,
+ * with f_p, E_v, E_col and w_col as for chi0_accumulate (w_col may be NULL).
+ * M: (device) [n_v*n_c][n_G] complex128; E_v (device) [n_v]; E_col, w_col
+ * (device) [n_c]; freq_re, freq_im (host) [n_freq], copied into the launch;
+ * chi0: (device) [n_freq][n_G][n_G] complex128, accumulated in place.
+ * Limits: 1 <= n_freq <= 64 and 1 <= n_G <= 65536, otherwise CHI0_ERR_INVALID
+ * with the reason in chi0_last_error(NULL).  Any number of pairs is accepted.
+ * Scratch: a fixed 4 MiB array of FP64 frequency factors in the library's
+ * device image, held by every device that loads the library until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (with the device current) and should come before any stream capture.  All
+ * calls share the array and it keeps the last call's contents; every entry a
+ * call reads is written earlier in the same call, so nothing needs clearing,
+ * but calls whose work can overlap on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller. */
+chi0_status chi0_accumulate_fp64_noalloc(int n_G, const void* M, int n_v, int n_c, const double* E_v,
+                                         const double* E_col, const double* w_col, int n_freq,
+                                         const double* freq_re, const double* freq_im, double delta,
+                                         void* chi0, void* stream);
+
 /* Band selection of Eq. 3 / Eq. 4 (host arrays, host computation).
  * E_c (host) [n_c] sorted ascending.  Columns 0..N0-1 are bands 0..N0-1 with
  * their own energy and weight 1.  E_0 = E_c[N0-1]; the interval (E_0, E_max]

@@ -80,6 +80,8 @@ struct chi0_plan_s {
 namespace chi0 {
 
 bool is_split(const chi0_plan_s* p);
+// record the text returned by chi0_last_error(NULL) on this thread
+void set_global_error(const std::string& msg);
 
 // Brackets the launches of one kernel family: counts them and, when timing
 // is on, records events on the stream before and after.

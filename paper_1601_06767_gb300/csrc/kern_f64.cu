@@ -1,6 +1,9 @@
 // Frequency factors of Eq. 1 (FP64) and the plain FP64 contraction
 //   chi0[w][G][G'] += sum_p f_p(w) M_p(G) conj(M_p(G'))
 // on the CUDA cores (DFMA), used by CHI0_FP64 plans.
+#include <mutex>
+#include <string>
+
 #include "cplx.cuh"
 #include "internal.h"
 
@@ -117,3 +120,114 @@ cudaError_t launch_contract_f64(const chi0_plan_s* p, int nG, const double2* M, 
 }
 
 }  // namespace chi0
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the FP64 accumulate (no counterpart in the paper).
+//
+// Some callers cannot allocate device memory at the point where they need
+// chi0: for example code running inside another framework that has reserved
+// all device memory for its own pool, or a latency-critical loop in which a
+// cudaMalloc (which may synchronise the device and can fail under memory
+// pressure) is not acceptable.  A plan allocates its workspace, so those
+// callers cannot use chi0_accumulate.  This variant needs no plan: the only
+// scratch it uses (the FP64 frequency factors of one block of pairs) lives in
+// the fixed array below, which every device that loads the library holds
+// until the process exits.
+// ---------------------------------------------------------------------------
+namespace chi0 {
+namespace {
+
+constexpr int kNoAllocMaxFreq = 64;                       // frequencies per call
+constexpr int64_t kNoAllocFactors = (int64_t)1 << 18;     // double2 entries: 4 MiB
+static __device__ __align__(256) double2 g_noalloc_factors[kNoAllocFactors];
+
+struct FreqList {
+  double2 om[kNoAllocMaxFreq];
+};
+
+// f[w][k] as k_weights, with the frequencies passed by value
+__global__ void k_weights_noalloc(int64_t p0, int64_t K, int n_c, const double* __restrict__ E_v,
+                                  const double* __restrict__ E_col, const double* __restrict__ w_col, FreqList fl,
+                                  int n_freq, double delta, double2* __restrict__ f) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  const int64_t p = p0 + k;
+  const int64_t iv = p / n_c, ic = p - iv * n_c;
+  const double dE = E_v[iv] - E_col[ic];
+  const double w = w_col ? w_col[ic] : 1.0;
+  for (int iw = 0; iw < n_freq; ++iw) {
+    const double2 om = fl.om[iw];
+    const double2 a = cinv(dE - om.x, delta - om.y);
+    const double2 b = cinv(dE + om.x, delta + om.y);
+    f[(int64_t)iw * K + k] = make_double2(0.5 * w * (a.x + b.x), 0.5 * w * (a.y + b.y));
+  }
+}
+
+std::mutex g_noalloc_mu;
+constexpr int kNoAllocMaxDevices = 64;
+double2* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+}  // namespace
+}  // namespace chi0
+
+extern "C" chi0_status chi0_accumulate_fp64_noalloc(int n_G, const void* M, int n_v, int n_c, const double* E_v,
+                                                    const double* E_col, const double* w_col, int n_freq,
+                                                    const double* freq_re, const double* freq_im, double delta,
+                                                    void* chi0, void* stream) {
+  using namespace chi0;
+  auto bad = [](const std::string& m) {
+    set_global_error("chi0_accumulate_fp64_noalloc: " + m);
+    return CHI0_ERR_INVALID;
+  };
+  if (n_G < 1 || n_G > 65536) return bad("n_G must be in [1, 65536]");
+  if (n_freq < 1 || n_freq > kNoAllocMaxFreq)
+    return bad("n_freq = " + std::to_string(n_freq) + " is outside [1, " + std::to_string(kNoAllocMaxFreq) +
+               "], the fixed limit of this allocation-free path");
+  if (n_v < 0 || n_c < 0) return bad("negative band count");
+  if (!freq_re || !freq_im) return bad("NULL frequency array");
+  if ((int64_t)n_v * n_c == 0) return CHI0_OK;
+  if (!M || !E_v || !E_col || !chi0) return bad("NULL buffer");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_global_error("chi0_accumulate_fp64_noalloc: no usable current device");
+    return CHI0_ERR_CUDA;
+  }
+  double2* scratch = nullptr;
+  {
+    // set-up, once per device, with that device current: the host-side name of
+    // the array is only a stand-in, so look up its device address
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      e = cudaGetSymbolAddress((void**)&g_noalloc_ptr[dev], g_noalloc_factors);
+      if (e != cudaSuccess) {
+        g_noalloc_ptr[dev] = nullptr;
+        set_global_error(std::string("chi0_accumulate_fp64_noalloc: cudaGetSymbolAddress: ") +
+                         cudaGetErrorString(e));
+        cudaGetLastError();
+        return CHI0_ERR_CUDA;
+      }
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  FreqList fl;
+  for (int i = 0; i < kNoAllocMaxFreq; ++i) fl.om[i] = make_double2(i < n_freq ? freq_re[i] : 0.0, i < n_freq ? freq_im[i] : 0.0);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t np = (int64_t)n_v * n_c;
+  const int64_t chunk = kNoAllocFactors / n_freq;   // pairs whose factors fit the array
+  const int t = (n_G + kT - 1) / kT;
+  for (int64_t p0 = 0; p0 < np; p0 += chunk) {
+    const int64_t K = std::min<int64_t>(chunk, np - p0);
+    // every factor the contraction reads is written first: nothing needs clearing
+    k_weights_noalloc<<<(unsigned)((K + 255) / 256), 256, 0, s>>>(p0, K, n_c, E_v, E_col, w_col, fl, n_freq, delta,
+                                                                 scratch);
+    k_contract_f64<<<dim3(t, t, n_freq), 256, 0, s>>>(n_G, (const double2*)M + p0 * n_G, K, scratch,
+                                                     (double2*)chi0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_global_error(std::string("chi0_accumulate_fp64_noalloc: launch: ") + cudaGetErrorString(e));
+      return CHI0_ERR_CUDA;
+    }
+  }
+  return CHI0_OK;
+}

@@ -232,6 +232,7 @@ ProfScope::~ProfScope() {
 }
 
 bool is_split(const chi0_plan_s* p) { return p->prec != CHI0_FP64; }
+void set_global_error(const std::string& msg) { g_create_err = msg; }
 size_t cbytes(const chi0_plan_s* p) { return is_split(p) ? sizeof(float2) : sizeof(double2); }
 }  // namespace chi0
 
