@@ -201,6 +201,236 @@ k_pair_gather(const typename Cx<R>::T* __restrict__ D, int nc, int64_t row0, int
   }
 }
 
+// ---------------------------------------------------------------------------
+// Stages 1+2 with register FFTs, for cubic grids n = P*Q with Q a power of two.
+// The frequency shift to the lowest kept k (k2min, k3min) is folded into the
+// valence planes when they are loaded:  u_v'(i2,i3) = u_v(i2,i3) e^{-2 pi i (k3min i3 + k2min i2)/n},
+// so each line transform only needs its first nk outputs:
+//   sum_i x(i) e^{2 pi i kk i/n} = sum_{a<P} e^{2 pi i a kk/n} F_a(kk mod Q),
+//   F_a(m) = sum_{b<Q} x(a + P b) e^{2 pi i b m/Q}   (Q-point FFT in registers).
+// Shared memory: Uv'[TV][n][ld], Uc[NCB][n][ld], X[NCB][TV][n][ldx], tables.
+// ---------------------------------------------------------------------------
+constexpr int NKMAX = 32;
+
+__device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <int Q>
+__host__ __device__ constexpr int bitrev(int i) {
+  int r = 0;
+  for (int b = 1; b < Q; b <<= 1) {
+    r = (r << 1) | (i & 1);
+    i >>= 1;
+  }
+  return r;
+}
+
+// in-place Q-point transform with e^{+2 pi i/Q}; tw[j] = e^{2 pi i j/Q}, j < Q/2
+template <int Q>
+__device__ __forceinline__ void fft_reg(float2 (&x)[Q], const float2* __restrict__ tw) {
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int j = bitrev<Q>(i);
+    if (j > i) {
+      const float2 t = x[i];
+      x[i] = x[j];
+      x[j] = t;
+    }
+  }
+#pragma unroll
+  for (int len = 2; len <= Q; len <<= 1) {
+#pragma unroll
+    for (int i = 0; i < Q; i += len) {
+#pragma unroll
+      for (int k = 0; k < len / 2; ++k) {
+        const float2 u = x[i + k];
+        float2 v = x[i + k + len / 2];
+        const int e = k * (Q / len);
+        if (e == 0) {
+        } else if (4 * e == Q) {           // multiply by i
+          v = make_float2(-v.y, v.x);
+        } else {
+          v = cmul(v, tw[e]);
+        }
+        x[i + k] = make_float2(u.x + v.x, u.y + v.y);
+        x[i + k + len / 2] = make_float2(u.x - v.x, u.y - v.y);
+      }
+    }
+  }
+}
+
+// acc[kk] (+)= sum over the P sub-sequences of one length-n line read through `ld`
+template <int P, int Q, typename Load>
+__device__ __forceinline__ void line_transform(Load load, int nk, const float2* __restrict__ ow,
+                                               const float2* __restrict__ tw, float2 (&acc)[NKMAX]) {
+#pragma unroll
+  for (int kk = 0; kk < NKMAX; ++kk) acc[kk] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int a = 0; a < P; ++a) {
+    float2 x[Q];
+#pragma unroll
+    for (int b = 0; b < Q; ++b) x[b] = load(a + P * b);
+    fft_reg<Q>(x, tw);
+#pragma unroll
+    for (int kk = 0; kk < NKMAX; ++kk) {
+      if (kk < nk) {
+        if (a == 0) {
+          acc[kk].x += x[kk % Q].x;
+          acc[kk].y += x[kk % Q].y;
+        } else {
+          cfma(acc[kk], x[kk % Q], ow[a * NKMAX + kk]);
+        }
+      }
+    }
+  }
+}
+
+template <int P, int Q, int TV, int NCB>
+__global__ void __launch_bounds__(192)
+k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ v_idx, int v0, int nv,
+                  const float2* __restrict__ psi_c, const int32_t* __restrict__ c_idx, int c0, int nc, int c_per_cta,
+                  int nk2, int nk3, int nk2p, int nk3p, const float2* __restrict__ T2, const float2* __restrict__ T3,
+                  float2* __restrict__ D) {
+  constexpr int n = P * Q;
+  constexpr int ld = n | 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* Uv = reinterpret_cast<float2*>(smem_raw);          // [TV][n][ld]
+  float2* Uc = Uv + TV * n * ld;                             // [NCB][n][ld]
+  const int ldx = nk3 | 1;
+  float2* X = Uc + NCB * n * ld;                             // [NCB][TV][n][ldx]
+  float2* ow = X + NCB * TV * n * ldx;                       // [P][NKMAX] e^{2 pi i a kk/n}
+  float2* tw = ow + P * NKMAX;                               // [Q/2]      e^{2 pi i j/Q}
+  const int i1 = blockIdx.x;
+  const int jv0 = blockIdx.y * TV;
+  const int jc_begin = blockIdx.z * c_per_cta;
+  const int jc_end = min(nc, jc_begin + c_per_cta);
+  constexpr int64_t nr = (int64_t)n * n * n;
+  constexpr int plane = n * n;
+  const int64_t box = (int64_t)nk2 * nk3;
+
+  for (int e = threadIdx.x; e < P * NKMAX; e += blockDim.x) {
+    const int a = e / NKMAX, kk = e - a * NKMAX;
+    double sn, cs;
+    sincospi(2.0 * (double)((a * kk) % n) / (double)n, &sn, &cs);
+    ow[e] = make_float2((float)cs, (float)sn);
+  }
+  for (int e = threadIdx.x; e < Q / 2; e += blockDim.x) {
+    double sn, cs;
+    sincospi(2.0 * (double)e / (double)Q, &sn, &cs);
+    tw[e] = make_float2((float)cs, (float)sn);
+  }
+  for (int j = 0; j < TV; ++j) {
+    const int jv = jv0 + j;
+    const bool ok = jv < nv;
+    const int64_t band = ok ? (v_idx ? v_idx[v0 + jv] : v0 + jv) : 0;
+    const float2* src = psi_v + band * nr + (int64_t)i1 * plane;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < plane; e += blockDim.x) {
+      const int i2 = e / n, i3 = e - i2 * n;
+      float2 v = make_float2(0.f, 0.f);
+      if (ok) {
+        // shift to the lowest kept frequencies: u_v * conj(e^{2 pi i (k3min i3 + k2min i2)/n})
+        const float2 s = cmul(T3[(size_t)i3 * nk3p], T2[(size_t)i2 * nk2p]);
+        v = cmul(src[e], make_float2(s.x, -s.y));
+      }
+      Uv[(j * n + i2) * ld + i3] = v;
+    }
+  }
+  const int items1 = NCB * TV * n;
+  const int items2 = NCB * TV * nk3;
+  for (int jc0 = jc_begin; jc0 < jc_end; jc0 += NCB) {
+#pragma unroll
+    for (int cb = 0; cb < NCB; ++cb) {
+      const int jc = jc0 + cb;
+      const int64_t band = jc < jc_end ? (c_idx ? c_idx[c0 + jc] : c0 + jc) : -1;
+      const float2* src = psi_c + (band < 0 ? 0 : band) * nr + (int64_t)i1 * plane;
+      // asynchronous copies: the whole plane is in flight at once
+      for (int e = threadIdx.x; e < plane; e += blockDim.x) {
+        const int i2 = e / n, i3 = e - i2 * n;
+        float2* dst = &Uc[(cb * n + i2) * ld + i3];
+        if (band < 0)
+          *dst = make_float2(0.f, 0.f);
+        else
+          cp_async8(dst, src + e);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // stage 1: one line (i2) of one (valence, conduction) pair per thread
+    for (int it = threadIdx.x; it < items1; it += blockDim.x) {
+      const int i2 = it % n, jj = it / n, j = jj % TV, cb = jj / TV;
+      const float2* uv = Uv + (j * n + i2) * ld;
+      const float2* uc = Uc + (cb * n + i2) * ld;
+      float2 acc[NKMAX];
+      line_transform<P, Q>([&](int i3) { return cconjmul(uv[i3], uc[i3]); }, nk3, ow, tw, acc);
+      float2* xo = X + ((cb * TV + j) * n + i2) * ldx;
+#pragma unroll
+      for (int kk = 0; kk < NKMAX; ++kk)
+        if (kk < nk3) xo[kk] = acc[kk];
+    }
+    __syncthreads();
+    // stage 2: one kept k3 column of one pair per thread
+    for (int it = threadIdx.x; it < items2; it += blockDim.x) {
+      const int kk3 = it % nk3, jj = it / nk3, j = jj % TV, cb = jj / TV;
+      const int jv = jv0 + j, jc = jc0 + cb;
+      const float2* xi = X + ((cb * TV + j) * n) * ldx + kk3;
+      float2 acc[NKMAX];
+      line_transform<P, Q>([&](int i2) { return xi[i2 * ldx]; }, nk2, ow, tw, acc);
+      if (jv < nv && jc < jc_end) {
+        float2* dst = D + ((int64_t)(jv * nc + jc) * n + i1) * box + kk3;
+#pragma unroll
+        for (int kk = 0; kk < NKMAX; ++kk)
+          if (kk < nk2) dst[(int64_t)kk * nk3] = acc[kk];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int P, int Q, int TV, int NCB>
+size_t fft_planes_smem(int nk3) {
+  constexpr int n = P * Q, ld = n | 1;
+  const int ldx = nk3 | 1;
+  return ((size_t)TV * n * ld + (size_t)NCB * n * ld + (size_t)NCB * TV * n * ldx + P * NKMAX + Q / 2) *
+         sizeof(float2);
+}
+
+template <int P, int Q, int TV, int NCB>
+cudaError_t launch_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void* psi_v, const int32_t* v_idx,
+                              int v0, int nv, const void* psi_c, const int32_t* c_idx, int c0, int nc, void* D,
+                              cudaStream_t st) {
+  const size_t sm = fft_planes_smem<P, Q, TV, NCB>(s.nk3);
+  auto kern = k_pair_planes_fft<P, Q, TV, NCB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const int vt = (nv + TV - 1) / TV;
+  int cpc = 16 * NCB;
+  while (cpc > NCB && (int64_t)p->n1 * vt * ((nc + cpc - 1) / cpc) < 4 * 152) cpc >>= 1;
+  dim3 grid(p->n1, vt, (nc + cpc - 1) / cpc);
+  kern<<<grid, 192, sm, st>>>((const float2*)psi_v, v_idx, v0, nv, (const float2*)psi_c, c_idx, c0, nc, cpc, s.nk2,
+                              s.nk3, s.nk2p, s.nk3p, s.T2f, s.T3f, (float2*)D);
+  return cudaGetLastError();
+}
+
+// FP32 planes with register FFTs when the grid is cubic, n = P*Q is supported and
+// the kept extents fit NKMAX; returns cudaErrorNotSupported otherwise.
+cudaError_t try_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void* psi_v, const int32_t* v_idx, int v0,
+                           int nv, const void* psi_c, const int32_t* c_idx, int c0, int nc, void* D,
+                           cudaStream_t st) {
+  if (!(p->n1 == p->n2 && p->n2 == p->n3) || s.nk2 > NKMAX || s.nk3 > NKMAX) return cudaErrorNotSupported;
+  switch (p->n3) {
+    case 24: return launch_fft_planes<3, 8, 2, 2>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
+    case 36: return launch_fft_planes<9, 4, 2, 2>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
+    case 48: return launch_fft_planes<3, 16, 2, 2>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
+    case 96: return launch_fft_planes<3, 32, 1, 1>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+
 size_t planes_smem(int tv, int n2, int ld3, int nk3p, size_t cb) {
   return ((size_t)tv * n2 * ld3 + (size_t)n2 * ld3 + (size_t)tv * n2 * nk3p) * cb;
 }
@@ -272,7 +502,11 @@ cudaError_t launch_pair_planes(const chi0_plan_s* p, int iq, const void* psi_v, 
                                int nv, const void* psi_c, const int32_t* c_idx, int c0, int nc, void* D,
                                cudaStream_t s) {
   const SphereQ& sq = p->q[iq];
-  if (is_split(p)) return launch_planes_r<float>(p, sq, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, s);
+  if (is_split(p)) {
+    cudaError_t e = try_fft_planes(p, sq, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, s);
+    if (e != cudaErrorNotSupported) return e;
+    return launch_planes_r<float>(p, sq, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, s);
+  }
   return launch_planes_r<double>(p, sq, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, s);
 }
 
