@@ -326,6 +326,32 @@ def run_ours(args):
     acc_pairs = prob.n_v * len(c_sel)
     del chi_a
 
+    # ---- the other split precision on the same build (reported beside the headline) ----
+    variants = {}
+    if not args.no_variants:
+        other = "fp16" if args.precision == "bf16" else "bf16"
+        plan2 = pkg.Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision=other, gw=prob.gw)
+        chi2 = plan2.new_chi(0)
+
+        def step2():
+            plan2.wfn_to_grid(cv, out=psi_v)
+            plan2.wfn_to_grid(cc, out=psi_c)
+            chi2.zero_()
+            plan2.build(0, psi_v, Ev, psi_c, Ec, chi=chi2)
+
+        step2()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            step2()
+        e1.record()
+        torch.cuda.synchronize()
+        plan2.sync_status()
+        v_ms = e0.elapsed_time(e1) / args.steps
+        variants[other] = {"ms_per_step": v_ms, "value": F / (v_ms / 1e3) / 1e12, "unit": "TFLOP/s",
+                           "precision": {"fp16": "fp16 split x3 products", "bf16": "bf16 split x6 products"}[other]}
+        del plan2, chi2
+
     # ---- plain FP64 GPU path on a sample of conduction bands, extrapolated ----
     fp64 = None
     if not args.no_fp64:
@@ -389,7 +415,7 @@ def run_ours(args):
             "accelerated": {"ms": acc_ms, "pairs": acc_pairs, "columns": len(c_sel),
                             "pair_ratio": n_pairs / acc_pairs, "speedup_vs_full": ms_step / acc_ms,
                             "N0": prob.N0, "dE_eV": 2.0},
-            "fp64_gpu": fp64, "clocks": clk.summary(), "input_gen_s": gen_s}
+            "fp64_gpu": fp64, "variants": variants, "clocks": clk.summary(), "input_gen_s": gen_s}
 
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(prob, plan, psi_v, psi_c, Ev, Ec)
@@ -460,6 +486,7 @@ def main(argv=None):
     ap.add_argument("--fp64-sample", type=int, default=32)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--case", choices=["contract", "pairs"], default=None,
                     help="run a small fixed case for profiling instead of the benchmark")
     args = ap.parse_args(argv)

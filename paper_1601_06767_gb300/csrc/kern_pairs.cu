@@ -210,7 +210,7 @@ k_pair_gather(const typename Cx<R>::T* __restrict__ D, int nc, int64_t row0, int
 //   F_a(m) = sum_{b<Q} x(a + P b) e^{2 pi i b m/Q}   (Q-point FFT in registers).
 // Shared memory: Uv'[TV][n][ld], Uc[NCB][n][ld], X[NCB][TV][n][ldx], tables.
 // ---------------------------------------------------------------------------
-constexpr int NKMAX = 32;
+constexpr int NKMAX = 28;
 
 __device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
@@ -241,8 +241,12 @@ __device__ __forceinline__ void fft_reg(float2 (&x)[Q], const float2* __restrict
       x[j] = t;
     }
   }
+  constexpr int LOG2Q = (Q >= 32) ? 5 : (Q >= 16) ? 4 : (Q >= 8) ? 3 : (Q >= 4) ? 2 : 1;
+  static_assert((1 << LOG2Q) == Q, "Q must be a power of two <= 32");
+  // stage loop with an additive counter so that it unrolls completely and x stays in registers
 #pragma unroll
-  for (int len = 2; len <= Q; len <<= 1) {
+  for (int stage = 0; stage < LOG2Q; ++stage) {
+    const int len = 2 << stage;
 #pragma unroll
     for (int i = 0; i < Q; i += len) {
 #pragma unroll
@@ -263,20 +267,20 @@ __device__ __forceinline__ void fft_reg(float2 (&x)[Q], const float2* __restrict
   }
 }
 
-// acc[kk] (+)= sum over the P sub-sequences of one length-n line read through `ld`
-template <int P, int Q, typename Load>
+// acc[kk] = sum over the P sub-sequences of one length-n line (outputs kk < nk <= NK)
+template <int P, int Q, int NK, typename Load>
 __device__ __forceinline__ void line_transform(Load load, int nk, const float2* __restrict__ ow,
-                                               const float2* __restrict__ tw, float2 (&acc)[NKMAX]) {
+                                               const float2* __restrict__ tw, float2 (&acc)[NK]) {
 #pragma unroll
-  for (int kk = 0; kk < NKMAX; ++kk) acc[kk] = make_float2(0.f, 0.f);
-#pragma unroll
+  for (int kk = 0; kk < NK; ++kk) acc[kk] = make_float2(0.f, 0.f);
+#pragma unroll 1
   for (int a = 0; a < P; ++a) {
     float2 x[Q];
 #pragma unroll
     for (int b = 0; b < Q; ++b) x[b] = load(a + P * b);
     fft_reg<Q>(x, tw);
 #pragma unroll
-    for (int kk = 0; kk < NKMAX; ++kk) {
+    for (int kk = 0; kk < NK; ++kk) {
       if (kk < nk) {
         if (a == 0) {
           acc[kk].x += x[kk % Q].x;
@@ -289,8 +293,8 @@ __device__ __forceinline__ void line_transform(Load load, int nk, const float2* 
   }
 }
 
-template <int P, int Q, int TV, int NCB>
-__global__ void __launch_bounds__(192)
+template <int P, int Q, int NK, int TV, int NCB>
+__global__ void __launch_bounds__(192, (TV * NCB >= 4) ? 2 : 1)
 k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ v_idx, int v0, int nv,
                   const float2* __restrict__ psi_c, const int32_t* __restrict__ c_idx, int c0, int nc, int c_per_cta,
                   int nk2, int nk3, int nk2p, int nk3p, const float2* __restrict__ T2, const float2* __restrict__ T3,
@@ -308,6 +312,7 @@ k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
   const int jv0 = blockIdx.y * TV;
   const int jc_begin = blockIdx.z * c_per_cta;
   const int jc_end = min(nc, jc_begin + c_per_cta);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   constexpr int64_t nr = (int64_t)n * n * n;
   constexpr int plane = n * n;
   const int64_t box = (int64_t)nk2 * nk3;
@@ -348,14 +353,17 @@ k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
       const int jc = jc0 + cb;
       const int64_t band = jc < jc_end ? (c_idx ? c_idx[c0 + jc] : c0 + jc) : -1;
       const float2* src = psi_c + (band < 0 ? 0 : band) * nr + (int64_t)i1 * plane;
-      // asynchronous copies: the whole plane is in flight at once
-      for (int e = threadIdx.x; e < plane; e += blockDim.x) {
-        const int i2 = e / n, i3 = e - i2 * n;
-        float2* dst = &Uc[(cb * n + i2) * ld + i3];
-        if (band < 0)
-          *dst = make_float2(0.f, 0.f);
-        else
-          cp_async8(dst, src + e);
+      // asynchronous copies, one row per warp: the whole plane is in flight at once
+      for (int i2 = warp; i2 < n; i2 += nwarp) {
+        float2* dst = Uc + (cb * n + i2) * ld;
+        const float2* sr = src + i2 * n;
+#pragma unroll
+        for (int i3 = lane; i3 < n; i3 += 32) {
+          if (band < 0)
+            dst[i3] = make_float2(0.f, 0.f);
+          else
+            cp_async8(dst + i3, sr + i3);
+        }
       }
     }
     cp_async_wait_all();
@@ -365,11 +373,11 @@ k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
       const int i2 = it % n, jj = it / n, j = jj % TV, cb = jj / TV;
       const float2* uv = Uv + (j * n + i2) * ld;
       const float2* uc = Uc + (cb * n + i2) * ld;
-      float2 acc[NKMAX];
-      line_transform<P, Q>([&](int i3) { return cconjmul(uv[i3], uc[i3]); }, nk3, ow, tw, acc);
+      float2 acc[NK];
+      line_transform<P, Q, NK>([&](int i3) { return cconjmul(uv[i3], uc[i3]); }, nk3, ow, tw, acc);
       float2* xo = X + ((cb * TV + j) * n + i2) * ldx;
 #pragma unroll
-      for (int kk = 0; kk < NKMAX; ++kk)
+      for (int kk = 0; kk < NK; ++kk)
         if (kk < nk3) xo[kk] = acc[kk];
     }
     __syncthreads();
@@ -378,12 +386,12 @@ k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
       const int kk3 = it % nk3, jj = it / nk3, j = jj % TV, cb = jj / TV;
       const int jv = jv0 + j, jc = jc0 + cb;
       const float2* xi = X + ((cb * TV + j) * n) * ldx + kk3;
-      float2 acc[NKMAX];
-      line_transform<P, Q>([&](int i2) { return xi[i2 * ldx]; }, nk2, ow, tw, acc);
+      float2 acc[NK];
+      line_transform<P, Q, NK>([&](int i2) { return xi[i2 * ldx]; }, nk2, ow, tw, acc);
       if (jv < nv && jc < jc_end) {
         float2* dst = D + ((int64_t)(jv * nc + jc) * n + i1) * box + kk3;
 #pragma unroll
-        for (int kk = 0; kk < NKMAX; ++kk)
+        for (int kk = 0; kk < NK; ++kk)
           if (kk < nk2) dst[(int64_t)kk * nk3] = acc[kk];
       }
     }
@@ -391,7 +399,7 @@ k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
   }
 }
 
-template <int P, int Q, int TV, int NCB>
+template <int P, int Q, int NK, int TV, int NCB>
 size_t fft_planes_smem(int nk3) {
   constexpr int n = P * Q, ld = n | 1;
   const int ldx = nk3 | 1;
@@ -399,12 +407,12 @@ size_t fft_planes_smem(int nk3) {
          sizeof(float2);
 }
 
-template <int P, int Q, int TV, int NCB>
+template <int P, int Q, int NK, int TV, int NCB>
 cudaError_t launch_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void* psi_v, const int32_t* v_idx,
                               int v0, int nv, const void* psi_c, const int32_t* c_idx, int c0, int nc, void* D,
                               cudaStream_t st) {
-  const size_t sm = fft_planes_smem<P, Q, TV, NCB>(s.nk3);
-  auto kern = k_pair_planes_fft<P, Q, TV, NCB>;
+  const size_t sm = fft_planes_smem<P, Q, NK, TV, NCB>(s.nk3);
+  auto kern = k_pair_planes_fft<P, Q, NK, TV, NCB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const int vt = (nv + TV - 1) / TV;
@@ -421,14 +429,21 @@ cudaError_t launch_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void
 cudaError_t try_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void* psi_v, const int32_t* v_idx, int v0,
                            int nv, const void* psi_c, const int32_t* c_idx, int c0, int nc, void* D,
                            cudaStream_t st) {
-  if (!(p->n1 == p->n2 && p->n2 == p->n3) || s.nk2 > NKMAX || s.nk3 > NKMAX) return cudaErrorNotSupported;
+  const int nk = std::max(s.nk2, s.nk3);
+  if (!(p->n1 == p->n2 && p->n2 == p->n3) || nk > NKMAX) return cudaErrorNotSupported;
+#define CHI0_FFT_CASE(P, Q, TV, NCB)                                                                    \
+  if (nk <= 12) return launch_fft_planes<P, Q, 12, TV, NCB>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st); \
+  if (nk <= 16) return launch_fft_planes<P, Q, 16, TV, NCB>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st); \
+  if (nk <= 20) return launch_fft_planes<P, Q, 20, TV, NCB>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st); \
+  return launch_fft_planes<P, Q, 28, TV, NCB>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
   switch (p->n3) {
-    case 24: return launch_fft_planes<3, 8, 2, 2>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
-    case 36: return launch_fft_planes<9, 4, 2, 2>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
-    case 48: return launch_fft_planes<3, 16, 2, 2>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
-    case 96: return launch_fft_planes<3, 32, 1, 1>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
+    case 24: { CHI0_FFT_CASE(3, 8, 2, 2) }
+    case 36: { CHI0_FFT_CASE(9, 4, 2, 2) }
+    case 48: { CHI0_FFT_CASE(3, 16, 2, 2) }
+    case 96: { CHI0_FFT_CASE(3, 32, 1, 1) }
     default: return cudaErrorNotSupported;
   }
+#undef CHI0_FFT_CASE
 }
 
 size_t planes_smem(int tv, int n2, int ld3, int nk3p, size_t cb) {
