@@ -136,6 +136,23 @@ chi0_status chi0_build(chi0_plan plan, int iq, const void* psi_v, int n_v, const
                        const void* psi_c, const int32_t* c_idx, int n_c,
                        const double* E_col, const double* w_col, void* chi0, void* stream);
 
+/* Adjoint of chi0_accumulate (derived from Eq. 1).  For a real loss L with
+ * upstream gradient Gamma_w = dL/dRe chi0[w] + i dL/dIm chi0[w]:
+ *   grad_M[p]    = sum_w conj(f_p(w)) Gamma_w M_p + f_p(w) Gamma_w^H M_p
+ *   grad dE_p    = sum_w Re( f'_p(w) conj(M_p^H Gamma_w M_p) ),
+ *   f'_p(w)      = -(w_p/2) [(dE_p - w + i d)^-2 + (dE_p + w + i d)^-2],
+ *   grad_Ev[iv]  = sum_ic grad dE_p,   grad_Ecol[ic] = -sum_iv grad dE_p.
+ * Complex gradients use the dL/dRe + i dL/dIm convention.  Give exactly one of
+ *   grad_chi0 (device) [n_freq][n_G][n_G] complex128: dense Gamma (FP64 CUDA-core products), or
+ *   diag_g    (device) [n_freq][n_G] double: Gamma_w = diag(diag_g[w]) (one fused pass; n_freq <= 64).
+ * M, E_v, E_col, w_col as for chi0_accumulate.  Outputs (written, not accumulated):
+ * grad_M (device) [n_v*n_c][n_G] complex (the plan's complex type), grad_Ev (device) [n_v],
+ * grad_Ecol (device) [n_c].  Deterministic (no atomics). */
+chi0_status chi0_backward(chi0_plan plan, int iq, const void* M, int n_v, int n_c, const double* E_v,
+                          const double* E_col, const double* w_col, const void* grad_chi0,
+                          const double* diag_g, void* grad_M, double* grad_Ev, double* grad_Ecol,
+                          void* stream);
+
 /* Kernel families counted and timed by the plan's instrumentation. */
 typedef enum {
   CHI0_K_WFN = 0,        /* wavefunctions on the grid */

@@ -3,6 +3,6 @@ the denominator-weighted contraction of Eq. 1, plain and with the accelerated
 conduction-band summation of Eq. 3/4.  The compute lives in libchi0.so
 (CUDA, sm_103a); this package is a thin binding over its C ABI."""
 from ._lib import Chi0Error, lib  # noqa: F401
-from .api import Chi0Plan, select_accelerated  # noqa: F401
+from .api import Chi0DiagLoss, Chi0Fn, Chi0Plan, select_accelerated  # noqa: F401
 
-__all__ = ["Chi0Plan", "Chi0Error", "select_accelerated", "lib"]
+__all__ = ["Chi0Plan", "Chi0Fn", "Chi0DiagLoss", "Chi0Error", "select_accelerated", "lib"]

@@ -156,6 +156,22 @@ class Chi0Plan:
                                             _ptr(w_col), _ptr(chi), _stream()))
         return chi
 
+    def backward(self, iq: int, M, n_v: int, n_c: int, E_v, E_col, w_col=None, grad_chi=None, diag_g=None):
+        """chi0_backward: returns (grad_M, grad_E_v, grad_E_col)."""
+        self._c(M, "M")
+        for t, nm in ((E_v, "E_v"), (E_col, "E_col"), (w_col, "w_col"), (diag_g, "diag_g")):
+            if t is not None:
+                self._c(t, nm, torch.float64)
+        if grad_chi is not None:
+            self._c(grad_chi, "grad_chi", torch.complex128)
+        gM = torch.empty_like(M)
+        gEv = torch.empty(n_v, dtype=torch.float64, device=self.device)
+        gEc = torch.empty(n_c, dtype=torch.float64, device=self.device)
+        self._check(L.lib().chi0_backward(self._h, iq, _ptr(M), n_v, n_c, _ptr(E_v), _ptr(E_col), _ptr(w_col),
+                                          _ptr(grad_chi), _ptr(diag_g), _ptr(gM), _ptr(gEv), _ptr(gEc),
+                                          _stream()))
+        return gM, gEv, gEc
+
     def build(self, iq: int, psi_v, E_v, psi_c, E_col, w_col=None, c_idx=None, chi=None):
         self._c(psi_v, "psi_v")
         self._c(psi_c, "psi_c")
@@ -185,3 +201,52 @@ def select_accelerated(E_c, N0: int, dE: float, dos_A: float, dos_V0: float, E_m
     if n < 0:
         raise L.Chi0Error(L.CHI0_ERR_INVALID, "chi0_select_accelerated rejected its input")
     return c_sel[:n].copy(), E_sel[:n].copy(), w_sel[:n].copy()
+
+
+class Chi0Fn(torch.autograd.Function):
+    """chi0 = Chi0Fn.apply(M, E_v, E_col, w_col, plan, iq): the contraction of
+    Eq. 1 as a differentiable op.  Gradients flow to M, E_v and E_col through
+    chi0_backward (dense upstream gradient)."""
+
+    @staticmethod
+    def forward(ctx, M, E_v, E_col, w_col, plan, iq):
+        n_v, n_c = int(E_v.numel()), int(E_col.numel())
+        chi = plan.accumulate(iq, M.contiguous(), n_v, n_c, E_v.contiguous(), E_col.contiguous(),
+                              None if w_col is None else w_col.contiguous())
+        ctx.save_for_backward(M, E_v, E_col, w_col)
+        ctx.plan, ctx.iq = plan, iq
+        return chi
+
+    @staticmethod
+    def backward(ctx, grad_chi):
+        M, E_v, E_col, w_col = ctx.saved_tensors
+        gM, gEv, gEc = ctx.plan.backward(ctx.iq, M.contiguous(), int(E_v.numel()), int(E_col.numel()),
+                                         E_v.contiguous(), E_col.contiguous(),
+                                         None if w_col is None else w_col.contiguous(),
+                                         grad_chi=grad_chi.contiguous())
+        return gM, gEv, gEc, None, None, None
+
+
+class Chi0DiagLoss(torch.autograd.Function):
+    """L = Chi0DiagLoss.apply(M, E_v, E_col, w_col, g, plan, iq) with
+    L = sum_w sum_G g[w][G] Re chi0_w(G, G); the backward uses the fused
+    diagonal adjoint of chi0_backward."""
+
+    @staticmethod
+    def forward(ctx, M, E_v, E_col, w_col, g, plan, iq):
+        n_v, n_c = int(E_v.numel()), int(E_col.numel())
+        chi = plan.accumulate(iq, M.contiguous(), n_v, n_c, E_v.contiguous(), E_col.contiguous(),
+                              None if w_col is None else w_col.contiguous())
+        loss = (g * torch.diagonal(chi, dim1=1, dim2=2).real).sum()
+        ctx.save_for_backward(M, E_v, E_col, w_col, g)
+        ctx.plan, ctx.iq = plan, iq
+        return loss
+
+    @staticmethod
+    def backward(ctx, gL):
+        M, E_v, E_col, w_col, g = ctx.saved_tensors
+        gM, gEv, gEc = ctx.plan.backward(ctx.iq, M.contiguous(), int(E_v.numel()), int(E_col.numel()),
+                                         E_v.contiguous(), E_col.contiguous(),
+                                         None if w_col is None else w_col.contiguous(),
+                                         diag_g=(g * gL).contiguous())
+        return gM, gEv, gEc, None, None, None, None

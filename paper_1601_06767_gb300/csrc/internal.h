@@ -67,6 +67,7 @@ struct chi0_plan_s {
   void* d_pack = nullptr;    // split operands of the tensor-core contraction
   size_t pack_bytes = 0;
   int* d_status = nullptr;   // device status word (bit 0: a bounded wait ran out)
+  double* d_bwd = nullptr;   // adjoint work: per-pair grad dE and per-tile partial sums
   size_t ws_bytes = 0;
   std::string err;
   bool tc_ready = false;     // tensor-map encoder resolved
@@ -114,6 +115,11 @@ cudaError_t launch_contract_f64(const chi0_plan_s* p, int nG, const double2* M, 
 cudaError_t launch_contract_tc(chi0_plan_s* p, int nG, const float2* M, int64_t K,
                                const double2* f, double2* chi, cudaStream_t s, std::string* why);
 size_t tc_pack_bytes(const chi0_plan_s* p, int64_t max_pairs, int max_nG);
+// adjoint of the contraction for pairs p0..p0+K (Gamma dense [n_freq][nG][nG] or diag [n_freq][nG])
+cudaError_t launch_backward(chi0_plan_s* p, int nG, const void* M, int64_t p0, int64_t K, int n_c,
+                            const double* E_v, const double* E_col, const double* w_col, const double2* gamma,
+                            const double* diag, void* gM, double* gEv, double* gEc, double* work, cudaStream_t s);
+int bwd_max_freq();
 bool tc_supported(std::string* why);
 
 }  // namespace chi0

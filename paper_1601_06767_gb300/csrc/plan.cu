@@ -100,7 +100,7 @@ void free_plan(chi0_plan_s* p) {
   cudaFree(w.T1d); cudaFree(w.T1f); cudaFree(w.T2d); cudaFree(w.T2f);
   cudaFree(w.T3d); cudaFree(w.T3f);
   cudaFree(p->d_omega); cudaFree(p->d_D); cudaFree(p->d_M); cudaFree(p->d_f);
-  cudaFree(p->d_pack); cudaFree(p->d_status);
+  cudaFree(p->d_pack); cudaFree(p->d_status); cudaFree(p->d_bwd);
 }
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -325,6 +325,7 @@ chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* d) {
   size_t bytes_M = (size_t)mp * p->max_nG * cb;
   size_t bytes_f = (size_t)p->n_freq * mp * sizeof(double2);
   p->pack_bytes = chi0::is_split(p) ? chi0::tc_pack_bytes(p, mp, p->max_nG) : 0;
+  const size_t bytes_bwd = (size_t)mp * (1 + (p->max_nG + 63) / 64) * sizeof(double);
   if (env_fault("oom")) { p->err = "injected fault: oom"; return bail(CHI0_ERR_OOM); }
   cudaError_t e;
   if ((e = cudaMalloc(&p->d_D, bytes_D)) != cudaSuccess ||
@@ -332,12 +333,13 @@ chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* d) {
       (e = cudaMalloc((void**)&p->d_f, bytes_f)) != cudaSuccess ||
       (p->pack_bytes && (e = cudaMalloc(&p->d_pack, p->pack_bytes)) != cudaSuccess) ||
       (e = cudaMalloc((void**)&p->d_status, sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&p->d_bwd, bytes_bwd)) != cudaSuccess ||
       (e = cudaMemset(p->d_status, 0, sizeof(int))) != cudaSuccess) {
     p->err = std::string("workspace allocation: ") + cudaGetErrorString(e);
     cudaGetLastError();
     return bail(e == cudaErrorMemoryAllocation ? CHI0_ERR_OOM : CHI0_ERR_CUDA);
   }
-  p->ws_bytes = bytes_D + bytes_M + bytes_f + p->pack_bytes + sizeof(int);
+  p->ws_bytes = bytes_D + bytes_M + bytes_f + p->pack_bytes + bytes_bwd + sizeof(int);
   *out = p;
   return CHI0_OK;
 }
@@ -464,6 +466,32 @@ chi0_status chi0_build(chi0_plan p, int iq, const void* psi_v, int n_v, const do
     if (st != CHI0_OK) return st;
     st = accumulate_impl(p, iq, p->d_M, n_v, nc, E_v, E_col + c0, w_col ? w_col + c0 : nullptr, chi0, s);
     if (st != CHI0_OK) return st;
+  }
+  return CHI0_OK;
+}
+
+chi0_status chi0_backward(chi0_plan p, int iq, const void* M, int n_v, int n_c, const double* E_v,
+                          const double* E_col, const double* w_col, const void* grad_chi0, const double* diag_g,
+                          void* grad_M, double* grad_Ev, double* grad_Ecol, void* stream) {
+  chi0_status st = check_plan(p);
+  if (st != CHI0_OK) return st;
+  if (iq < 0 || iq >= (int)p->q.size()) return fail(p, CHI0_ERR_INVALID, "iq out of range");
+  if (n_v < 0 || n_c < 0) return fail(p, CHI0_ERR_INVALID, "negative band count");
+  if ((grad_chi0 == nullptr) == (diag_g == nullptr))
+    return fail(p, CHI0_ERR_INVALID, "give exactly one of grad_chi0 and diag_g");
+  if (diag_g && p->n_freq > chi0::bwd_max_freq())
+    return fail(p, CHI0_ERR_INVALID, "the diagonal adjoint supports at most 64 frequencies");
+  if ((int64_t)n_v * n_c == 0) return CHI0_OK;
+  if (!M || !E_v || !E_col || !grad_M || !grad_Ev || !grad_Ecol) return fail(p, CHI0_ERR_INVALID, "NULL buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nG = p->q[iq].nG;
+  CK(p, cudaMemsetAsync(grad_Ev, 0, sizeof(double) * n_v, s));
+  CK(p, cudaMemsetAsync(grad_Ecol, 0, sizeof(double) * n_c, s));
+  const int64_t np = (int64_t)n_v * n_c;
+  for (int64_t p0 = 0; p0 < np; p0 += p->max_pairs) {
+    const int64_t K = std::min<int64_t>(p->max_pairs, np - p0);
+    CK(p, chi0::launch_backward(p, nG, M, p0, K, n_c, E_v, E_col, w_col, (const double2*)grad_chi0, diag_g,
+                                grad_M, grad_Ev, grad_Ecol, p->d_bwd, s));
   }
   return CHI0_OK;
 }
