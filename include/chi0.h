@@ -153,6 +153,13 @@ chi0_status chi0_backward(chi0_plan plan, int iq, const void* M, int n_v, int n_
                           const double* diag_g, void* grad_M, double* grad_Ev, double* grad_Ecol,
                           void* stream);
 
+/* Diagnostic (not part of the method): enqueue a one-thread wait on a barrier
+ * that nothing releases, bounded by budget_ms (0 < budget_ms <= 1000), through
+ * the same bounded-wait code the tensor-core kernels use.  The wait runs out,
+ * records the failure in the plan's device status word and returns, so the
+ * next chi0_sync_status reports CHI0_ERR_TIMEOUT and the plan stays usable. */
+chi0_status chi0_selftest_wait(chi0_plan plan, double budget_ms, void* stream);
+
 /* Kernel families counted and timed by the plan's instrumentation. */
 typedef enum {
   CHI0_K_WFN = 0,        /* wavefunctions on the grid */

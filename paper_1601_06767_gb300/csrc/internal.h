@@ -120,6 +120,7 @@ cudaError_t launch_backward(chi0_plan_s* p, int nG, const void* M, int64_t p0, i
                             const double* E_v, const double* E_col, const double* w_col, const double2* gamma,
                             const double* diag, void* gM, double* gEv, double* gEc, double* work, cudaStream_t s);
 int bwd_max_freq();
+cudaError_t launch_wait_selftest(chi0_plan_s* p, double budget_ms, cudaStream_t s);
 bool tc_supported(std::string* why);
 
 }  // namespace chi0

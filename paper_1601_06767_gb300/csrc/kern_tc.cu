@@ -369,6 +369,19 @@ k_contract_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   if (warp == 1) tc::tmem_dealloc(tbase, TMEM_COLS);
 }
 
+// Diagnostic: wait on an mbarrier that nothing arrives on, with the same
+// bounded wait as the contraction, so the time-out path can be exercised.
+__global__ void k_wait_selftest(uint64_t budget_ns, int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) tc::mbar_wait(&bar, 0, status, 1, budget_ns);
+  __syncthreads();
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 bool resolve_encoder(std::string* why) {
@@ -401,6 +414,11 @@ bool encode_planes(CUtensorMap* tm, void* base, bool bf16, int Kp, int nGp, int 
 }
 
 }  // namespace
+
+cudaError_t launch_wait_selftest(chi0_plan_s* p, double budget_ms, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>((uint64_t)(budget_ms * 1e6), p->d_status);
+  return cudaGetLastError();
+}
 
 bool tc_supported(std::string* why) {
   int dev = 0;

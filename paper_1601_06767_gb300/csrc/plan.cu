@@ -496,6 +496,14 @@ chi0_status chi0_backward(chi0_plan p, int iq, const void* M, int n_v, int n_c, 
   return CHI0_OK;
 }
 
+chi0_status chi0_selftest_wait(chi0_plan p, double budget_ms, void* stream) {
+  chi0_status st = check_plan(p);
+  if (st != CHI0_OK) return st;
+  if (!(budget_ms > 0.0) || budget_ms > 1000.0) return fail(p, CHI0_ERR_INVALID, "budget_ms must be in (0, 1000]");
+  CK(p, chi0::launch_wait_selftest(p, budget_ms, (cudaStream_t)stream));
+  return CHI0_OK;
+}
+
 chi0_status chi0_profile_enable(chi0_plan p, int timing_on) {
   if (!p) return CHI0_ERR_INVALID;
   p->prof_timing = timing_on != 0;
