@@ -136,6 +136,22 @@ chi0_status chi0_build(chi0_plan plan, int iq, const void* psi_v, int n_v, const
                        const void* psi_c, const int32_t* c_idx, int n_c,
                        const double* E_col, const double* w_col, void* chi0, void* stream);
 
+/* Batched build of every q-point of the plan (Eq. 1 per q-point, q-points with
+ * different sphere sizes): for each block of conduction columns, the pair
+ * elements and factors of every q-point are formed and ONE persistent
+ * tensor-core launch contracts all (q-point, frequency, tile) work items.
+ * psi_v, E_v, chi0: (host) arrays [n_q] of (device) pointers: the valence grids
+ * at k+q ([n_v][N_r] complex), their energies [n_v] and chi0[q]
+ * ([n_freq][n_G[q]][n_G[q]] complex128, accumulated).  psi_c, c_idx, n_c,
+ * E_col, w_col as for chi0_build (shared by all q-points).
+ * use_graph != 0: the enqueued work is captured into a CUDA graph on a
+ * plan-owned stream the first time these arguments are seen and the graph is
+ * launched on `stream`; later calls with the same arguments relaunch it.
+ * FP64 plans run the q-points one after another.  At most 16 q-points. */
+chi0_status chi0_build_batched(chi0_plan plan, const void* const* psi_v, int n_v, const double* const* E_v,
+                               const void* psi_c, const int32_t* c_idx, int n_c, const double* E_col,
+                               const double* w_col, void* const* chi0, int use_graph, void* stream);
+
 /* Adjoint of chi0_accumulate (derived from Eq. 1).  For a real loss L with
  * upstream gradient Gamma_w = dL/dRe chi0[w] + i dL/dIm chi0[w]:
  *   grad_M[p]    = sum_w conj(f_p(w)) Gamma_w M_p + f_p(w) Gamma_w^H M_p

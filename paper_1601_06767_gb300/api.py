@@ -156,6 +156,28 @@ class Chi0Plan:
                                             _ptr(w_col), _ptr(chi), _stream()))
         return chi
 
+    def build_batched(self, psi_vs, E_vs, psi_c, E_col, w_col=None, c_idx=None, chis=None, use_graph=True):
+        """chi0_build_batched over all q-points of the plan; returns the list of chi0[q]."""
+        nq = len(self.n_G)
+        if len(psi_vs) != nq or len(E_vs) != nq:
+            raise ValueError("one valence grid and one energy vector per q-point")
+        for t in psi_vs:
+            self._c(t, "psi_v")
+        self._c(psi_c, "psi_c")
+        n_v = psi_vs[0].shape[0]
+        n_c = psi_c.shape[0] if c_idx is None else int(c_idx.numel())
+        if c_idx is not None:
+            self._c(c_idx, "c_idx", torch.int32)
+        for t in list(E_vs) + [E_col] + ([w_col] if w_col is not None else []):
+            self._c(t, "energies", torch.float64)
+        chis = [self.new_chi(q) for q in range(nq)] if chis is None else chis
+        for t in chis:
+            self._c(t, "chi", torch.complex128)
+        arr = lambda ts: (C.c_void_p * nq)(*[t.data_ptr() for t in ts])
+        self._check(L.lib().chi0_build_batched(self._h, arr(psi_vs), n_v, arr(E_vs), _ptr(psi_c), _ptr(c_idx), n_c,
+                                               _ptr(E_col), _ptr(w_col), arr(chis), int(use_graph), _stream()))
+        return chis
+
     def backward(self, iq: int, M, n_v: int, n_c: int, E_v, E_col, w_col=None, grad_chi=None, diag_g=None):
         """chi0_backward: returns (grad_M, grad_E_v, grad_E_col)."""
         self._c(M, "M")

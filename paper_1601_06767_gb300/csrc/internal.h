@@ -67,10 +67,21 @@ struct chi0_plan_s {
   void* d_pack = nullptr;    // split operands of the tensor-core contraction
   size_t pack_bytes = 0;
   int* d_status = nullptr;   // device status word (bit 0: a bounded wait ran out)
+  // per-q workspace sets of the batched build (index 0 aliases d_M / d_f / d_pack)
+  std::vector<void*> bq_M;
+  std::vector<double2*> bq_f;
+  std::vector<void*> bq_pack;
+  // graph of the last batched build
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<const void*> graph_key;
+  int64_t graph_family[CHI0_K_COUNT] = {};   // kernel launches per family inside the captured graph
   double* d_bwd = nullptr;   // adjoint work: per-pair grad dE and per-tile partial sums
   size_t ws_bytes = 0;
   std::string err;
   bool tc_ready = false;     // tensor-map encoder resolved
+  int tc_group = 8;          // tile-row group of the contraction's raster order
+  int tc_ctas_per_sm = 1;    // persistent CTAs per SM
   // instrumentation
   bool prof_timing = false;
   int64_t prof_launches[CHI0_K_COUNT] = {};
@@ -111,6 +122,16 @@ cudaError_t launch_weights(const chi0_plan_s* p, int64_t p0, int64_t K, int n_c,
                            const double* E_col, const double* w_col, double2* f, cudaStream_t s);
 cudaError_t launch_contract_f64(const chi0_plan_s* p, int nG, const double2* M, int64_t K,
                                 const double2* f, double2* chi, cudaStream_t s);
+// one q-point's share of a batched tensor-core contraction
+struct TcJob {
+  int nG;
+  const float2* M;        // [K][nG]
+  const double2* f;       // [n_freq][K]
+  double2* chi;           // [n_freq][nG][nG]
+  void* pack;             // split-plane workspace (tc_pack_bytes)
+};
+cudaError_t launch_contract_tc_batch(chi0_plan_s* p, const TcJob* jobs, int n_jobs, int64_t K, cudaStream_t s,
+                                     std::string* why);
 // split-precision tensor-core path for K pairs of M (float2) with factors f
 cudaError_t launch_contract_tc(chi0_plan_s* p, int nG, const float2* M, int64_t K,
                                const double2* f, double2* chi, cudaStream_t s, std::string* why);

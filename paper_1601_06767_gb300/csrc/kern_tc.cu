@@ -21,6 +21,8 @@
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
+#include <string.h>
+
 #include <algorithm>
 #include <string>
 
@@ -232,19 +234,56 @@ __device__ __forceinline__ void issue_stage(const unsigned char* st, uint32_t d_
   }
 }
 
+// One persistent launch over a list of work items (q-point, frequency, 128x128
+// output tile), q-points with different sphere sizes in one batch.  Every
+// item contracts the same number of pairs (nK stages), so items are assigned
+// round-robin; the stage and chain counters run on across items, so the TMA
+// ring and the TMEM double buffers never drain between items.
+constexpr int MAXQ = 16;
+
+struct TcBatch {
+  CUtensorMap tmA[MAXQ];
+  CUtensorMap tmB[MAXQ];
+  double2* chi[MAXQ];
+  const double* inv[MAXQ];
+  int nG[MAXQ];
+  int tiles[MAXQ];
+  int64_t item0[MAXQ + 1];   // first item of each q-point
+  int n_q, n_freq, nK, chain_k, n_products, group;
+  int64_t total_items;
+};
+
+// item -> (q, frequency, tile row, tile column); tiles are visited in groups of
+// `group` tile rows, column by column inside a group (keeps A and B tiles of
+// concurrently running CTAs close together in L2)
+__device__ __forceinline__ void decode_item(const TcBatch& P, int64_t item, int& q, int& iw, int& tm, int& tn) {
+  q = 0;
+  while (q + 1 < P.n_q && item >= P.item0[q + 1]) ++q;
+  const int64_t r = item - P.item0[q];
+  const int T = P.tiles[q];
+  const int64_t tt = (int64_t)T * T;
+  iw = (int)(r / tt);
+  const int t = (int)(r - (int64_t)iw * tt);
+  const int g = min(P.group, T);
+  const int grp = t / (g * T);
+  const int first = grp * g;
+  const int rows = min(g, T - first);
+  const int within = t - grp * g * T;
+  tm = first + within % rows;
+  tn = within / rows;
+}
+
 template <bool BF16, int NT>
 __global__ void __launch_bounds__(THREADS, 1)
-k_contract_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int nG, int nK,
-              int chain_k, int n_products, const double* __restrict__ inv_scale, double2* __restrict__ chi,
-              int* __restrict__ status) {
+k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
   using RG = Ring<NT>;
-  constexpr int STAGES = RG::STAGES, STAGE_BYTES = RG::STAGE_BYTES, P = RG::PLANES;
+  constexpr int STAGES = RG::STAGES, STAGE_BYTES = RG::STAGE_BYTES, PL = RG::PLANES;
   extern __shared__ __align__(1024) unsigned char smem_tc[];
   unsigned char* tiles = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_tc) + 1023) & ~uintptr_t(1023));
   Barriers* bar = reinterpret_cast<Barriers*>(tiles + RING_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int H0 = blockIdx.x * BN, G0 = blockIdx.y * BM, iw = blockIdx.z;
+  const int nK = P.nK, chain_k = P.chain_k;
   const int nchains = (nK + chain_k - 1) / chain_k;
 
   if (threadIdx.x == 0) {
@@ -258,8 +297,10 @@ k_contract_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     }
     tc::mbar_init(&bar->done, 1);
     tc::fence_mbar_init();
-    tc::prefetch_tmap(&tmA);
-    tc::prefetch_tmap(&tmB);
+    for (int q = 0; q < P.n_q; ++q) {
+      tc::prefetch_tmap(&P.tmA[q]);
+      tc::prefetch_tmap(&P.tmB[q]);
+    }
   }
   if (warp == 1) {
     tc::tmem_alloc(&bar->tmem_base, TMEM_COLS);
@@ -273,92 +314,119 @@ k_contract_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
-      int issued = 0;
-      for (int kc = 0; kc < nK; ++kc) {
-        const int s = kc % STAGES, u = kc / STAGES;
-        if (!tc::mbar_wait(&bar->empty[s], (u & 1) ^ 1, status, 1, WAIT_BUDGET_NS)) break;
-        tc::mbar_arrive_expect_tx(&bar->full[s], STAGE_BYTES);
-        unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
+      int64_t gs = 0;
+      bool ok = true;
+      for (int64_t item = blockIdx.x; item < P.total_items && ok; item += gridDim.x) {
+        int q, iw, tm, tn;
+        decode_item(P, item, q, iw, tm, tn);
+        for (int kc = 0; kc < nK; ++kc, ++gs) {
+          const int s = (int)(gs % STAGES);
+          const uint32_t u = (uint32_t)(gs / STAGES);
+          if (!tc::mbar_wait(&bar->empty[s], (u & 1) ^ 1, status, 1, WAIT_BUDGET_NS)) { ok = false; break; }
+          tc::mbar_arrive_expect_tx(&bar->full[s], STAGE_BYTES);
+          unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
 #pragma unroll
-        for (int j = 0; j < P; ++j)
-          tc::tma_load_3d(st + j * TILE_BYTES, &tmA, &bar->full[s], kc * BK, G0, iw * P + j);
+          for (int j = 0; j < PL; ++j)
+            tc::tma_load_3d(st + j * TILE_BYTES, &P.tmA[q], &bar->full[s], kc * BK, tm * BM, iw * PL + j);
 #pragma unroll
-        for (int j = 0; j < P; ++j)
-          tc::tma_load_3d(st + (P + j) * TILE_BYTES, &tmB, &bar->full[s], kc * BK, H0, j);
-        issued = kc + 1;
+          for (int j = 0; j < PL; ++j)
+            tc::tma_load_3d(st + (PL + j) * TILE_BYTES, &P.tmB[q], &bar->full[s], kc * BK, tn * BN, j);
+        }
       }
       // copies still in flight must land before the CTA may exit
-      for (int kc = max(0, issued - STAGES); kc < issued; ++kc)
-        tc::mbar_wait(&bar->full[kc % STAGES], (kc / STAGES) & 1, status, 1, WAIT_BUDGET_NS);
+      for (int64_t g = max((int64_t)0, gs - STAGES); g < gs; ++g)
+        tc::mbar_wait(&bar->full[g % STAGES], (uint32_t)((g / STAGES) & 1), status, 1, WAIT_BUDGET_NS);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      for (int kc = 0; kc < nK; ++kc) {
-        const int c = kc / chain_k, buf = c & 1;
-        const bool first = (kc % chain_k) == 0;
-        if (first) {
-          if (!tc::mbar_wait(&bar->tempty[buf], ((c >> 1) & 1) ^ 1, status, 1, WAIT_BUDGET_NS)) break;
+      int64_t gs = 0, gc = 0;
+      bool ok = true;
+      for (int64_t item = blockIdx.x; item < P.total_items && ok; item += gridDim.x) {
+        for (int kc = 0; kc < nK; ++kc, ++gs) {
+          const int buf = (int)(gc & 1);
+          const bool first = (kc % chain_k) == 0;
+          if (first) {
+            if (!tc::mbar_wait(&bar->tempty[buf], (uint32_t)(((gc >> 1) & 1) ^ 1), status, 1, WAIT_BUDGET_NS)) {
+              ok = false;
+              break;
+            }
+            tc::fence_after();
+          }
+          const int s = (int)(gs % STAGES);
+          if (!tc::mbar_wait(&bar->full[s], (uint32_t)((gs / STAGES) & 1), status, 1, WAIT_BUDGET_NS)) {
+            ok = false;
+            break;
+          }
           tc::fence_after();
+          const unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
+          const uint32_t d_re = tbase + buf * 256, d_im = d_re + 128;
+          issue_stage<BF16, NT>(st, d_re, d_im, first, P.n_products);
+          tc::mma_commit(&bar->empty[s]);
+          if ((kc % chain_k) == chain_k - 1 || kc == nK - 1) {
+            tc::mma_commit(&bar->tfull[buf]);
+            ++gc;
+          }
         }
-        const int s = kc % STAGES;
-        if (!tc::mbar_wait(&bar->full[s], (kc / STAGES) & 1, status, 1, WAIT_BUDGET_NS)) break;
-        tc::fence_after();
-        const unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
-        const uint32_t d_re = tbase + buf * 256, d_im = d_re + 128;
-        issue_stage<BF16, NT>(st, d_re, d_im, first, n_products);
-        tc::mma_commit(&bar->empty[s]);
-        if ((kc % chain_k) == chain_k - 1 || kc == nK - 1) tc::mma_commit(&bar->tfull[buf]);
       }
       tc::mma_commit(&bar->done);
       tc::mbar_wait(&bar->done, 0, status, 1, WAIT_BUDGET_NS);
     }
   } else {
-    // ---------------- epilogue: drain chains, then FP64 merge ----------------
+    // ---------------- epilogue: drain chains, then FP64 merge per item ----------------
     const int ew = warp - 2, quad = warp & 3, half = ew >> 2;
     const int row = quad * 32 + lane;
-    float sre[64], sim[64];
-#pragma unroll
-    for (int i = 0; i < 64; ++i) { sre[i] = 0.f; sim[i] = 0.f; }
+    int64_t gc = 0;
     bool ok = true;
-    for (int c = 0; c < nchains; ++c) {
-      const int buf = c & 1;
-      if (!tc::mbar_wait(&bar->tfull[buf], (c >> 1) & 1, status, 1, WAIT_BUDGET_NS)) { ok = false; break; }
-      tc::fence_after();
-      const uint32_t ta = tbase + ((uint32_t)(quad * 32) << 16) + buf * 256 + half * 64;
-      float v[32];
-      tc::tmem_ld32(ta, v);
-      tc::tmem_ld_wait();
+    for (int64_t item = blockIdx.x; item < P.total_items && ok; item += gridDim.x) {
+      int q, iw, tm, tn;
+      decode_item(P, item, q, iw, tm, tn);
+      float sre[64], sim[64];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) sre[i] += v[i];
-      tc::tmem_ld32(ta + 32, v);
-      tc::tmem_ld_wait();
+      for (int i = 0; i < 64; ++i) { sre[i] = 0.f; sim[i] = 0.f; }
+      for (int c = 0; c < nchains; ++c, ++gc) {
+        const int buf = (int)(gc & 1);
+        if (!tc::mbar_wait(&bar->tfull[buf], (uint32_t)((gc >> 1) & 1), status, 1, WAIT_BUDGET_NS)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after();
+        const uint32_t ta = tbase + ((uint32_t)(quad * 32) << 16) + buf * 256 + half * 64;
+        float v[32];
+        tc::tmem_ld32(ta, v);
+        tc::tmem_ld_wait();
 #pragma unroll
-      for (int i = 0; i < 32; ++i) sre[32 + i] += v[i];
-      tc::tmem_ld32(ta + 128, v);
-      tc::tmem_ld_wait();
+        for (int i = 0; i < 32; ++i) sre[i] += v[i];
+        tc::tmem_ld32(ta + 32, v);
+        tc::tmem_ld_wait();
 #pragma unroll
-      for (int i = 0; i < 32; ++i) sim[i] += v[i];
-      tc::tmem_ld32(ta + 160, v);
-      tc::tmem_ld_wait();
+        for (int i = 0; i < 32; ++i) sre[32 + i] += v[i];
+        tc::tmem_ld32(ta + 128, v);
+        tc::tmem_ld_wait();
 #pragma unroll
-      for (int i = 0; i < 32; ++i) sim[32 + i] += v[i];
-      tc::fence_before();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&bar->tempty[buf]);
-    }
-    const int G = G0 + row;
-    if (ok && G < nG) {
-      const double sc = inv_scale[iw];
-      const int Hb = H0 + half * 64;
-      double2* out = chi + ((size_t)iw * nG + G) * nG + Hb;
+        for (int i = 0; i < 32; ++i) sim[i] += v[i];
+        tc::tmem_ld32(ta + 160, v);
+        tc::tmem_ld_wait();
 #pragma unroll
-      for (int i = 0; i < 64; ++i) {
-        if (Hb + i < nG) {
-          double2 o = out[i];
-          o.x += (double)sre[i] * sc;
-          o.y += (double)sim[i] * sc;
-          out[i] = o;
+        for (int i = 0; i < 32; ++i) sim[32 + i] += v[i];
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&bar->tempty[buf]);
+      }
+      const int nG = P.nG[q];
+      const int G = tm * BM + row;
+      if (ok && G < nG) {
+        const double sc = P.inv[q][iw];
+        const int Hb = tn * BN + half * 64;
+        double2* out = P.chi[q] + ((size_t)iw * nG + G) * nG + Hb;
+#pragma unroll
+        for (int i = 0; i < 64; ++i) {
+          if (Hb + i < nG) {
+            double2 o = out[i];
+            o.x += (double)sre[i] * sc;
+            o.y += (double)sim[i] * sc;
+            out[i] = o;
+          }
         }
       }
     }
@@ -445,59 +513,114 @@ size_t tc_pack_bytes(const chi0_plan_s* p, int64_t max_pairs, int max_nG) {
   return planes * nGp * Kp * 2 + scal;
 }
 
-template <bool BF16, int NT>
-cudaError_t run_tc(chi0_plan_s* p, int nG, const float2* M, int64_t K, const double2* f, double2* chi,
-                   cudaStream_t s, std::string* why) {
-  const int nGp = round_up_i(nG, BM);
-  const int Kp = (int)((K + 63) / 64 * 64);
+// workspace of one q-point's split planes: B, A, then amax / scales / inverse scales
+struct PackWs {
+  uint16_t* Bp;
+  uint16_t* Ap;
+  unsigned int* amax;
+  float* scale;
+  double* inv;
+};
+
+static PackWs pack_ws(const chi0_plan_s* p, void* base, int nGp, int Kp) {
   const size_t planes_ws = 2 * (size_t)n_terms(p) * (1 + (size_t)p->n_freq) * (size_t)round_up_i(p->max_nG, BM) *
                            (size_t)((p->max_pairs + 63) / 64 * 64) * 2;
-  uint16_t* Bp = reinterpret_cast<uint16_t*>(p->d_pack);
-  uint16_t* Ap = Bp + (size_t)2 * NT * nGp * Kp;
-  unsigned char* tail = reinterpret_cast<unsigned char*>(p->d_pack) + planes_ws;
-  unsigned int* amax = reinterpret_cast<unsigned int*>(tail);                     // [1 + n_freq]
-  float* scale = reinterpret_cast<float*>(tail + 8 * (size_t)(p->n_freq + 1));   // [1 + n_freq]
-  double* inv = reinterpret_cast<double*>(tail + 16 * (size_t)(p->n_freq + 1));              // [n_freq]
-  cudaError_t e;
-  {
-    ProfScope ps(p, CHI0_K_PACK, s, 3);
-    e = cudaMemsetAsync(amax, 0, sizeof(unsigned int) * (p->n_freq + 1), s);
-    if (e != cudaSuccess) return e;
-    k_absmax<<<2 * 152, 256, 0, s>>>(M, K * nG, f, K, p->n_freq, amax);
-    k_scales<<<1, 128, 0, s>>>(amax, p->n_freq, scale, inv);
-    dim3 gpk(nGp / 32, Kp / 64);
-    const size_t smp = (size_t)(64 * 33 + 64 * p->n_freq) * sizeof(float2);
-    e = cudaFuncSetAttribute(k_pack<BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
-    if (e != cudaSuccess) return e;
-    k_pack<BF16, NT><<<gpk, 256, smp, s>>>(M, nG, K, nGp, Kp, f, p->n_freq, scale, (uint32_t*)Bp, (uint32_t*)Ap);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  CUtensorMap tmA, tmB;
-  if (!encode_planes(&tmB, Bp, BF16, Kp, nGp, 2 * NT, why)) return cudaErrorInvalidValue;
-  if (!encode_planes(&tmA, Ap, BF16, Kp, nGp, 2 * NT * p->n_freq, why)) return cudaErrorInvalidValue;
-  const int nK = Kp / BK;
-  const int chain_k = std::max(1, p->chain_pairs / BK);
-  dim3 grid(nGp / BN, nGp / BM, p->n_freq);
-  e = cudaFuncSetAttribute(k_contract_tc<BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  PackWs w;
+  w.Bp = reinterpret_cast<uint16_t*>(base);
+  w.Ap = w.Bp + (size_t)2 * n_terms(p) * nGp * Kp;
+  unsigned char* tail = reinterpret_cast<unsigned char*>(base) + planes_ws;
+  w.amax = reinterpret_cast<unsigned int*>(tail);
+  w.scale = reinterpret_cast<float*>(tail + 8 * (size_t)(p->n_freq + 1));
+  w.inv = reinterpret_cast<double*>(tail + 16 * (size_t)(p->n_freq + 1));
+  return w;
+}
+
+template <bool BF16, int NT>
+static cudaError_t pack_one(chi0_plan_s* p, int nG, const float2* M, int64_t K, const double2* f, const PackWs& w,
+                            int nGp, int Kp, cudaStream_t s) {
+  ProfScope ps(p, CHI0_K_PACK, s, 3);
+  cudaError_t e = cudaMemsetAsync(w.amax, 0, sizeof(unsigned int) * (p->n_freq + 1), s);
   if (e != cudaSuccess) return e;
-  ProfScope ps(p, CHI0_K_CONTRACT_TC, s, 1);
-  k_contract_tc<BF16, NT><<<grid, THREADS, SMEM_BYTES, s>>>(tmA, tmB, nG, nK, chain_k, p->n_products, inv, chi,
-                                                           p->d_status);
+  k_absmax<<<2 * 152, 256, 0, s>>>(M, K * nG, f, K, p->n_freq, w.amax);
+  k_scales<<<1, 128, 0, s>>>(w.amax, p->n_freq, w.scale, w.inv);
+  dim3 gpk(nGp / 32, Kp / 64);
+  const size_t smp = (size_t)(64 * 33 + 64 * p->n_freq) * sizeof(float2);
+  e = cudaFuncSetAttribute(k_pack<BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+  if (e != cudaSuccess) return e;
+  k_pack<BF16, NT><<<gpk, 256, smp, s>>>(M, nG, K, nGp, Kp, f, p->n_freq, w.scale, (uint32_t*)w.Bp,
+                                         (uint32_t*)w.Ap);
   return cudaGetLastError();
+}
+
+template <bool BF16, int NT>
+static cudaError_t run_tc(chi0_plan_s* p, const TcJob* jobs, int n_jobs, int64_t K, cudaStream_t s,
+                          std::string* why) {
+  const int Kp = (int)((K + 63) / 64 * 64);
+  TcBatch* P = new TcBatch();
+  memset(P, 0, sizeof(TcBatch));
+  int64_t items = 0;
+  for (int j = 0; j < n_jobs; ++j) {
+    const TcJob& jb = jobs[j];
+    const int nGp = round_up_i(jb.nG, BM);
+    PackWs w = pack_ws(p, jb.pack, nGp, Kp);
+    cudaError_t e = pack_one<BF16, NT>(p, jb.nG, jb.M, K, jb.f, w, nGp, Kp, s);
+    if (e != cudaSuccess) { delete P; return e; }
+    if (!encode_planes(&P->tmB[j], w.Bp, BF16, Kp, nGp, 2 * NT, why) ||
+        !encode_planes(&P->tmA[j], w.Ap, BF16, Kp, nGp, 2 * NT * p->n_freq, why)) {
+      delete P;
+      return cudaErrorInvalidValue;
+    }
+    P->chi[j] = jb.chi;
+    P->inv[j] = w.inv;
+    P->nG[j] = jb.nG;
+    P->tiles[j] = nGp / BM;
+    P->item0[j] = items;
+    items += (int64_t)(nGp / BM) * (nGp / BM) * p->n_freq;
+  }
+  P->item0[n_jobs] = items;
+  P->n_q = n_jobs;
+  P->n_freq = p->n_freq;
+  P->nK = Kp / BK;
+  P->chain_k = std::max(1, p->chain_pairs / BK);
+  P->n_products = p->n_products;
+  P->group = p->tc_group > 0 ? p->tc_group : 8;
+  P->total_items = items;
+  cudaError_t e = cudaFuncSetAttribute(k_contract_tc<BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)SMEM_BYTES);
+  if (e != cudaSuccess) { delete P; return e; }
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::min<int64_t>(items, (int64_t)nsm * std::max(1, p->tc_ctas_per_sm));
+  {
+    ProfScope ps(p, CHI0_K_CONTRACT_TC, s, 1);
+    k_contract_tc<BF16, NT><<<grid, THREADS, SMEM_BYTES, s>>>(*P, p->d_status);
+  }
+  delete P;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contract_tc_batch(chi0_plan_s* p, const TcJob* jobs, int n_jobs, int64_t K, cudaStream_t s,
+                                     std::string* why) {
+  if (K <= 0 || n_jobs <= 0) return cudaSuccess;
+  if (n_jobs > MAXQ) {
+    if (why) *why = "at most 16 q-points per batch";
+    return cudaErrorInvalidValue;
+  }
+  if (!resolve_encoder(why)) return cudaErrorNotSupported;
+  const bool bf16 = p->prec == CHI0_SPLIT_BF16;
+  if (n_terms(p) == 3) {
+    if (bf16) return run_tc<true, 3>(p, jobs, n_jobs, K, s, why);
+    return run_tc<false, 3>(p, jobs, n_jobs, K, s, why);
+  }
+  if (bf16) return run_tc<true, 2>(p, jobs, n_jobs, K, s, why);
+  return run_tc<false, 2>(p, jobs, n_jobs, K, s, why);
 }
 
 cudaError_t launch_contract_tc(chi0_plan_s* p, int nG, const float2* M, int64_t K, const double2* f, double2* chi,
                                cudaStream_t s, std::string* why) {
-  if (K <= 0) return cudaSuccess;
-  if (!resolve_encoder(why)) return cudaErrorNotSupported;
-  const bool bf16 = p->prec == CHI0_SPLIT_BF16;
-  if (n_terms(p) == 3) {
-    if (bf16) return run_tc<true, 3>(p, nG, M, K, f, chi, s, why);
-    return run_tc<false, 3>(p, nG, M, K, f, chi, s, why);
-  }
-  if (bf16) return run_tc<true, 2>(p, nG, M, K, f, chi, s, why);
-  return run_tc<false, 2>(p, nG, M, K, f, chi, s, why);
+  TcJob jb{nG, M, f, chi, p->d_pack};
+  return launch_contract_tc_batch(p, &jb, 1, K, s, why);
 }
 
 }  // namespace chi0

@@ -101,6 +101,13 @@ void free_plan(chi0_plan_s* p) {
   cudaFree(w.T3d); cudaFree(w.T3f);
   cudaFree(p->d_omega); cudaFree(p->d_D); cudaFree(p->d_M); cudaFree(p->d_f);
   cudaFree(p->d_pack); cudaFree(p->d_status); cudaFree(p->d_bwd);
+  for (size_t i = 1; i < p->bq_M.size(); ++i) {
+    cudaFree(p->bq_M[i]);
+    cudaFree(p->bq_f[i]);
+    cudaFree(p->bq_pack[i]);
+  }
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
 }
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -340,6 +347,28 @@ chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* d) {
     return bail(e == cudaErrorMemoryAllocation ? CHI0_ERR_OOM : CHI0_ERR_CUDA);
   }
   p->ws_bytes = bytes_D + bytes_M + bytes_f + p->pack_bytes + bytes_bwd + sizeof(int);
+  p->bq_M.assign(1, p->d_M);
+  p->bq_f.assign(1, p->d_f);
+  p->bq_pack.assign(1, p->d_pack);
+  if (chi0::is_split(p) && d->n_q > 1) {
+    for (int i = 1; i < d->n_q; ++i) {
+      void *m = nullptr, *pk = nullptr;
+      double2* f = nullptr;
+      if ((e = cudaMalloc(&m, bytes_M)) != cudaSuccess || (e = cudaMalloc((void**)&f, bytes_f)) != cudaSuccess ||
+          (e = cudaMalloc(&pk, p->pack_bytes)) != cudaSuccess) {
+        cudaFree(m);
+        cudaFree(f);
+        cudaFree(pk);
+        p->err = std::string("batched workspace allocation: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        return bail(e == cudaErrorMemoryAllocation ? CHI0_ERR_OOM : CHI0_ERR_CUDA);
+      }
+      p->bq_M.push_back(m);
+      p->bq_f.push_back(f);
+      p->bq_pack.push_back(pk);
+      p->ws_bytes += bytes_M + bytes_f + p->pack_bytes;
+    }
+  }
   *out = p;
   return CHI0_OK;
 }
@@ -538,6 +567,91 @@ chi0_status chi0_profile_read(chi0_plan p, double* total_ms, int64_t* launches) 
     if (total_ms) total_ms[k] = t;
     if (launches) launches[k] = p->prof_launches[k];
   }
+  return CHI0_OK;
+}
+
+// enqueue the batched build of every q-point of the plan on stream s
+static chi0_status build_batched_enqueue(chi0_plan p, const void* const* psi_v, int n_v, const double* const* E_v,
+                                         const void* psi_c, const int32_t* c_idx, int n_c, const double* E_col,
+                                         const double* w_col, void* const* chi, cudaStream_t s) {
+  const int nq = (int)p->q.size();
+  const int cb = (int)std::max<int64_t>(1, p->max_pairs / n_v);
+  for (int c0 = 0; c0 < n_c; c0 += cb) {
+    const int nc = std::min(cb, n_c - c0);
+    const int64_t K = (int64_t)n_v * nc;
+    if (!chi0::is_split(p)) {
+      for (int q = 0; q < nq; ++q) {
+        chi0_status st = pairs_impl(p, q, psi_v[q], nullptr, n_v, psi_c, c_idx, c0, nc, p->d_M, nc, s);
+        if (st != CHI0_OK) return st;
+        st = accumulate_impl(p, q, p->d_M, n_v, nc, E_v[q], E_col + c0, w_col ? w_col + c0 : nullptr, chi[q], s);
+        if (st != CHI0_OK) return st;
+      }
+      continue;
+    }
+    std::vector<chi0::TcJob> jobs(nq);
+    for (int q = 0; q < nq; ++q) {
+      chi0_status st = pairs_impl(p, q, psi_v[q], nullptr, n_v, psi_c, c_idx, c0, nc, p->bq_M[q], nc, s);
+      if (st != CHI0_OK) return st;
+      {
+        chi0::ProfScope ps(p, CHI0_K_WEIGHTS, s, 1);
+        CK(p, chi0::launch_weights(p, 0, K, nc, E_v[q], E_col + c0, w_col ? w_col + c0 : nullptr, p->bq_f[q], s));
+      }
+      jobs[q] = chi0::TcJob{p->q[q].nG, (const float2*)p->bq_M[q], p->bq_f[q], (double2*)chi[q], p->bq_pack[q]};
+    }
+    std::string why;
+    cudaError_t e = chi0::launch_contract_tc_batch(p, jobs.data(), nq, K, s, &why);
+    if (e != cudaSuccess) return fail(p, CHI0_ERR_CUDA, "batched contraction: " + why + " " + cudaGetErrorString(e));
+  }
+  return CHI0_OK;
+}
+
+chi0_status chi0_build_batched(chi0_plan p, const void* const* psi_v, int n_v, const double* const* E_v,
+                               const void* psi_c, const int32_t* c_idx, int n_c, const double* E_col,
+                               const double* w_col, void* const* chi, int use_graph, void* stream) {
+  chi0_status st = check_plan(p);
+  if (st != CHI0_OK) return st;
+  const int nq = (int)p->q.size();
+  if (!psi_v || !E_v || !chi) return fail(p, CHI0_ERR_INVALID, "NULL host pointer array");
+  if (n_v < 0 || n_c < 0) return fail(p, CHI0_ERR_INVALID, "negative band count");
+  if ((int64_t)n_v * n_c == 0) return CHI0_OK;
+  if (!psi_c || !E_col) return fail(p, CHI0_ERR_INVALID, "NULL buffer");
+  for (int q = 0; q < nq; ++q)
+    if (!psi_v[q] || !E_v[q] || !chi[q]) return fail(p, CHI0_ERR_INVALID, "NULL buffer in a per-q array");
+  if (n_v > p->max_pairs) return fail(p, CHI0_ERR_INVALID, "n_v exceeds the plan's pair block; raise max_pairs");
+  if (nq > 16) return fail(p, CHI0_ERR_INVALID, "at most 16 q-points per batched build");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!use_graph) return build_batched_enqueue(p, psi_v, n_v, E_v, psi_c, c_idx, n_c, E_col, w_col, chi, s);
+  // graph mode: capture once per argument set on a plan-owned stream, then launch the graph on `stream`
+  std::vector<const void*> key;
+  for (int q = 0; q < nq; ++q) { key.push_back(psi_v[q]); key.push_back(E_v[q]); key.push_back(chi[q]); }
+  key.push_back(psi_c); key.push_back(c_idx); key.push_back(E_col); key.push_back(w_col);
+  key.push_back((const void*)(intptr_t)n_v); key.push_back((const void*)(intptr_t)n_c);
+  if (!p->graph_exec || key != p->graph_key) {
+    if (p->graph_exec) { cudaGraphExecDestroy(p->graph_exec); p->graph_exec = nullptr; }
+    if (!p->cap_stream) CK(p, cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    const bool timing = p->prof_timing;
+    p->prof_timing = false;    // no timing events inside the captured graph
+    int64_t saved[CHI0_K_COUNT];
+    for (int k = 0; k < CHI0_K_COUNT; ++k) saved[k] = p->prof_launches[k];
+    CK(p, cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed));
+    st = build_batched_enqueue(p, psi_v, n_v, E_v, psi_c, c_idx, n_c, E_col, w_col, chi, p->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+    p->prof_timing = timing;
+    // launches are counted when the graph runs, not when it is captured
+    for (int k = 0; k < CHI0_K_COUNT; ++k) {
+      p->graph_family[k] = p->prof_launches[k] - saved[k];
+      p->prof_launches[k] = saved[k];
+    }
+    if (st != CHI0_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return fail(p, CHI0_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&p->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { p->graph_exec = nullptr; return fail(p, CHI0_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e)); }
+    p->graph_key = key;
+  }
+  CK(p, cudaGraphLaunch(p->graph_exec, s));
+  for (int k = 0; k < CHI0_K_COUNT; ++k) p->prof_launches[k] += p->graph_family[k];
   return CHI0_OK;
 }
 
