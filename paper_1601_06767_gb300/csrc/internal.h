@@ -81,6 +81,7 @@ struct chi0_plan_s {
   std::string err;
   bool tc_ready = false;     // tensor-map encoder resolved
   int tc_group = 8;          // tile-row group of the contraction's raster order
+  int64_t block_pairs = 0;   // pairs per contraction launch (<= max_pairs); set by the autotuner
   int tc_ctas_per_sm = 1;    // persistent CTAs per SM
   // instrumentation
   bool prof_timing = false;
@@ -141,6 +142,8 @@ cudaError_t launch_backward(chi0_plan_s* p, int nG, const void* M, int64_t p0, i
                             const double* E_v, const double* E_col, const double* w_col, const double2* gamma,
                             const double* diag, void* gM, double* gEv, double* gEc, double* work, cudaStream_t s);
 int bwd_max_freq();
+// autotuner: apply a cached entry for sphere iq if one exists (returns true if applied)
+bool tune_apply_cached(chi0_plan_s* p, int iq);
 cudaError_t launch_wait_selftest(chi0_plan_s* p, double budget_ms, cudaStream_t s);
 bool tc_supported(std::string* why);
 

@@ -326,6 +326,7 @@ chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* d) {
   int64_t mp = d->max_pairs ? d->max_pairs : (chi0::is_split(p) ? 8192 : 4096);
   mp = std::max<int64_t>(64, (mp + 63) / 64 * 64);
   p->max_pairs = mp;
+  p->block_pairs = mp;
   // D holds the per-plane transforms of up to D_pairs pairs (about 1 GiB)
   p->D_pairs = std::max<int64_t>(64, std::min<int64_t>(mp, ((int64_t)1 << 30) / (box * (int64_t)cb)));
   size_t bytes_D = (size_t)p->D_pairs * box * cb;
@@ -369,6 +370,7 @@ chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* d) {
       p->ws_bytes += bytes_M + bytes_f + p->pack_bytes;
     }
   }
+  if (chi0::is_split(p)) chi0::tune_apply_cached(p, 0);
   *out = p;
   return CHI0_OK;
 }
@@ -445,8 +447,9 @@ static chi0_status accumulate_impl(chi0_plan p, int iq, const void* M, int n_v, 
                                    void* chi, cudaStream_t s) {
   const int nG = p->q[iq].nG;
   const int64_t np = (int64_t)n_v * n_c;
-  for (int64_t p0 = 0; p0 < np; p0 += p->max_pairs) {
-    int64_t K = std::min<int64_t>(p->max_pairs, np - p0);
+  const int64_t blk = p->block_pairs > 0 ? std::min(p->block_pairs, p->max_pairs) : p->max_pairs;
+  for (int64_t p0 = 0; p0 < np; p0 += blk) {
+    int64_t K = std::min<int64_t>(blk, np - p0);
     {
       chi0::ProfScope ps(p, CHI0_K_WEIGHTS, s, 1);
       CK(p, chi0::launch_weights(p, p0, K, n_c, E_v, E_col, w_col, p->d_f, s));
@@ -488,7 +491,8 @@ chi0_status chi0_build(chi0_plan p, int iq, const void* psi_v, int n_v, const do
   if (n_v > p->max_pairs)
     return fail(p, CHI0_ERR_INVALID, "n_v exceeds the plan's pair block; raise max_pairs");
   cudaStream_t s = (cudaStream_t)stream;
-  const int cb = (int)std::max<int64_t>(1, p->max_pairs / n_v);
+  const int64_t blk = p->block_pairs > 0 ? std::min(p->block_pairs, p->max_pairs) : p->max_pairs;
+  const int cb = (int)std::max<int64_t>(1, blk / n_v);
   for (int c0 = 0; c0 < n_c; c0 += cb) {
     int nc = std::min(cb, n_c - c0);
     st = pairs_impl(p, iq, psi_v, nullptr, n_v, psi_c, c_idx, c0, nc, p->d_M, nc, s);
@@ -575,7 +579,8 @@ static chi0_status build_batched_enqueue(chi0_plan p, const void* const* psi_v, 
                                          const void* psi_c, const int32_t* c_idx, int n_c, const double* E_col,
                                          const double* w_col, void* const* chi, cudaStream_t s) {
   const int nq = (int)p->q.size();
-  const int cb = (int)std::max<int64_t>(1, p->max_pairs / n_v);
+  const int64_t blk = p->block_pairs > 0 ? std::min(p->block_pairs, p->max_pairs) : p->max_pairs;
+  const int cb = (int)std::max<int64_t>(1, blk / n_v);
   for (int c0 = 0; c0 < n_c; c0 += cb) {
     const int nc = std::min(cb, n_c - c0);
     const int64_t K = (int64_t)n_v * nc;

@@ -1,0 +1,183 @@
+// Autotuner of the tensor-core contraction's launch parameters (raster group
+// of the persistent work list, pairs per launch).  Candidates are timed with
+// CUDA events on synthetic operands held in the plan's own workspace; the
+// fastest is kept in the plan and appended to a small text cache.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <sys/stat.h>
+#include <sys/types.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace chi0 {
+namespace {
+
+// deterministic operands: |M| ~ 1e-2 with pseudo-random phases, energies of a gap system
+__global__ void k_fill_synthetic(float2* M, int64_t n, double* Ev, int nv, double* Ec, int nc) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)(i * 2654435761u) ^ (uint32_t)(i >> 32);
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    const float a = (float)(h & 0xFFFF) / 65536.f - 0.5f, b = (float)(h >> 16) / 65536.f - 0.5f;
+    M[i] = make_float2(0.02f * a, 0.02f * b);
+  }
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nv) Ev[t] = -0.25 + 0.25 * (t + 0.5) / nv;
+  if (t < nc) Ec[t] = 0.17 + 2.0 * (t + 0.5) / nc;
+}
+
+void mkdir_one(const std::string& dir) { mkdir(dir.c_str(), 0755); }
+
+std::string cache_path() {
+  const char* e = getenv("CHI0_TUNE_CACHE");
+  if (e && *e) return e;
+  const char* h = getenv("HOME");
+  return std::string(h ? h : "/tmp") + "/.cache/chi0_tune.txt";
+}
+
+std::string key_of(const chi0_plan_s* p, int iq) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  cudaGetDevice(&dev);
+  char name[64] = "unknown";
+  if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) snprintf(name, sizeof(name), "sm%d%d", prop.major, prop.minor);
+  cudaGetLastError();
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s nG=%d nf=%d prec=%d np=%d maxpairs=%lld", name, p->q[iq].nG, p->n_freq, (int)p->prec,
+           p->n_products, (long long)p->max_pairs);
+  return buf;
+}
+
+}  // namespace
+
+bool tune_apply_cached(chi0_plan_s* p, int iq) {
+  FILE* fh = fopen(cache_path().c_str(), "r");
+  if (!fh) return false;
+  const std::string key = key_of(p, iq);
+  char line[512];
+  bool hit = false;
+  while (fgets(line, sizeof(line), fh)) {
+    if (strncmp(line, key.c_str(), key.size()) != 0 || line[key.size()] != ' ') continue;
+    int g = 0;
+    long long b = 0;
+    if (sscanf(line + key.size(), " group=%d block=%lld", &g, &b) == 2 && g > 0 && b > 0 && b <= p->max_pairs) {
+      p->tc_group = g;
+      p->block_pairs = b;
+      hit = true;   // the last matching line wins
+    }
+  }
+  fclose(fh);
+  return hit;
+}
+
+}  // namespace chi0
+
+extern "C" chi0_status chi0_autotune(chi0_plan p, int iq, int flags, double* best_us_per_pair, void* stream) {
+  using namespace chi0;
+  if (!p) return CHI0_ERR_INVALID;
+  if (iq < 0 || iq >= (int)p->q.size()) {
+    p->err = "iq out of range";
+    return CHI0_ERR_INVALID;
+  }
+  if (!is_split(p)) {
+    p->err = "the autotuner covers the tensor-core contraction of split-precision plans";
+    return CHI0_ERR_UNSUPPORTED;
+  }
+  if (!(flags & 1) && tune_apply_cached(p, iq)) {
+    if (best_us_per_pair) *best_us_per_pair = -1.0;
+    return CHI0_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nG = p->q[iq].nG;
+  const int T = (nG + 127) / 128;
+  // synthetic operands: M block in the plan's M workspace, energies in the adjoint workspace
+  const int nv = 128;
+  const int64_t Kmax = p->max_pairs / nv * nv;
+  if (Kmax <= 0) {
+    p->err = "max_pairs too small to tune";
+    return CHI0_ERR_INVALID;
+  }
+  const int ncmax = (int)(Kmax / nv);
+  double* Ev = p->d_bwd;
+  double* Ec = p->d_bwd + nv;
+  k_fill_synthetic<<<304, 256, 0, s>>>((float2*)p->d_M, Kmax * nG, Ev, nv, Ec, ncmax);
+  double2* chi = nullptr;
+  cudaError_t e = cudaMalloc((void**)&chi, sizeof(double2) * (size_t)p->n_freq * nG * nG);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    p->err = "autotune: cannot allocate a scratch chi0";
+    return CHI0_ERR_OOM;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const bool timing = p->prof_timing;
+  p->prof_timing = false;
+  std::vector<int> groups = {1, 2, 4, 8, 16};
+  if (T > 16) groups.push_back(T);
+  std::vector<int64_t> blocks;
+  for (int64_t b = 2048; b <= Kmax; b *= 2) blocks.push_back(b / nv * nv);
+  if (blocks.empty() || blocks.back() != Kmax) blocks.push_back(Kmax);
+  const int saved_group = p->tc_group;
+  const int64_t saved_block = p->block_pairs;
+  double best = 1e30;
+  int best_g = saved_group;
+  int64_t best_b = saved_block;
+  std::string why;
+  for (int64_t b : blocks)
+    for (int g : groups) {
+      p->tc_group = g;
+      p->block_pairs = b;
+      const int nc = (int)(b / nv);
+      float ms = 0.f;
+      cudaError_t le = cudaSuccess;
+      for (int rep = 0; rep < 3 && le == cudaSuccess; ++rep) {
+        if (rep == 1) cudaEventRecord(e0, s);
+        le = launch_weights(p, 0, b, nc, Ev, Ec, nullptr, p->d_f, s);
+        if (le == cudaSuccess) le = launch_contract_tc(p, nG, (const float2*)p->d_M, b, p->d_f, chi, s, &why);
+      }
+      cudaEventRecord(e1, s);
+      if (le != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double us = 1e3 * ms / 2.0 / (double)b;
+      if (us < best) {
+        best = us;
+        best_g = g;
+        best_b = b;
+      }
+    }
+  p->prof_timing = timing;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(chi);
+  p->tc_group = best_g;
+  p->block_pairs = best_b;
+  if (best_us_per_pair) *best_us_per_pair = best;
+  if (best < 1e30) {
+    const std::string path = cache_path();
+    const size_t slash = path.find_last_of('/');
+    if (slash != std::string::npos && slash > 0) mkdir_one(path.substr(0, slash));   // one level
+    FILE* fh = fopen(path.c_str(), "a");
+    if (fh) {
+      fprintf(fh, "%s group=%d block=%lld us_per_pair=%.6f\n", key_of(p, iq).c_str(), best_g, (long long)best_b, best);
+      fclose(fh);
+    }
+  }
+  return CHI0_OK;
+}
+
+extern "C" chi0_status chi0_get_tuning(chi0_plan p, int* group, int64_t* block_pairs) {
+  if (!p) return CHI0_ERR_INVALID;
+  if (group) *group = p->tc_group;
+  if (block_pairs) *block_pairs = p->block_pairs;
+  return CHI0_OK;
+}

@@ -54,3 +54,27 @@ def test_batched_matches_oracle_and_single_q(name, nG, nv, nc, n_imag):
             assert rel_fro(got[q][iw], ref[iw]) < TOL
         assert np.array_equal(got[q], again[q])
         assert np.array_equal(got[q], single[q])
+
+
+def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
+    import torch
+    from paper_1601_06767_gb300 import Chi0Plan
+    monkeypatch.setenv("CHI0_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    prob = make_problem("c1", n_imag=2)
+    with Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision="fp16", max_pairs=8192) as plan:
+        t = plan.autotune(0, force=True)
+        assert t["group"] in (1, 2, 4, 8, 16) and 0 < t["block_pairs"] <= 8192 and t["us_per_pair"] > 0
+        # the tuned plan still computes Eq. 1
+        rng = np.random.default_rng(2)
+        M = (rng.standard_normal((4 * 40, 350)) + 1j * rng.standard_normal((4 * 40, 350))) * 0.02
+        Ev, Ec = prob.E_v[:4], prob.E_c[:40]
+        dE = (Ev[:, None] - Ec[None, :]).reshape(-1)
+        ref = chi0_from_pairs(M, freq_factor(dE, np.ones_like(dE), prob.omega, prob.delta))
+        chi = plan.accumulate(0, _dev(M.astype(np.complex64)), 4, 40, _dev(Ev), _dev(Ec)).cpu().numpy()
+        assert max(rel_fro(chi[i], ref[i]) for i in range(3)) < TOL
+    lines = (tmp_path / "tune.txt").read_text().splitlines()
+    assert len(lines) == 1 and f"group={t['group']}" in lines[0]
+    with Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision="fp16", max_pairs=8192) as plan2:
+        t2 = plan2.autotune(0)          # served from the cache
+        assert t2["us_per_pair"] == -1.0
+        assert (t2["group"], t2["block_pairs"]) == (t["group"], t["block_pairs"])
