@@ -475,6 +475,139 @@ def run_case(args):
     return 0
 
 
+def _threaded_coeff(prob, stream: int, bands, workers: int = 16):
+    """band_coefficients for `bands`, generated by a thread pool (numpy's
+    generators release the GIL while filling) into one pinned host tensor."""
+    import concurrent.futures as cf
+    import numpy as np
+    import torch
+    from synth import band_coefficients
+    bands = np.asarray(bands)
+    out = torch.empty((bands.size, prob.npw), dtype=torch.complex128).pin_memory()
+    o = out.numpy()
+    step = max(1, (bands.size + 4 * workers - 1) // (4 * workers))
+
+    def fill(i0):
+        o[i0:i0 + step] = band_coefficients(prob.seed, stream, bands[i0:i0 + step], prob.npw)
+
+    with cf.ThreadPoolExecutor(workers) as ex:
+        list(ex.map(fill, range(0, bands.size, step)))
+    return out
+
+
+def run_c5(args):
+    """256-atom-MgO-sized workload: the split path (full Eq. 1 sum and Eq. 3/4),
+    conduction bands streamed in blocks from host-generated coefficients; the
+    FP64 path on a sample, extrapolated; parity of a pair sample vs the oracle."""
+    import threading
+    import numpy as np
+    import torch
+    import paper_1601_06767_gb300 as pkg
+    from oracle import chi0_from_pairs, freq_factor, pair_elements, rel_fro, wfn_to_grid
+    from synth import make_problem
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    prob = make_problem("c5")
+    nG, nf = prob.gvec[0].shape[0], prob.omega.size
+    n_c_run = max(1, int(round(prob.n_c * args.c5_frac)))
+    CB = 512
+    t0 = time.time()
+    cv = _threaded_coeff(prob, 1, np.arange(prob.n_v)).to(dev)
+    Ev = torch.from_numpy(prob.E_v).to(dev)
+    Ec_all = torch.from_numpy(prob.E_c).to(dev)
+    plan = pkg.Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision=args.precision, gw=prob.gw,
+                        n_products=args.n_products, max_pairs=8192)
+    psi_v = plan.wfn_to_grid(cv)
+    chi = plan.new_chi(0)
+    psi_c = torch.empty((CB,) + plan.n, dtype=plan.cdtype, device=dev)
+
+    def stream_build(bands, E_cols, w_cols, chi_out):
+        """wavefunctions + build for conduction bands `bands` (host-generated, prefetched)."""
+        blocks = [bands[i:i + CB] for i in range(0, len(bands), CB)]
+        box = {}
+
+        def gen(k):
+            box[k] = _threaded_coeff(prob, 0, blocks[k])
+
+        th = threading.Thread(target=gen, args=(0,))
+        th.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        wall0 = time.time()
+        e0.record()
+        for k, blk in enumerate(blocks):
+            th.join()
+            host = box.pop(k)
+            if k + 1 < len(blocks):
+                th = threading.Thread(target=gen, args=(k + 1,))
+                th.start()
+            cc = host.to(dev, non_blocking=True)
+            out = psi_c[:len(blk)]
+            plan.wfn_to_grid(cc, out=out)
+            sl = slice(k * CB, k * CB + len(blk))
+            plan.build(0, psi_v, Ev, out, E_cols[sl].contiguous(),
+                       w_col=None if w_cols is None else w_cols[sl].contiguous(), chi=chi_out)
+        e1.record()
+        torch.cuda.synchronize()
+        plan.sync_status()
+        return e0.elapsed_time(e1) / 1e3, time.time() - wall0
+
+    # warm-up on one small block
+    stream_build(np.arange(64), Ec_all, None, chi)
+    chi.zero_()
+    full_s, full_wall = stream_build(np.arange(n_c_run), Ec_all, None, chi)
+    scale = prob.n_c / n_c_run
+    F = algorithmic_flops(nG, prob.n_v * prob.n_c, nf)
+    # accelerated sum of Eq. 3/4
+    c_sel, E_sel, w_sel = pkg.select_accelerated(prob.E_c, prob.N0, prob.dE, prob.dos_A, prob.dos_V0, prob.E_max)
+    chi_a = chi  # reuse the buffer
+    chi_a.zero_()
+    acc_s, _ = stream_build(c_sel.astype(np.int64), torch.from_numpy(E_sel).to(dev), torch.from_numpy(w_sel).to(dev),
+                            chi_a)
+    # parity on a pair sample (rows of chi0 limited to the first 400 sphere vectors)
+    vb, cb = np.arange(2), np.array([0, 7001, 13002, 19999])
+    cvs, ccs = prob.coeff_v(0, vb), prob.coeff_c(cb)
+    ref_M = pair_elements(wfn_to_grid(cvs, prob.gw, prob.n), wfn_to_grid(ccs, prob.gw, prob.n), prob.gvec[0], prob.n)
+    dE = (prob.E_v[vb][:, None] - prob.E_c[cb][None, :]).reshape(-1)
+    fq = freq_factor(dE, np.ones_like(dE), prob.omega, prob.delta)
+    rows = 400
+    ref = np.stack([(ref_M[:, :rows].T * fq[i][None, :]) @ ref_M.conj() for i in range(nf)])
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    psv = plan.wfn_to_grid(d(cvs))
+    psc = plan.wfn_to_grid(d(ccs))
+    Mg = plan.pairs(0, psv, psc)
+    chi_s = plan.accumulate(0, Mg, 2, 4, d(prob.E_v[vb]), d(prob.E_c[cb]))
+    torch.cuda.synchronize()
+    par = max(rel_fro(chi_s[i, :rows].cpu().numpy(), ref[i]) for i in range(nf))
+    del chi, chi_a, chi_s, psi_c
+    # FP64 path on a sample: all valence bands x 2 conduction bands
+    plan64 = pkg.Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision="fp64", gw=prob.gw, max_pairs=1024)
+    pv64 = plan64.wfn_to_grid(cv)
+    cc64 = d(prob.coeff_c(np.arange(2)))
+    pc64 = plan64.wfn_to_grid(cc64)
+    chi64 = plan64.new_chi(0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan64.build(0, pv64, Ev, pc64, Ec_all[:2].contiguous(), chi=chi64)
+    e1.record()
+    torch.cuda.synchronize()
+    plan64.sync_status()
+    fp64_s = e0.elapsed_time(e1) / 1e3 * prob.n_c / 2
+    line = {"case": "c5", "workload": ("256-atom-MgO-sized chi0: N_v=512, N_c=20000, grid 96^3, N_G=8000, "
+                                         "omega = 0 + 8 imaginary; conduction bands streamed in blocks of 512"),
+            "precision": args.precision, "timed_conduction_bands": n_c_run,
+            "full": {"build_s": full_s * scale, "extrapolated": n_c_run < prob.n_c, "wall_s": full_wall * scale,
+                     "effective_tflops": F / (full_s * scale) / 1e12},
+            "accelerated": {"build_s": acc_s, "columns": len(c_sel), "pairs": prob.n_v * len(c_sel),
+                            "speedup_vs_full": full_s * scale / acc_s},
+            "fp64_gpu": {"build_s_extrapolated": fp64_s, "sample": "512 valence x 2 conduction bands",
+                         "effective_tflops": F / fp64_s / 1e12},
+            "mixed_vs_fp64": fp64_s / (full_s * scale),
+            "parity_sample_rel_fro": par, "input_gen_s": time.time() - t0}
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -487,9 +620,13 @@ def main(argv=None):
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--case", choices=["contract", "pairs"], default=None,
-                    help="run a small fixed case for profiling instead of the benchmark")
+    ap.add_argument("--case", choices=["contract", "pairs", "c5"], default=None,
+                    help="run a small fixed case for profiling (contract, pairs) or the 256-atom-sized "
+                         "measurement (c5) instead of the benchmark")
+    ap.add_argument("--c5-frac", type=float, default=1.0, help="fraction of conduction bands timed in --case c5")
     args = ap.parse_args(argv)
+    if args.case == "c5":
+        return run_c5(args)
     if args.case:
         return run_case(args)
     if args.impl == "reference":

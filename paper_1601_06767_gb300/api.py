@@ -280,3 +280,32 @@ class Chi0DiagLoss(torch.autograd.Function):
                                          None if w_col is None else w_col.contiguous(),
                                          diag_g=(g * gL).contiguous())
         return gM, gEv, gEc, None, None, None, None
+
+
+def grid_energies_of_bands(E_c, N0: int, dE: float, E_max: float):
+    """For every conduction band above N0, the midpoint E_i of the Eq. 4 energy
+    step that contains its energy (steps of width dE from E_0 = E_c[N0-1], the
+    last one clipped at E_max); bands up to N0 keep their own energy."""
+    E_c = np.asarray(E_c, dtype=np.float64)
+    out = E_c.copy()
+    if N0 <= 0 or N0 >= E_c.size:
+        return out
+    E0 = E_c[N0 - 1]
+    k = np.floor((E_c[N0:] - E0) / dE)
+    k = np.clip(k, 0, max(np.ceil((E_max - E0) / dE - 1e-12) - 1, 0))
+    lo = E0 + k * dE
+    hi = np.minimum(lo + dE, E_max)
+    out[N0:] = 0.5 * (lo + hi)
+    return out
+
+
+def energy_substitution_estimate(plan, iq: int, M, E_v, E_c, w_col, N0: int, dE: float, E_max: float,
+                                 diag_g=None, grad_chi=None):
+    """First-order estimate of the change of a loss when every conduction band
+    above N0 is given the energy of its Eq. 4 grid point instead of its own:
+    dL ~ sum_c dL/dE_c (E_i(c) - E_c), with dL/dE_c from chi0_backward on the
+    full band sum.  Returns (estimate, grad_E_c)."""
+    n_v, n_c = int(E_v.numel()), int(E_c.numel())
+    _, _, gEc = plan.backward(iq, M, n_v, n_c, E_v, E_c, w_col, grad_chi=grad_chi, diag_g=diag_g)
+    Ei = torch.from_numpy(grid_energies_of_bands(E_c.cpu().numpy(), N0, dE, E_max)).to(E_c.device)
+    return float((gEc * (Ei - E_c)).sum()), gEc

@@ -446,6 +446,111 @@ cudaError_t try_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void* p
 #undef CHI0_FFT_CASE
 }
 
+// ---------------------------------------------------------------------------
+// Stages 1+2 for planes too large for shared memory (FP64 on large grids):
+// stage 1 runs over chunks of ROWS rows (i2) of the plane, reading the valence
+// and conduction rows of each chunk; stage 2 follows once X holds every row.
+// Shared memory: Uv[ROWS][ld3], Uc[ROWS][ld3], X[n2][nk3p].  One valence band
+// per CTA, a run of conduction bands.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_pair_planes_rows(const typename Cx<R>::T* __restrict__ psi_v, const int32_t* __restrict__ v_idx, int v0,
+                   int nv, const typename Cx<R>::T* __restrict__ psi_c, const int32_t* __restrict__ c_idx, int c0,
+                   int nc, int c_per_cta, int n1, int n2, int n3, int ld3, int rows, int nk2, int nk3, int nk2p,
+                   int nk3p, const typename Cx<R>::T* __restrict__ T2, const typename Cx<R>::T* __restrict__ T3,
+                   typename Cx<R>::T* __restrict__ D) {
+  using C = typename Cx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* Uv = reinterpret_cast<C*>(smem_raw);
+  C* Uc = Uv + (size_t)rows * ld3;
+  C* X = Uc + (size_t)rows * ld3;
+  const int i1 = blockIdx.x;
+  const int jv = blockIdx.y;
+  const int jc_begin = blockIdx.z * c_per_cta;
+  const int jc_end = min(nc, jc_begin + c_per_cta);
+  const int64_t nr = (int64_t)n1 * n2 * n3;
+  const int plane = n2 * n3;
+  const int64_t box = (int64_t)nk2 * nk3;
+  const int64_t vband = v_idx ? v_idx[v0 + jv] : v0 + jv;
+  const C* vsrc = psi_v + vband * nr + (int64_t)i1 * plane;
+  for (int jc = jc_begin; jc < jc_end; ++jc) {
+    const int64_t band = c_idx ? c_idx[c0 + jc] : c0 + jc;
+    const C* csrc = psi_c + band * nr + (int64_t)i1 * plane;
+    for (int r0 = 0; r0 < n2; r0 += rows) {
+      const int nrow = min(rows, n2 - r0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < nrow * n3; e += blockDim.x) {
+        const int r = e / n3, i3 = e - r * n3;
+        Uv[(size_t)r * ld3 + i3] = vsrc[(int64_t)(r0 + r) * n3 + i3];
+        Uc[(size_t)r * ld3 + i3] = csrc[(int64_t)(r0 + r) * n3 + i3];
+      }
+      __syncthreads();
+      // stage 1 for rows r0..r0+nrow
+      const int items1 = nrow * (nk3p >> 2);
+      for (int it = threadIdx.x; it < items1; it += blockDim.x) {
+        const int r = it % nrow, kb = (it / nrow) << 2;
+        C acc[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = cz(C());
+        const C* uv = Uv + (size_t)r * ld3;
+        const C* uc = Uc + (size_t)r * ld3;
+        for (int i3 = 0; i3 < n3; ++i3) {
+          const C rho = cconjmul(uv[i3], uc[i3]);
+          const C* t = T3 + (size_t)i3 * nk3p + kb;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cfma(acc[q], rho, __ldg(t + q));
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) X[(size_t)(r0 + r) * nk3p + kb + q] = acc[q];
+      }
+    }
+    __syncthreads();
+    // stage 2 (along i2)
+    const int items2 = nk3 * (nk2p >> 2);
+    for (int it = threadIdx.x; it < items2; it += blockDim.x) {
+      const int k3 = it % nk3, kb = (it / nk3) << 2;
+      C acc[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = cz(C());
+      for (int i2 = 0; i2 < n2; ++i2) {
+        const C x = X[(size_t)i2 * nk3p + k3];
+        const C* t = T2 + (size_t)i2 * nk2p + kb;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cfma(acc[q], x, __ldg(t + q));
+      }
+      C* dst = D + ((int64_t)(jv * nc + jc) * n1 + i1) * box + k3;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (kb + q < nk2) dst[(int64_t)(kb + q) * nk3] = acc[q];
+    }
+  }
+}
+
+template <typename R>
+cudaError_t launch_planes_rows(const chi0_plan_s* p, const SphereQ& s, const void* psi_v, const int32_t* v_idx,
+                               int v0, int nv, const void* psi_c, const int32_t* c_idx, int c0, int nc, void* D,
+                               cudaStream_t st) {
+  using C = typename Cx<R>::T;
+  const int ld3 = p->n3 | 1;
+  const size_t xbytes = (size_t)p->n2 * s.nk3p * sizeof(C);
+  const size_t cap = (size_t)200 * 1024;
+  if (xbytes + 2 * (size_t)ld3 * sizeof(C) > cap) return cudaErrorInvalidConfiguration;
+  int rows = (int)std::min<size_t>((size_t)p->n2, (cap - xbytes) / (2 * (size_t)ld3 * sizeof(C)));
+  const size_t sm = 2 * (size_t)rows * ld3 * sizeof(C) + xbytes;
+  auto kern = k_pair_planes_rows<R>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int cpc = 16;
+  while (cpc > 1 && (int64_t)p->n1 * nv * ((nc + cpc - 1) / cpc) < 4 * 152) cpc >>= 1;
+  dim3 grid(p->n1, nv, (nc + cpc - 1) / cpc);
+  const C* T2 = std::is_same<R, float>::value ? (const C*)s.T2f : (const C*)s.T2d;
+  const C* T3 = std::is_same<R, float>::value ? (const C*)s.T3f : (const C*)s.T3d;
+  kern<<<grid, kThreads, sm, st>>>((const C*)psi_v, v_idx, v0, nv, (const C*)psi_c, c_idx, c0, nc, cpc, p->n1, p->n2,
+                                   p->n3, ld3, rows, s.nk2, s.nk3, s.nk2p, s.nk3p, T2, T3, (C*)D);
+  return cudaGetLastError();
+}
+
 size_t planes_smem(int tv, int n2, int ld3, int nk3p, size_t cb) {
   return ((size_t)tv * n2 * ld3 + (size_t)n2 * ld3 + (size_t)tv * n2 * nk3p) * cb;
 }
@@ -487,7 +592,8 @@ cudaError_t launch_planes_r(const chi0_plan_s* p, const SphereQ& s, const void* 
     if (planes_smem(1, p->n2, ld3, s.nk3p, cb) <= cap)
       return launch_planes_tv<R, 1>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
   }
-  return cudaErrorInvalidConfiguration;
+  // whole planes do not fit: stage 1 over chunks of rows
+  return launch_planes_rows<R>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
 }
 
 }  // namespace

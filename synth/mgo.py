@@ -189,3 +189,34 @@ def make_problem(name: str = "custom", *, n_v=None, n_c=None, n=None, n_G=None,
         dos_A=float(A), dos_V0=V0_HA, E_max=V0_HA + WIDTH_HA,
         N0=spec.get("N0"), dE=None if dE is None else float(dE) / HARTREE_EV,
         seed=SEED_BASE + 100 * idx if seed is None else int(seed))
+
+
+def _fill_bands(args):
+    shm_name, shape, seed, stream, b0, b1 = args
+    from multiprocessing import shared_memory
+    shm = shared_memory.SharedMemory(name=shm_name)
+    try:
+        out = np.ndarray(shape, dtype=np.complex128, buffer=shm.buf)
+        out[b0:b1] = band_coefficients(seed, stream, np.arange(b0, b1), shape[1])
+    finally:
+        shm.close()
+    return b1 - b0
+
+
+def band_coefficients_parallel(seed: int, stream: int, n_bands: int, npw: int, workers: int = 0):
+    """The same coefficients as band_coefficients(seed, stream, range(n_bands), npw),
+    generated by `workers` spawned processes into shared memory.  Returns
+    (array, shm); the caller keeps shm alive while the array is in use and
+    then calls shm.close(); shm.unlink().  Call before the first CUDA call of
+    the process (the workers are spawned, not forked)."""
+    import multiprocessing as mp
+    import os
+    from multiprocessing import shared_memory
+    workers = workers or max(1, (os.cpu_count() or 2) - 1)
+    shape = (n_bands, npw)
+    shm = shared_memory.SharedMemory(create=True, size=int(np.prod(shape)) * 16)
+    step = max(1, (n_bands + 4 * workers - 1) // (4 * workers))
+    jobs = [(shm.name, shape, seed, stream, b, min(n_bands, b + step)) for b in range(0, n_bands, step)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        pool.map(_fill_bands, jobs)
+    return np.ndarray(shape, dtype=np.complex128, buffer=shm.buf), shm

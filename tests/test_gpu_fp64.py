@@ -134,3 +134,17 @@ def test_empty_inputs_are_no_ops():
                         _dev(prob.E_v[:1]), _dev(prob.E_c[:5]), chi=chi)
         plan.sync_status()
         assert float(chi.abs().max()) == 0.0
+
+
+def test_pairs_fp64_large_grid_row_chunks():
+    """96^3 grid with the 8000-vector sphere: planes do not fit shared memory in
+    FP64, so the row-chunked kernel runs."""
+    prob = make_problem("c5")
+    cv, cc = prob.coeff_v(0, np.arange(2)), prob.coeff_c(np.arange(2))
+    uv, uc = wfn_to_grid(cv, prob.gw, prob.n), wfn_to_grid(cc, prob.gw, prob.n)
+    ref = pair_elements(uv, uc, prob.gvec[0], prob.n)
+    with _plan(prob) as plan:
+        M = plan.pairs(0, plan.wfn_to_grid(_dev(cv)), plan.wfn_to_grid(_dev(cc)))
+        plan.sync_status()
+        M = M.cpu().numpy()
+    assert rel_fro(M, ref) < TOL64

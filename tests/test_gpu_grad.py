@@ -107,3 +107,32 @@ def test_autograd_matches_central_differences():
                 e[i] = h
                 fd = (fn(Ev, Ec + e) - fn(Ev, Ec - e)) / (2 * h)
                 assert abs(gc[i] - fd) <= 1e-6 * max(1.0, abs(fd))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp16"])
+def test_energy_substitution_estimate_gpu(precision):
+    """The adjoint-based first-order estimate of the energy-substitution part of
+    the accelerated sum's error, against the actual change of the loss computed
+    by two forward builds (Eq. 1 with E_c and with the grid energies)."""
+    import torch
+    from paper_1601_06767_gb300 import Chi0Plan, energy_substitution_estimate, grid_energies_of_bands
+    prob, M, Ev, Ec, w, rng = _case("c1", nv=4, nc=200, seed=5)
+    nG = M.shape[1]
+    wG = rng.uniform(0, 1, nG)
+    cdt = np.complex128 if precision == "fp64" else np.complex64
+    N0 = 40
+    with Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision=precision) as plan:
+        Md, Evd, Ecd, gd = _dev(M.astype(cdt)), _dev(Ev), _dev(Ec), _dev(wG[None])
+
+        def loss(E):
+            c = plan.accumulate(0, Md, Ev.size, Ec.size, Evd, _dev(E))
+            return float((gd[0] * torch.diagonal(c[0]).real).sum())
+
+        rows = []
+        for dE in (0.04, 0.02, 0.01):
+            est, _ = energy_substitution_estimate(plan, 0, Md, Evd, Ecd, None, N0, dE, prob.E_max, diag_g=gd)
+            Esub = grid_energies_of_bands(Ec, N0, dE, prob.E_max)
+            rows.append((abs(loss(Esub) - loss(Ec)), abs(loss(Esub) - loss(Ec) - est)))
+    for (a1, r1), (a2, r2) in zip(rows, rows[1:]):
+        assert r2 < 0.5 * r1
+    assert rows[-1][1] < 0.05 * rows[-1][0]

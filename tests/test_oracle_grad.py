@@ -56,3 +56,40 @@ def test_diagonal_loss_closed_form():
     fprime = -w / (dE + 1e-3j) ** 2
     assert np.allclose(gM, 2 * f.real[:, None] * wG[None, :] * M, rtol=1e-13, atol=1e-15)
     assert np.allclose(gd, fprime.real * (np.abs(M) ** 2 @ wG), rtol=1e-13, atol=1e-15)
+
+
+def test_first_order_energy_substitution_estimate():
+    """Giving every band above N0 the energy of its Eq. 4 grid point changes a
+    loss by sum_c dL/dE_c (E_i(c) - E_c) to first order: the residual of the
+    linear estimate falls quadratically with the step while the change itself
+    falls linearly."""
+    from oracle import select_accelerated
+    rng = np.random.default_rng(11)
+    nv, nc, ng = 3, 60, 6
+    M = (rng.standard_normal((nv * nc, ng)) + 1j * rng.standard_normal((nv * nc, ng))) / 4
+    Ev = np.linspace(-0.25, -0.02, nv)
+    Ec = np.sort(rng.uniform(0.17, 2.2, nc))
+    wG = rng.uniform(0, 1, ng)
+    Gam = np.diag(wG).astype(complex)[None]
+    N0 = 10
+
+    def loss(Ec_):
+        dE_ = (Ev[:, None] - Ec_[None, :]).reshape(-1)
+        chi = chi0_from_pairs(M, freq_factor(dE_, np.ones_like(dE_), [0.0], 1e-3))
+        return float(np.sum(wG * np.real(np.diagonal(chi[0]))))
+
+    dEp = (Ev[:, None] - Ec[None, :]).reshape(-1)
+    _, gd = chi0_grad(M, dEp, np.ones_like(dEp), np.array([0.0]), 1e-3, Gam)
+    gEc = -gd.reshape(nv, nc).sum(0)
+    out = []
+    for step in (0.08, 0.04, 0.02):
+        sel = select_accelerated(Ec, N0, step, 1.0, 0.17, 2.2)
+        k = np.clip(np.searchsorted(sel["edges"], Ec[N0:], side="right") - 1, 0, sel["E_i"].size - 1)
+        Esub = Ec.copy()
+        Esub[N0:] = sel["E_i"][k]
+        actual = loss(Esub) - loss(Ec)
+        est = float(np.sum(gEc * (Esub - Ec)))
+        out.append((abs(actual), abs(actual - est)))
+    for (a1, r1), (a2, r2) in zip(out, out[1:]):
+        assert r2 < 0.5 * r1            # residual: second order
+    assert out[-1][1] < 0.05 * out[-1][0]
