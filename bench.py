@@ -608,6 +608,142 @@ def run_c5(args):
     return 0
 
 
+def run_c3(args):
+    """Batched workload: 8 q-points (shifted 2x2x2 grid, N_G 2200-2600), 32
+    frequencies, 128 x 4000 bands, split FP16 x3; the whole build as one CUDA
+    graph with one persistent contraction launch per conduction block."""
+    import numpy as np
+    import torch
+    import paper_1601_06767_gb300 as pkg
+    from oracle import chi0_from_pairs, freq_factor, pair_elements, rel_fro, wfn_to_grid
+    from synth import make_problem
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    prob = make_problem("c3")
+    nGs = [g.shape[0] for g in prob.gvec]
+    nf = prob.omega.size
+    n_c = max(1, int(round(prob.n_c * args.c5_frac)))
+    t0 = time.time()
+    cc = _threaded_coeff(prob, 0, np.arange(n_c)).to(dev)
+    cvs = [_threaded_coeff(prob, 1 + q, np.arange(prob.n_v)).to(dev) for q in range(prob.n_q)]
+    gen_s = time.time() - t0
+    plan = pkg.Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision="fp16", gw=prob.gw, max_pairs=8192)
+    tune = plan.autotune(0)
+    psi_c = plan.wfn_to_grid(cc)
+    psi_vs = [plan.wfn_to_grid(c) for c in cvs]
+    Evs = [torch.from_numpy(prob.E_v).to(dev) for _ in range(prob.n_q)]
+    Ec = torch.from_numpy(prob.E_c[:n_c]).to(dev)
+    chis = [plan.new_chi(q) for q in range(prob.n_q)]
+    plan.build_batched(psi_vs, Evs, psi_c, Ec, chis=chis, use_graph=True)    # capture + first run
+    torch.cuda.synchronize()
+    plan.profile(True)
+    plan.profile_reset()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan.build_batched(psi_vs, Evs, psi_c, Ec, chis=chis, use_graph=True)
+    e1.record()
+    torch.cuda.synchronize()
+    plan.sync_status()
+    ms = e0.elapsed_time(e1)
+    prof = plan.profile_read()
+    F = sum(algorithmic_flops(g, prob.n_v * n_c, nf) for g in nGs)
+    # parity: 2 q-points x (2 x 4) pairs, first 300 rows, vs the oracle
+    vb, cb = np.arange(2), np.array([0, 1, n_c // 2, n_c - 1])
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    par = 0.0
+    for q in (0, prob.n_q - 1):
+        cvq, ccq = prob.coeff_v(q, vb), prob.coeff_c(cb)
+        Mr = pair_elements(wfn_to_grid(cvq, prob.gw, prob.n), wfn_to_grid(ccq, prob.gw, prob.n), prob.gvec[q], prob.n)
+        dE = (prob.E_v[vb][:, None] - prob.E_c[cb][None, :]).reshape(-1)
+        fq = freq_factor(dE, np.ones_like(dE), prob.omega, prob.delta)
+        Mg = plan.pairs(q, plan.wfn_to_grid(d(cvq)), plan.wfn_to_grid(d(ccq)))
+        cg = plan.accumulate(q, Mg, 2, 4, d(prob.E_v[vb]), d(prob.E_c[cb]))
+        torch.cuda.synchronize()
+        for i in (0, nf // 2, nf - 1):
+            ref = (Mr[:, :300].T * fq[i][None, :]) @ Mr.conj()
+            par = max(par, rel_fro(cg[i, :300].cpu().numpy(), ref))
+    line = {"case": "c3", "workload": ("batched chi0: 8 q-points on a shifted 2x2x2 grid, N_G 2200-2600, "
+                                         "32 frequencies, N_v=128, N_c=4000, grid 48^3, split FP16 x3, "
+                                         "one CUDA graph, one persistent contraction launch per block"),
+            "timed_conduction_bands": n_c, "build_s": ms / 1e3 * prob.n_c / n_c,
+            "extrapolated": n_c < prob.n_c, "effective_tflops": F / (ms / 1e3) / 1e12,
+            "tensor_tflops_contraction": 3 * F / (prof["contract_tc"][0] / 1e3) / 1e12 if prof["contract_tc"][0] else None,
+            "kernel_ms": {k: round(v[0], 2) for k, v in prof.items()},
+            "launches_per_build": sum(v[1] for v in prof.values()), "tuning": tune,
+            "parity_sample_rel_fro": par, "input_gen_s": gen_s}
+    print(json.dumps(line))
+    return 0
+
+
+def run_c4(args):
+    """Adjoint workload: L = sum_G Re(w_G chi0_GG(q, 0)), N_v=64, N_c=2000, 36^3,
+    N_G=1200: forward + backward of the split FP16 path vs the FP64 path, and
+    central finite differences (h = 1e-6 Ha) of the FP64 path."""
+    import numpy as np
+    import torch
+    import paper_1601_06767_gb300 as pkg
+    from synth import make_problem
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    prob = make_problem("c4")
+    nG = prob.gvec[0].shape[0]
+    wG = torch.from_numpy(np.random.default_rng(prob.seed + 4).uniform(0, 1, (1, nG))).to(dev)
+    cv = _threaded_coeff(prob, 1, np.arange(prob.n_v)).to(dev)
+    cc = _threaded_coeff(prob, 0, np.arange(prob.n_c)).to(dev)
+    Ev = torch.from_numpy(prob.E_v).to(dev)
+    Ec = torch.from_numpy(prob.E_c).to(dev)
+    res = {}
+    grads = {}
+    for prec in ("fp16", "fp64"):
+        plan = pkg.Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision=prec, gw=prob.gw)
+        pv, pc = plan.wfn_to_grid(cv), plan.wfn_to_grid(cc)
+        M = plan.pairs(0, pv, pc)
+        Mr = M.clone().requires_grad_(True)
+        Evr, Ecr = Ev.clone().requires_grad_(True), Ec.clone().requires_grad_(True)
+        for _ in range(2):
+            L = pkg.Chi0DiagLoss.apply(Mr, Evr, Ecr, None, wG, plan, 0)
+            gM, gEv, gEc = torch.autograd.grad(L, (Mr, Evr, Ecr))
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        L = pkg.Chi0DiagLoss.apply(Mr, Evr, Ecr, None, wG, plan, 0)
+        e1.record()
+        gM, gEv, gEc = torch.autograd.grad(L, (Mr, Evr, Ecr))
+        e2.record()
+        torch.cuda.synchronize()
+        plan.sync_status()
+        res[prec] = {"forward_ms": e0.elapsed_time(e1), "backward_ms": e1.elapsed_time(e2), "loss": float(L)}
+        grads[prec] = (gM.to(torch.complex128), gEv, gEc, float(L))
+        if prec == "fp64":
+            h = 1e-6
+            fd = []
+            for idx in (0, prob.n_v // 2, prob.n_v - 1):
+                e = torch.zeros_like(Ev)
+                e[idx] = h
+                lp = float(pkg.Chi0DiagLoss.apply(M, Ev + e, Ec, None, wG, plan, 0))
+                lm = float(pkg.Chi0DiagLoss.apply(M, Ev - e, Ec, None, wG, plan, 0))
+                fd.append(abs((lp - lm) / (2 * h) - float(gEv[idx])) / max(1.0, abs(float(gEv[idx]))))
+            for idx in (0, prob.n_c // 2, prob.n_c - 1):
+                e = torch.zeros_like(Ec)
+                e[idx] = h
+                lp = float(pkg.Chi0DiagLoss.apply(M, Ev, Ec + e, None, wG, plan, 0))
+                lm = float(pkg.Chi0DiagLoss.apply(M, Ev, Ec - e, None, wG, plan, 0))
+                fd.append(abs((lp - lm) / (2 * h) - float(gEc[idx])) / max(1.0, abs(float(gEc[idx]))))
+            res["fp64"]["fd_max_rel_err"] = max(fd)
+        del plan, pv, pc, M, Mr
+    rel = lambda a, b: float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    g16, g64 = grads["fp16"], grads["fp64"]
+    line = {"case": "c4", "workload": ("adjoint: L = sum_G Re(w_G chi0_GG(q,0)), w_G ~ U(0,1); N_v=64, N_c=2000, "
+                                         "grid 36^3, N_G=1200"),
+            "timing": res,
+            "split_vs_fp64_rel_err": {"grad_M": rel(g16[0], g64[0]), "grad_E_v": rel(g16[1], g64[1]),
+                                      "grad_E_c": rel(g16[2], g64[2]), "loss": abs(g16[3] - g64[3]) / abs(g64[3])}}
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -620,13 +756,17 @@ def main(argv=None):
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--case", choices=["contract", "pairs", "c5"], default=None,
+    ap.add_argument("--case", choices=["contract", "pairs", "c3", "c4", "c5"], default=None,
                     help="run a small fixed case for profiling (contract, pairs) or the 256-atom-sized "
                          "measurement (c5) instead of the benchmark")
     ap.add_argument("--c5-frac", type=float, default=1.0, help="fraction of conduction bands timed in --case c5")
     args = ap.parse_args(argv)
     if args.case == "c5":
         return run_c5(args)
+    if args.case == "c3":
+        return run_c3(args)
+    if args.case == "c4":
+        return run_c4(args)
     if args.case:
         return run_case(args)
     if args.impl == "reference":
