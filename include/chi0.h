@@ -176,19 +176,23 @@ chi0_status chi0_backward(chi0_plan plan, int iq, const void* M, int n_v, int n_
  * next chi0_sync_status reports CHI0_ERR_TIMEOUT and the plan stays usable. */
 chi0_status chi0_selftest_wait(chi0_plan plan, double budget_ms, void* stream);
 
-/* Autotuner of the tensor-core contraction (split plans): times the raster
- * group of the persistent work list (1, 2, 4, 8, 16 or all tile rows) and the
- * pairs per launch (2048, 4096, ... up to max_pairs) on synthetic operands
+/* Autotuner of the tensor-core contraction (split plans): times the kernel
+ * variant (single CTAs with 128 x 128 tiles, or CTA pairs sharing one
+ * tcgen05.mma.cta_group::2 over 256 x 128 tiles), the raster group of the
+ * persistent work list (1, 2, 4, 8, 16 or all tile rows) and the pairs per
+ * launch (2048, 4096, ... up to max_pairs) on synthetic operands
  * written into the plan's workspace for sphere iq (a scratch chi0 is
  * allocated and freed), keeps the fastest in the plan and appends it to the
  * text cache named by the environment variable CHI0_TUNE_CACHE (default
  * $HOME/.cache/chi0_tune.txt).  Unless flags & 1, a cached entry for the same
  * device, sphere size, frequency count, precision and products is applied
- * instead of timing; chi0_plan_create applies one for sphere 0.
+ * instead of timing; chi0_plan_create applies one for sphere 0.  Before tuning,
+ * the environment variable CHI0_TC_PAIR (0 or 1) read at plan creation selects
+ * the variant.
  * *best_us_per_pair (may be NULL) receives the best time per pair, -1 if cached.
  * Synchronises the stream. */
 chi0_status chi0_autotune(chi0_plan plan, int iq, int flags, double* best_us_per_pair, void* stream);
-chi0_status chi0_get_tuning(chi0_plan plan, int* group, int64_t* block_pairs);
+chi0_status chi0_get_tuning(chi0_plan plan, int* group, int64_t* block_pairs, int* cta_pair);
 
 /* Kernel families counted and timed by the plan's instrumentation. */
 typedef enum {

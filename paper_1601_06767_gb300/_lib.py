@@ -50,7 +50,7 @@ SIGNATURES = [
     ("chi0_backward", _I, [_VP, _I, _VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("chi0_selftest_wait", _I, [_VP, _D, _VP]),
     ("chi0_autotune", _I, [_VP, _I, _I, _VP, _VP]),
-    ("chi0_get_tuning", _I, [_VP, _VP, _VP]),
+    ("chi0_get_tuning", _I, [_VP, _VP, _VP, _VP]),
     ("chi0_profile_enable", _I, [_VP, _I]),
     ("chi0_profile_reset", _I, [_VP]),
     ("chi0_profile_read", _I, [_VP, _VP, _VP]),

@@ -104,9 +104,9 @@ class Chi0Plan:
     def autotune(self, iq: int = 0, force: bool = False) -> dict:
         best = C.c_double(0.0)
         self._check(L.lib().chi0_autotune(self._h, iq, int(force), C.byref(best), _stream()))
-        g, b = C.c_int(0), C.c_int64(0)
-        self._check(L.lib().chi0_get_tuning(self._h, C.byref(g), C.byref(b)))
-        return {"group": g.value, "block_pairs": b.value, "us_per_pair": best.value}
+        g, b, pr = C.c_int(0), C.c_int64(0), C.c_int(0)
+        self._check(L.lib().chi0_get_tuning(self._h, C.byref(g), C.byref(b), C.byref(pr)))
+        return {"group": g.value, "block_pairs": b.value, "cta_pair": pr.value, "us_per_pair": best.value}
 
     # -- instrumentation -------------------------------------------------
     def profile(self, timing: bool = True):

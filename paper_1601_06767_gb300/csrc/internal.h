@@ -83,6 +83,7 @@ struct chi0_plan_s {
   int tc_group = 8;          // tile-row group of the contraction's raster order
   int64_t block_pairs = 0;   // pairs per contraction launch (<= max_pairs); set by the autotuner
   int tc_ctas_per_sm = 1;    // persistent CTAs per SM
+  int tc_pair = 0;           // 1: CTA-pair (cta_group::2) contraction
   // instrumentation
   bool prof_timing = false;
   int64_t prof_launches[CHI0_K_COUNT] = {};

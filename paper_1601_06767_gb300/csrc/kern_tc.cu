@@ -199,12 +199,15 @@ struct Barriers {
 // to one stage and ordered smallest-first: every term product t_i t_j with
 // i + j > 0 goes in while the accumulator is still small, and the t0 t0
 // products (the only large ones) come last.
-template <bool BF16, int NT>
+template <bool BF16, int NT, bool PAIR = false>
 __device__ __forceinline__ void issue_stage(const unsigned char* st, uint32_t d_re, uint32_t d_im, bool first,
                                             int n_products) {
   constexpr int P = 2 * NT;
-  const uint32_t id_pos = tc::idesc_f16(BF16, false, BM, BN);
-  const uint32_t id_neg = tc::idesc_f16(BF16, true, BM, BN);
+  // in a CTA pair each CTA holds 128 rows of A and 64 rows of B; the MMA spans 256 rows
+  constexpr int B_BYTES = PAIR ? TILE_BYTES / 2 : TILE_BYTES;
+  const uint32_t id_pos = tc::idesc_f16(BF16, false, PAIR ? 2 * BM : BM, BN);
+  const uint32_t id_neg = tc::idesc_f16(BF16, true, PAIR ? 2 * BM : BM, BN);
+  const unsigned char* bt = st + P * TILE_BYTES;
   uint32_t acc_re = first ? 0u : 1u, acc_im = acc_re;
 #pragma unroll
   for (int order = 2 * NT - 2; order >= 0; --order) {
@@ -219,16 +222,25 @@ __device__ __forceinline__ void issue_stage(const unsigned char* st, uint32_t d_
         // planes: Re terms 0..NT-1, Im terms NT..2NT-1; K step ks is +32 bytes
         const uint64_t ar = tc::sdesc_kmajor_sw64(st + i * TILE_BYTES) + (uint64_t)(ks * 2);
         const uint64_t ai = tc::sdesc_kmajor_sw64(st + (NT + i) * TILE_BYTES) + (uint64_t)(ks * 2);
-        const uint64_t br = tc::sdesc_kmajor_sw64(st + (P + j) * TILE_BYTES) + (uint64_t)(ks * 2);
-        const uint64_t bi = tc::sdesc_kmajor_sw64(st + (P + NT + j) * TILE_BYTES) + (uint64_t)(ks * 2);
-        // Re += Wr Mr + Wi Mi
-        tc::mma_f16(d_re, ar, br, id_pos, acc_re);
-        acc_re = 1u;
-        tc::mma_f16(d_re, ai, bi, id_pos, 1u);
-        // Im += Wi Mr - Wr Mi
-        tc::mma_f16(d_im, ai, br, id_pos, acc_im);
-        acc_im = 1u;
-        tc::mma_f16(d_im, ar, bi, id_neg, 1u);
+        const uint64_t br = tc::sdesc_kmajor_sw64(bt + j * B_BYTES) + (uint64_t)(ks * 2);
+        const uint64_t bi = tc::sdesc_kmajor_sw64(bt + (NT + j) * B_BYTES) + (uint64_t)(ks * 2);
+        if constexpr (PAIR) {
+          tc::mma_f16_pair(d_re, ar, br, id_pos, acc_re);
+          acc_re = 1u;
+          tc::mma_f16_pair(d_re, ai, bi, id_pos, 1u);
+          tc::mma_f16_pair(d_im, ai, br, id_pos, acc_im);
+          acc_im = 1u;
+          tc::mma_f16_pair(d_im, ar, bi, id_neg, 1u);
+        } else {
+          // Re += Wr Mr + Wi Mi
+          tc::mma_f16(d_re, ar, br, id_pos, acc_re);
+          acc_re = 1u;
+          tc::mma_f16(d_re, ai, bi, id_pos, 1u);
+          // Im += Wi Mr - Wr Mi
+          tc::mma_f16(d_im, ai, br, id_pos, acc_im);
+          acc_im = 1u;
+          tc::mma_f16(d_im, ar, bi, id_neg, 1u);
+        }
       }
     }
   }
@@ -247,7 +259,8 @@ struct TcBatch {
   double2* chi[MAXQ];
   const double* inv[MAXQ];
   int nG[MAXQ];
-  int tiles[MAXQ];
+  int tiles_m[MAXQ];         // tiles along G (rows of chi0)
+  int tiles_n[MAXQ];         // tiles along G' (columns)
   int64_t item0[MAXQ + 1];   // first item of each q-point
   int n_q, n_freq, nK, chain_k, n_products, group;
   int64_t total_items;
@@ -260,15 +273,15 @@ __device__ __forceinline__ void decode_item(const TcBatch& P, int64_t item, int&
   q = 0;
   while (q + 1 < P.n_q && item >= P.item0[q + 1]) ++q;
   const int64_t r = item - P.item0[q];
-  const int T = P.tiles[q];
-  const int64_t tt = (int64_t)T * T;
+  const int TM = P.tiles_m[q], TN = P.tiles_n[q];
+  const int64_t tt = (int64_t)TM * TN;
   iw = (int)(r / tt);
   const int t = (int)(r - (int64_t)iw * tt);
-  const int g = min(P.group, T);
-  const int grp = t / (g * T);
+  const int g = min(P.group, TM);
+  const int grp = t / (g * TN);
   const int first = grp * g;
-  const int rows = min(g, T - first);
-  const int within = t - grp * g * T;
+  const int rows = min(g, TM - first);
+  const int within = t - grp * g * TN;
   tm = first + within % rows;
   tn = within / rows;
 }
@@ -437,6 +450,204 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
   if (warp == 1) tc::tmem_dealloc(tbase, TMEM_COLS);
 }
 
+// ---------------------------------------------------------------------------
+// CTA-pair variant: a cluster of two CTAs computes a 256 x 128 output tile with
+// tcgen05.mma.cta_group::2 (each CTA holds 128 rows of A and 64 rows of B, the
+// MMA issued by the first CTA reads both).  Shared-memory operand traffic per
+// MMA drops from 8 KB to 6 KB per CTA, which is what limits the single-CTA
+// kernel.  The first CTA's "full" barriers count the loads of both CTAs; its
+// MMA commits release both CTAs' stages and accumulators; both CTAs' epilogues
+// release the accumulators on the first CTA's "tempty" barriers.
+// ---------------------------------------------------------------------------
+constexpr int RING2_BYTES = 216 * 1024;
+constexpr size_t SMEM2_BYTES = (size_t)RING2_BYTES + 1024 + 256;
+
+template <int NT> struct Ring2 {
+  static constexpr int PLANES = 2 * NT;
+  static constexpr int A_BYTES = TILE_BYTES;          // 128 rows x 32 pairs
+  static constexpr int B_BYTES = TILE_BYTES / 2;      // 64 rows x 32 pairs
+  static constexpr int STAGE_BYTES = PLANES * (A_BYTES + B_BYTES);
+  static constexpr int STAGES = RING2_BYTES / STAGE_BYTES;   // 4 for NT = 2, 3 for NT = 3
+};
+
+template <bool BF16, int NT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
+k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
+  using RG = Ring2<NT>;
+  constexpr int STAGES = RG::STAGES, STAGE_BYTES = RG::STAGE_BYTES, PL = RG::PLANES;
+  static_assert(STAGES <= MAX_STAGES + 1, "barrier array too small");
+  extern __shared__ __align__(1024) unsigned char smem_tc2[];
+  unsigned char* tiles = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_tc2) + 1023) & ~uintptr_t(1023));
+  struct Bars {
+    uint64_t full[4], empty[4], tfull[2], tempty[2], done;
+    uint32_t tmem_base;
+  };
+  Bars* bar = reinterpret_cast<Bars*>(tiles + RING2_BYTES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = tc::cluster_rank();
+  const bool leader = rank == 0;
+  const int64_t pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+  const int nK = P.nK, chain_k = P.chain_k;
+  const int nchains = (nK + chain_k - 1) / chain_k;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&bar->full[s], 1);
+      tc::mbar_init(&bar->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&bar->tfull[b], 1);
+      tc::mbar_init(&bar->tempty[b], 2 * EPI_WARPS);
+    }
+    tc::mbar_init(&bar->done, 1);
+    tc::fence_mbar_init();
+    for (int q = 0; q < P.n_q; ++q) {
+      tc::prefetch_tmap(&P.tmA[q]);
+      tc::prefetch_tmap(&P.tmB[q]);
+    }
+  }
+  if (warp == 1) {
+    tc::tmem_alloc_pair(&bar->tmem_base, TMEM_COLS);
+    tc::tmem_relinquish_pair();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::cluster_sync();      // barriers of both CTAs initialised before any remote use
+  tc::fence_after();
+  const uint32_t tbase = bar->tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer (both CTAs) ----------------
+      int64_t gs = 0;
+      bool ok = true;
+      for (int64_t item = pair; item < P.total_items && ok; item += npairs) {
+        int q, iw, tm, tn;
+        decode_item(P, item, q, iw, tm, tn);
+        const int arow = tm * 2 * BM + (int)rank * BM;     // this CTA's 128 rows of A
+        const int brow = tn * BN + (int)rank * (BN / 2);   // this CTA's 64 rows of B
+        for (int kc = 0; kc < nK; ++kc, ++gs) {
+          const int s = (int)(gs % STAGES);
+          const uint32_t u = (uint32_t)(gs / STAGES);
+          if (!tc::mbar_wait(&bar->empty[s], (u & 1) ^ 1, status, 1, WAIT_BUDGET_NS)) { ok = false; break; }
+          if (leader) tc::mbar_arrive_expect_tx(&bar->full[s], 2 * STAGE_BYTES);
+          const uint32_t fb = tc::mapa(&bar->full[s], 0);
+          unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
+#pragma unroll
+          for (int j = 0; j < PL; ++j)
+            tc::tma_load_3d_pair(st + j * RG::A_BYTES, &P.tmA[q], fb, kc * BK, arow, iw * PL + j);
+#pragma unroll
+          for (int j = 0; j < PL; ++j)
+            tc::tma_load_3d_pair(st + PL * RG::A_BYTES + j * RG::B_BYTES, &P.tmB[q], fb, kc * BK, brow, j);
+        }
+      }
+      // copies of this CTA still in flight land before it may exit: wait until the
+      // pair's MMA has released the stages it issued last
+      for (int64_t g = max((int64_t)0, gs - STAGES); g < gs; ++g)
+        tc::mbar_wait(&bar->empty[g % STAGES], (uint32_t)((g / STAGES) & 1), status, 1, WAIT_BUDGET_NS);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && leader) {
+      // ---------------- MMA issuer (first CTA of the pair) ----------------
+      int64_t gs = 0, gc = 0;
+      bool ok = true;
+      for (int64_t item = pair; item < P.total_items && ok; item += npairs) {
+        for (int kc = 0; kc < nK; ++kc, ++gs) {
+          const int buf = (int)(gc & 1);
+          const bool first = (kc % chain_k) == 0;
+          if (first) {
+            if (!tc::mbar_wait(&bar->tempty[buf], (uint32_t)(((gc >> 1) & 1) ^ 1), status, 1, WAIT_BUDGET_NS)) {
+              ok = false;
+              break;
+            }
+            tc::fence_after();
+          }
+          const int s = (int)(gs % STAGES);
+          if (!tc::mbar_wait(&bar->full[s], (uint32_t)((gs / STAGES) & 1), status, 1, WAIT_BUDGET_NS)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after();
+          const unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
+          const uint32_t d_re = tbase + buf * 256, d_im = d_re + 128;
+          issue_stage<BF16, NT, true>(st, d_re, d_im, first, P.n_products);
+          tc::mma_commit_pair(&bar->empty[s], 0x3);
+          if ((kc % chain_k) == chain_k - 1 || kc == nK - 1) {
+            tc::mma_commit_pair(&bar->tfull[buf], 0x3);
+            ++gc;
+          }
+        }
+      }
+      tc::mma_commit_pair(&bar->done, 0x1);
+      tc::mbar_wait(&bar->done, 0, status, 1, WAIT_BUDGET_NS);
+    }
+  } else {
+    // ---------------- epilogue (both CTAs, own 128 rows) ----------------
+    const int ew = warp - 2, quad = warp & 3, half = ew >> 2;
+    const int row = quad * 32 + lane;
+    int64_t gc = 0;
+    bool ok = true;
+    for (int64_t item = pair; item < P.total_items && ok; item += npairs) {
+      int q, iw, tm, tn;
+      decode_item(P, item, q, iw, tm, tn);
+      float sre[64], sim[64];
+#pragma unroll
+      for (int i = 0; i < 64; ++i) { sre[i] = 0.f; sim[i] = 0.f; }
+      for (int c = 0; c < nchains; ++c, ++gc) {
+        const int buf = (int)(gc & 1);
+        if (!tc::mbar_wait(&bar->tfull[buf], (uint32_t)((gc >> 1) & 1), status, 1, WAIT_BUDGET_NS)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after();
+        const uint32_t ta = tbase + ((uint32_t)(quad * 32) << 16) + buf * 256 + half * 64;
+        float v[32];
+        tc::tmem_ld32(ta, v);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) sre[i] += v[i];
+        tc::tmem_ld32(ta + 32, v);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) sre[32 + i] += v[i];
+        tc::tmem_ld32(ta + 128, v);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) sim[i] += v[i];
+        tc::tmem_ld32(ta + 160, v);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) sim[32 + i] += v[i];
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive_cluster(tc::mapa(&bar->tempty[buf], 0));
+      }
+      const int nG = P.nG[q];
+      const int G = tm * 2 * BM + (int)rank * BM + row;
+      if (ok && G < nG) {
+        const double sc = P.inv[q][iw];
+        const int Hb = tn * BN + half * 64;
+        double2* out = P.chi[q] + ((size_t)iw * nG + G) * nG + Hb;
+#pragma unroll
+        for (int i = 0; i < 64; ++i) {
+          if (Hb + i < nG) {
+            double2 o = out[i];
+            o.x += (double)sre[i] * sc;
+            o.y += (double)sim[i] * sc;
+            out[i] = o;
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::cluster_sync();      // neither CTA leaves while the pair's MMAs may still read its operands
+  tc::fence_after();
+  if (warp == 1) tc::tmem_dealloc_pair(tbase, TMEM_COLS);
+}
+
 // Diagnostic: wait on an mbarrier that nothing arrives on, with the same
 // bounded wait as the contraction, so the time-out path can be exercised.
 __global__ void k_wait_selftest(uint64_t budget_ns, int* status) {
@@ -466,10 +677,11 @@ bool resolve_encoder(std::string* why) {
   return true;
 }
 
-bool encode_planes(CUtensorMap* tm, void* base, bool bf16, int Kp, int nGp, int planes, std::string* why) {
+bool encode_planes(CUtensorMap* tm, void* base, bool bf16, int Kp, int nGp, int planes, std::string* why,
+                   int box_rows = BM) {
   cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)nGp, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * nGp};
-  cuuint32_t box[3] = {BK, BM, 1};
+  cuuint32_t box[3] = {BK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
@@ -506,7 +718,7 @@ bool tc_supported(std::string* why) {
 int n_terms(const chi0_plan_s* p) { return p->n_products == 6 ? 3 : 2; }
 
 size_t tc_pack_bytes(const chi0_plan_s* p, int64_t max_pairs, int max_nG) {
-  const size_t nGp = (size_t)round_up_i(max_nG, BM);
+  const size_t nGp = (size_t)round_up_i(max_nG, 2 * BM);
   const size_t Kp = (size_t)((max_pairs + 63) / 64 * 64);
   const size_t planes = 2 * (size_t)n_terms(p) * (1 + (size_t)p->n_freq);
   const size_t scal = 256 + 32 * (size_t)(p->n_freq + 1);   // amax, scales, inverse scales
@@ -523,7 +735,7 @@ struct PackWs {
 };
 
 static PackWs pack_ws(const chi0_plan_s* p, void* base, int nGp, int Kp) {
-  const size_t planes_ws = 2 * (size_t)n_terms(p) * (1 + (size_t)p->n_freq) * (size_t)round_up_i(p->max_nG, BM) *
+  const size_t planes_ws = 2 * (size_t)n_terms(p) * (1 + (size_t)p->n_freq) * (size_t)round_up_i(p->max_nG, 2 * BM) *
                            (size_t)((p->max_pairs + 63) / 64 * 64) * 2;
   PackWs w;
   w.Bp = reinterpret_cast<uint16_t*>(base);
@@ -559,23 +771,25 @@ static cudaError_t run_tc(chi0_plan_s* p, const TcJob* jobs, int n_jobs, int64_t
   TcBatch* P = new TcBatch();
   memset(P, 0, sizeof(TcBatch));
   int64_t items = 0;
+  const bool pair = p->tc_pair != 0;
   for (int j = 0; j < n_jobs; ++j) {
     const TcJob& jb = jobs[j];
-    const int nGp = round_up_i(jb.nG, BM);
+    const int nGp = round_up_i(jb.nG, pair ? 2 * BM : BM);
     PackWs w = pack_ws(p, jb.pack, nGp, Kp);
     cudaError_t e = pack_one<BF16, NT>(p, jb.nG, jb.M, K, jb.f, w, nGp, Kp, s);
     if (e != cudaSuccess) { delete P; return e; }
-    if (!encode_planes(&P->tmB[j], w.Bp, BF16, Kp, nGp, 2 * NT, why) ||
-        !encode_planes(&P->tmA[j], w.Ap, BF16, Kp, nGp, 2 * NT * p->n_freq, why)) {
+    if (!encode_planes(&P->tmB[j], w.Bp, BF16, Kp, nGp, 2 * NT, why, pair ? BN / 2 : BN) ||
+        !encode_planes(&P->tmA[j], w.Ap, BF16, Kp, nGp, 2 * NT * p->n_freq, why, BM)) {
       delete P;
       return cudaErrorInvalidValue;
     }
     P->chi[j] = jb.chi;
     P->inv[j] = w.inv;
     P->nG[j] = jb.nG;
-    P->tiles[j] = nGp / BM;
+    P->tiles_m[j] = nGp / (pair ? 2 * BM : BM);
+    P->tiles_n[j] = nGp / BN;
     P->item0[j] = items;
-    items += (int64_t)(nGp / BM) * (nGp / BM) * p->n_freq;
+    items += (int64_t)P->tiles_m[j] * P->tiles_n[j] * p->n_freq;
   }
   P->item0[n_jobs] = items;
   P->n_q = n_jobs;
@@ -585,14 +799,22 @@ static cudaError_t run_tc(chi0_plan_s* p, const TcJob* jobs, int n_jobs, int64_t
   P->n_products = p->n_products;
   P->group = p->tc_group > 0 ? p->tc_group : 8;
   P->total_items = items;
-  cudaError_t e = cudaFuncSetAttribute(k_contract_tc<BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)SMEM_BYTES);
-  if (e != cudaSuccess) { delete P; return e; }
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = (int)std::min<int64_t>(items, (int64_t)nsm * std::max(1, p->tc_ctas_per_sm));
-  {
+  cudaError_t e;
+  if (pair) {
+    e = cudaFuncSetAttribute(k_contract_tc2<BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM2_BYTES);
+    if (e != cudaSuccess) { delete P; return e; }
+    const int pairs = (int)std::min<int64_t>(items, (int64_t)(nsm / 2));
+    ProfScope ps(p, CHI0_K_CONTRACT_TC, s, 1);
+    k_contract_tc2<BF16, NT><<<2 * pairs, THREADS, SMEM2_BYTES, s>>>(*P, p->d_status);
+  } else {
+    e = cudaFuncSetAttribute(k_contract_tc<BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES);
+    if (e != cudaSuccess) { delete P; return e; }
+    const int grid = (int)std::min<int64_t>(items, (int64_t)nsm * std::max(1, p->tc_ctas_per_sm));
     ProfScope ps(p, CHI0_K_CONTRACT_TC, s, 1);
     k_contract_tc<BF16, NT><<<grid, THREADS, SMEM_BYTES, s>>>(*P, p->d_status);
   }

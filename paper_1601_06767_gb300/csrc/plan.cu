@@ -370,7 +370,11 @@ chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* d) {
       p->ws_bytes += bytes_M + bytes_f + p->pack_bytes;
     }
   }
-  if (chi0::is_split(p)) chi0::tune_apply_cached(p, 0);
+  if (chi0::is_split(p)) {
+    const char* pe = getenv("CHI0_TC_PAIR");   // contraction variant: CTA pairs (1) or single CTAs (0)
+    if (pe && *pe) p->tc_pair = atoi(pe) != 0;
+    chi0::tune_apply_cached(p, 0);
+  }
   *out = p;
   return CHI0_OK;
 }

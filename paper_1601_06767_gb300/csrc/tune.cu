@@ -64,11 +64,13 @@ bool tune_apply_cached(chi0_plan_s* p, int iq) {
   bool hit = false;
   while (fgets(line, sizeof(line), fh)) {
     if (strncmp(line, key.c_str(), key.size()) != 0 || line[key.size()] != ' ') continue;
-    int g = 0;
+    int g = 0, pr = 0;
     long long b = 0;
-    if (sscanf(line + key.size(), " group=%d block=%lld", &g, &b) == 2 && g > 0 && b > 0 && b <= p->max_pairs) {
+    if (sscanf(line + key.size(), " group=%d block=%lld pair=%d", &g, &b, &pr) == 3 && g > 0 && b > 0 &&
+        b <= p->max_pairs) {
       p->tc_group = g;
       p->block_pairs = b;
+      p->tc_pair = pr != 0;
       hit = true;   // the last matching line wins
     }
   }
@@ -126,12 +128,15 @@ extern "C" chi0_status chi0_autotune(chi0_plan p, int iq, int flags, double* bes
   if (blocks.empty() || blocks.back() != Kmax) blocks.push_back(Kmax);
   const int saved_group = p->tc_group;
   const int64_t saved_block = p->block_pairs;
+  const int saved_pair = p->tc_pair;
   double best = 1e30;
-  int best_g = saved_group;
+  int best_g = saved_group, best_pair = saved_pair;
   int64_t best_b = saved_block;
   std::string why;
+  for (int pair = 0; pair < 2; ++pair)
   for (int64_t b : blocks)
     for (int g : groups) {
+      p->tc_pair = pair;
       p->tc_group = g;
       p->block_pairs = b;
       const int nc = (int)(b / nv);
@@ -153,6 +158,7 @@ extern "C" chi0_status chi0_autotune(chi0_plan p, int iq, int flags, double* bes
         best = us;
         best_g = g;
         best_b = b;
+        best_pair = pair;
       }
     }
   p->prof_timing = timing;
@@ -161,6 +167,7 @@ extern "C" chi0_status chi0_autotune(chi0_plan p, int iq, int flags, double* bes
   cudaFree(chi);
   p->tc_group = best_g;
   p->block_pairs = best_b;
+  p->tc_pair = best_pair;
   if (best_us_per_pair) *best_us_per_pair = best;
   if (best < 1e30) {
     const std::string path = cache_path();
@@ -168,16 +175,18 @@ extern "C" chi0_status chi0_autotune(chi0_plan p, int iq, int flags, double* bes
     if (slash != std::string::npos && slash > 0) mkdir_one(path.substr(0, slash));   // one level
     FILE* fh = fopen(path.c_str(), "a");
     if (fh) {
-      fprintf(fh, "%s group=%d block=%lld us_per_pair=%.6f\n", key_of(p, iq).c_str(), best_g, (long long)best_b, best);
+      fprintf(fh, "%s group=%d block=%lld pair=%d us_per_pair=%.6f\n", key_of(p, iq).c_str(), best_g,
+              (long long)best_b, best_pair, best);
       fclose(fh);
     }
   }
   return CHI0_OK;
 }
 
-extern "C" chi0_status chi0_get_tuning(chi0_plan p, int* group, int64_t* block_pairs) {
+extern "C" chi0_status chi0_get_tuning(chi0_plan p, int* group, int64_t* block_pairs, int* cta_pair) {
   if (!p) return CHI0_ERR_INVALID;
   if (group) *group = p->tc_group;
   if (block_pairs) *block_pairs = p->block_pairs;
+  if (cta_pair) *cta_pair = p->tc_pair;
   return CHI0_OK;
 }

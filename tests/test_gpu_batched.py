@@ -64,6 +64,7 @@ def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
     with Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision="fp16", max_pairs=8192) as plan:
         t = plan.autotune(0, force=True)
         assert t["group"] in (1, 2, 4, 8, 16) and 0 < t["block_pairs"] <= 8192 and t["us_per_pair"] > 0
+        assert t["cta_pair"] in (0, 1)
         # the tuned plan still computes Eq. 1
         rng = np.random.default_rng(2)
         M = (rng.standard_normal((4 * 40, 350)) + 1j * rng.standard_normal((4 * 40, 350))) * 0.02
@@ -77,4 +78,4 @@ def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
     with Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision="fp16", max_pairs=8192) as plan2:
         t2 = plan2.autotune(0)          # served from the cache
         assert t2["us_per_pair"] == -1.0
-        assert (t2["group"], t2["block_pairs"]) == (t["group"], t["block_pairs"])
+        assert (t2["group"], t2["block_pairs"], t2["cta_pair"]) == (t["group"], t["block_pairs"], t["cta_pair"])

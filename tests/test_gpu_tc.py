@@ -111,3 +111,19 @@ def test_build_accelerated_bf16():
                          c_idx=_dev(c_idx.astype(np.int32))).cpu().numpy()
     for iw in range(prob.omega.size):
         assert rel_fro(chi[iw], ref[iw]) < TOL
+
+
+@pytest.mark.parametrize("precision,n_products", [("fp16", 3), ("bf16", 6)])
+def test_cta_pair_variant_matches_eq1(precision, n_products, monkeypatch):
+    """The CTA-pair contraction (tcgen05.mma.cta_group::2, 256 x 128 tiles) on a
+    ragged sphere (N_G = 350 is not a multiple of 256) with several pair blocks."""
+    monkeypatch.setenv("CHI0_TC_PAIR", "1")
+    prob, cv, cc, uv, uc, M = _c1_pairs(n_imag=2)
+    nv, nc = prob.n_v, prob.n_c
+    dE = (prob.E_v[:, None] - prob.E_c[None, :]).reshape(-1)
+    ref = chi0_from_pairs(M, freq_factor(dE, np.ones_like(dE), prob.omega, prob.delta))
+    with _plan(prob, precision=precision, n_products=n_products, max_pairs=1024) as plan:
+        chi = plan.accumulate(0, _dev(M.astype(np.complex64)), nv, nc, _dev(prob.E_v), _dev(prob.E_c))
+        plan.sync_status()
+        chi = chi.cpu().numpy()
+    assert max(rel_fro(chi[i], ref[i]) for i in range(prob.omega.size)) < TOL
