@@ -207,7 +207,9 @@ __device__ __forceinline__ void issue_stage(const unsigned char* st, uint32_t d_
   constexpr int B_BYTES = PAIR ? TILE_BYTES / 2 : TILE_BYTES;
   const uint32_t id_pos = tc::idesc_f16(BF16, false, PAIR ? 2 * BM : BM, BN);
   const uint32_t id_neg = tc::idesc_f16(BF16, true, PAIR ? 2 * BM : BM, BN);
-  const unsigned char* bt = st + P * TILE_BYTES;
+  // one descriptor for the stage; tiles and K steps are constant offsets of its address field
+  const uint64_t d0 = tc::sdesc_kmajor_sw64(st);
+  constexpr uint64_t kTile = TILE_BYTES >> 4, kBTile = B_BYTES >> 4, kB0 = (uint64_t)(P * TILE_BYTES) >> 4;
   uint32_t acc_re = first ? 0u : 1u, acc_im = acc_re;
 #pragma unroll
   for (int order = 2 * NT - 2; order >= 0; --order) {
@@ -220,10 +222,10 @@ __device__ __forceinline__ void issue_stage(const unsigned char* st, uint32_t d_
         const bool keep = (i + j < NT) || (NT == 2 && n_products == 4 && i == 1 && j == 1);
         if (!keep) continue;
         // planes: Re terms 0..NT-1, Im terms NT..2NT-1; K step ks is +32 bytes
-        const uint64_t ar = tc::sdesc_kmajor_sw64(st + i * TILE_BYTES) + (uint64_t)(ks * 2);
-        const uint64_t ai = tc::sdesc_kmajor_sw64(st + (NT + i) * TILE_BYTES) + (uint64_t)(ks * 2);
-        const uint64_t br = tc::sdesc_kmajor_sw64(bt + j * B_BYTES) + (uint64_t)(ks * 2);
-        const uint64_t bi = tc::sdesc_kmajor_sw64(bt + (NT + j) * B_BYTES) + (uint64_t)(ks * 2);
+        const uint64_t ar = d0 + (uint64_t)i * kTile + (uint64_t)(ks * 2);
+        const uint64_t ai = d0 + (uint64_t)(NT + i) * kTile + (uint64_t)(ks * 2);
+        const uint64_t br = d0 + kB0 + (uint64_t)j * kBTile + (uint64_t)(ks * 2);
+        const uint64_t bi = d0 + kB0 + (uint64_t)(NT + j) * kBTile + (uint64_t)(ks * 2);
         if constexpr (PAIR) {
           tc::mma_f16_pair(d_re, ar, br, id_pos, acc_re);
           acc_re = 1u;

@@ -127,3 +127,23 @@ def test_cta_pair_variant_matches_eq1(precision, n_products, monkeypatch):
         plan.sync_status()
         chi = chi.cpu().numpy()
     assert max(rel_fro(chi[i], ref[i]) for i in range(prob.omega.size)) < TOL
+
+
+@pytest.mark.parametrize("nG,nv,nc,pair", [(57, 1, 1, "0"), (128, 1, 33, "0"), (256, 2, 31, "1"), (257, 3, 5, "1"),
+                                          (57, 1, 1, "1")])
+def test_tc_edge_shapes(nG, nv, nc, pair, monkeypatch):
+    """Single pairs, sphere sizes below, at and just above the tile sizes, pair
+    counts that are not multiples of the 32-pair stage, both kernel variants."""
+    monkeypatch.setenv("CHI0_TC_PAIR", pair)
+    prob = make_problem("c1", n_G=[nG], n_imag=1)
+    rng = np.random.default_rng(nG + nv + nc)
+    M = (rng.standard_normal((nv * nc, nG)) + 1j * rng.standard_normal((nv * nc, nG))) * 0.02
+    Ev, Ec = prob.E_v[:nv], prob.E_c[:nc]
+    dE = (Ev[:, None] - Ec[None, :]).reshape(-1)
+    ref = chi0_from_pairs(M, freq_factor(dE, np.ones_like(dE), prob.omega, prob.delta))
+    for prec in ("fp16", "bf16"):
+        with _plan(prob, precision=prec, max_pairs=64) as plan:
+            chi = plan.accumulate(0, _dev(M.astype(np.complex64)), nv, nc, _dev(Ev), _dev(Ec))
+            plan.sync_status()
+            chi = chi.cpu().numpy()
+        assert max(rel_fro(chi[i], ref[i]) for i in range(2)) < TOL, (prec, nG, nv, nc)
