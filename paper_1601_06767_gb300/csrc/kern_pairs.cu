@@ -599,6 +599,18 @@ cudaError_t launch_planes_r(const chi0_plan_s* p, const SphereQ& s, const void* 
 }  // namespace
 
 cudaError_t launch_wfn_to_grid(const chi0_plan_s* p, const double2* coeff, int nb, void* psi, cudaStream_t s) {
+  // grid.y is limited to 65535 bands per launch
+  constexpr int kMaxY = 65535;
+  if (nb > kMaxY) {
+    const size_t cbw = is_split(p) ? sizeof(float2) : sizeof(double2);
+    for (int b0 = 0; b0 < nb; b0 += kMaxY) {
+      const int n = std::min(kMaxY, nb - b0);
+      cudaError_t e = launch_wfn_to_grid(p, coeff + (size_t)b0 * p->w.npw, n,
+                                         (char*)psi + (size_t)b0 * p->nr * cbw, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   const WfnSphere& w = p->w;
   dim3 grid(p->n1, nb);
   if (is_split(p)) {

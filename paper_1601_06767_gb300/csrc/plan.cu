@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 using chi0::SphereQ;
@@ -219,7 +221,12 @@ static cudaEvent_t pool_get(chi0_plan_s* p) {
   return e;
 }
 
+static const char* const kFamilyNames[CHI0_K_COUNT] = {"chi0.wfn_to_grid", "chi0.pair_planes", "chi0.pair_gather",
+                                                       "chi0.weights", "chi0.pack", "chi0.contract_tc",
+                                                       "chi0.contract_f64"};
+
 ProfScope::ProfScope(chi0_plan_s* plan, int kernel, cudaStream_t st, int launches) : p(plan), k(kernel), s(st) {
+  nvtxRangePushA(kFamilyNames[k]);   // host-side range around the launches (visible to nsys / ncu)
   p->prof_launches[k] += launches;
   if (p->prof_timing) {
     e1 = pool_get(p);
@@ -228,6 +235,7 @@ ProfScope::ProfScope(chi0_plan_s* plan, int kernel, cudaStream_t st, int launche
 }
 
 ProfScope::~ProfScope() {
+  nvtxRangePop();
   if (!e1) return;
   cudaEvent_t e2 = pool_get(p);
   if (!e2) {
