@@ -32,6 +32,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -169,6 +171,18 @@ def algorithmic_flops(nG: int, n_pairs: int, n_freq: int) -> float:
 # ---------------------------------------------------------------------------
 # the oracle on host cores (cpu_baseline / reference arm)
 # ---------------------------------------------------------------------------
+def h2_products(Ev, Ec, omega, delta, n_prod):
+    """Products of the H2 part per frequency in Hermitian mode: three where
+    |Im f_p| <= 2^-6 |Re f_p| for every pair (then the block maxima the library
+    compares satisfy the same bound), otherwise n_prod (an upper bound)."""
+    dE = (np.asarray(Ev)[:, None] - np.asarray(Ec)[None, :]).reshape(-1)
+    out = []
+    for om in np.atleast_1d(omega):
+        f = 1.0 / (dE - om + 1j * delta) + 1.0 / (dE + om + 1j * delta)
+        out.append(3 if np.all(np.abs(f.imag) <= np.abs(f.real) * 2.0 ** -6) else n_prod)
+    return np.array(out)
+
+
 def oracle_sample(prob, nv: int, nc: int, seed_offset: int = 0):
     """Time the FP64 oracle on nv x nc pairs of the workload (wavefunctions,
     pair elements, factors, contraction).  Returns (seconds, flops, chi, bands)."""
@@ -241,8 +255,9 @@ def run_ours(args):
     cv, cc = cv_h.to(dev), cc_h.to(dev)
     Ev, Ec = Ev_h.to(dev), Ec_h.to(dev)
 
+    herm = {"auto": None, "on": True, "off": False}[args.hermitian]
     plan = pkg.Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision=args.precision, gw=prob.gw,
-                        n_products=args.n_products)
+                        n_products=args.n_products, hermitian=herm)
     tuning = plan.autotune(0)
     psi_v = torch.empty((prob.n_v,) + plan.n, dtype=plan.cdtype, device=dev)
     psi_c = torch.empty((prob.n_c,) + plan.n, dtype=plan.cdtype, device=dev)
@@ -388,10 +403,19 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (tensor-core contraction) ----
     pk, pk_kind = peaks()
     n_prod = {"fp16": 3, "bf16": 6}[args.precision] if args.n_products == 0 else args.n_products
+    hermitian = plan.hermitian
     tc_ms, tc_n = prof["contract_tc"]
+    nG = prob.gvec[0].shape[0]
+    if hermitian:
+        # H1 (n_prod products) and H2 (3 products where max|Im f| <= 2^-6 max|Re f|,
+        # which holds pair by pair here, so in every block) on the G <= G' triangle
+        n2 = h2_products(prob.E_v, prob.E_c, prob.omega, prob.delta, n_prod)
+        tensor_flops_total = (4.0 * nG * (nG + 1) * n_pairs * (n_prod + n2)).sum() * args.steps
+    else:
+        n2 = None
+        tensor_flops_total = n_prod * F * args.steps
     # every launch contracts one block of pairs; summed over the timed steps this is
     # (tensor flops per launch x launches) / (average launch time x launches)
-    tensor_flops_total = n_prod * F * args.steps
     avg_launch_s = tc_ms / 1e3 / max(tc_n, 1)
     tensor_flops_launch = tensor_flops_total / max(tc_n, 1)
     ach = tensor_flops_launch / avg_launch_s / 1e12
@@ -400,7 +424,8 @@ def run_ours(args):
     roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
             "traffic": traffic, "kernel": "k_contract_tc", "peak_source": f"{pk_kind} bf16_tflops_sustained",
             "flops_per_launch": tensor_flops_launch, "launches": tc_n,
-            "algorithmic_tflops": ach / n_prod}
+            "algorithmic_tflops": F * args.steps / max(tc_n, 1) / avg_launch_s / 1e12,
+            "hermitian": hermitian, "h2_products": None if n2 is None else [int(x) for x in n2]}
     kernel_ms = {k: round(v[0] / args.steps, 3) for k, v in prof.items()}
 
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -408,7 +433,8 @@ def run_ours(args):
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": WORKLOAD, "pairs": n_pairs, "n_freq": nf,
                        "precision": f"{args.precision} split x{n_prod} products, FP32 TMEM chains of "
-                                    f"32 pairs, FP64 factors and merge",
+                                    f"32 pairs, FP64 factors and merge"
+                                    + ("; Hermitian parts H1 + i H2 on the upper triangle" if hermitian else ""),
                        "l2": "no flush: resident inputs (6.6 GB) exceed the 129 MB L2",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "kernel_ms_per_step": kernel_ms, "gpu_launches": launches,
@@ -756,6 +782,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["bf16", "fp16"], default="bf16")
     ap.add_argument("--n-products", type=int, default=0)
+    ap.add_argument("--hermitian", choices=["auto", "on", "off"], default="auto")
     ap.add_argument("--fp64-sample", type=int, default=32)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -30,6 +30,7 @@ class Chi0PlanDesc(C.Structure):
         ("n_products", C.c_int),
         ("max_pairs", C.c_int64),
         ("chain_pairs", C.c_int),
+        ("hermitian", C.c_int),
     ]
 
 

@@ -33,7 +33,8 @@ class Chi0Plan:
     """A chi0 plan on the current CUDA device (see chi0_plan_create)."""
 
     def __init__(self, n, gvecs, omega, delta: float, precision: str = "fp64", gw=None,
-                 n_products: int = 0, max_pairs: int = 0, chain_pairs: int = 0):
+                 n_products: int = 0, max_pairs: int = 0, chain_pairs: int = 0,
+                 hermitian: bool | None = None):
         lib = L.lib()
         n1, n2, n3 = (n, n, n) if np.isscalar(n) else tuple(int(x) for x in n)
         self.n = (n1, n2, n3)
@@ -63,6 +64,10 @@ class Chi0Plan:
         d.n_products = int(n_products)
         d.max_pairs = int(max_pairs)
         d.chain_pairs = int(chain_pairs)
+        d.hermitian = 0 if hermitian is None else (1 if hermitian else -1)
+        # the library's rule: split precisions only; automatic means on for six products
+        eff_np = int(n_products) or (3 if precision == "fp16" else 6)
+        self.hermitian = precision != "fp64" and (bool(hermitian) if hermitian is not None else eff_np == 6)
         h = C.c_void_p()
         L.check(lib.chi0_plan_create(C.byref(h), C.byref(d)), None)
         self._h = h

@@ -84,6 +84,7 @@ struct chi0_plan_s {
   int64_t block_pairs = 0;   // pairs per contraction launch (<= max_pairs); set by the autotuner
   int tc_ctas_per_sm = 1;    // persistent CTAs per SM
   int tc_pair = 0;           // 1: CTA-pair (cta_group::2) contraction
+  bool tc_herm = false;      // contract the Hermitian parts H1, H2 on upper-triangle tiles
   // instrumentation
   bool prof_timing = false;
   int64_t prof_launches[CHI0_K_COUNT] = {};

@@ -16,6 +16,14 @@
 //           double-buffered TMEM accumulator pairs (Re, Im), warps 2..9 drain
 //           finished accumulation chains into FP32 registers and finally add
 //           the tile into chi0 in FP64.
+//
+// Hermitian mode: chi0 = H1 + i H2 with H1 = sum Re(f) M M^H, H2 = sum Im(f) M M^H,
+// both Hermitian.  A item then contracts W1 = Re(f) M and W2 = Im(f) M (two
+// parts, each with its own power-of-two scale) for one tile on or above the
+// diagonal, adds the elements with G <= G' and writes the conjugate transpose
+// of those with G < G' into the lower triangle.  H2 is the small part
+// (|Im f| / |Re f| <= delta / |E_v - E_c| on the imaginary axis), so it takes
+// three products (two terms) when its weights are below 2^-6 of H1's.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -79,7 +87,8 @@ __device__ __forceinline__ void splitn(float a, float b, uint32_t (&w)[NT]) {
   }
 }
 
-// largest |component| of the M block -> amax[0]; of f(w) -> amax[1 + w]
+// largest |component| of the M block -> amax[0]; largest |Re f(w)| -> amax[1 + 2w],
+// largest |Im f(w)| -> amax[2 + 2w]
 __global__ void k_absmax(const float2* __restrict__ M, int64_t n, const double2* __restrict__ f, int64_t K,
                          int n_freq, unsigned int* __restrict__ amax) {
   float m = 0.f;
@@ -90,13 +99,20 @@ __global__ void k_absmax(const float2* __restrict__ M, int64_t n, const double2*
   for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(amax, __float_as_uint(m));
   for (int iw = 0; iw < n_freq; ++iw) {
-    float g = 0.f;
+    float gr = 0.f, gi = 0.f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x) {
       const double2 v = f[(int64_t)iw * K + i];
-      g = fmaxf(g, (float)fmax(fabs(v.x), fabs(v.y)));
+      gr = fmaxf(gr, (float)fabs(v.x));
+      gi = fmaxf(gi, (float)fabs(v.y));
     }
-    for (int o = 16; o; o >>= 1) g = fmaxf(g, __shfl_xor_sync(0xffffffffu, g, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(amax + 1 + iw, __float_as_uint(g));
+    for (int o = 16; o; o >>= 1) {
+      gr = fmaxf(gr, __shfl_xor_sync(0xffffffffu, gr, o));
+      gi = fmaxf(gi, __shfl_xor_sync(0xffffffffu, gi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(amax + 1 + 2 * iw, __float_as_uint(gr));
+      atomicMax(amax + 2 + 2 * iw, __float_as_uint(gi));
+    }
   }
 }
 
@@ -108,17 +124,31 @@ __device__ __forceinline__ float pow2_scale(float x) {
   return ldexpf(1.f, 14 - e);
 }
 
-// scale[0] = sM; scale[1 + w] = sW(w); inv[w] = 1 / (sM sW(w))
-__global__ void k_scales(const unsigned int* __restrict__ amax, int n_freq, float* __restrict__ scale,
-                         double* __restrict__ inv) {
+// scale[0] = sM; scale[1 + w] = sW(w); inv[w] = 1 / (sM sW(w)).  Hermitian mode:
+// scale[1 + w], inv[w] belong to W1 = Re(f) M, scale[1 + n_freq + w],
+// inv[n_freq + w] to W2 = Im(f) M, and h2np[w] is the product count of the W2 part.
+__global__ void k_scales(const unsigned int* __restrict__ amax, int n_freq, int herm, int n_products,
+                         float* __restrict__ scale, double* __restrict__ inv, int* __restrict__ h2np) {
   const float mM = __uint_as_float(amax[0]);
   const float sM = pow2_scale(mM);
   if (threadIdx.x == 0) scale[0] = sM;
   for (int iw = threadIdx.x; iw < n_freq; iw += blockDim.x) {
-    // |Re W|, |Im W| <= 2 max|f| max|M|
-    const float sW = pow2_scale(2.f * __uint_as_float(amax[1 + iw]) * mM);
-    scale[1 + iw] = sW;
-    inv[iw] = 1.0 / ((double)sM * (double)sW);
+    const float fr = __uint_as_float(amax[1 + 2 * iw]), fi = __uint_as_float(amax[2 + 2 * iw]);
+    if (herm) {
+      // |components of W1| <= max|Re f| max|M|, of W2 <= max|Im f| max|M|
+      const float s1 = pow2_scale(fr * mM), s2 = pow2_scale(fi * mM);
+      scale[1 + iw] = s1;
+      scale[1 + n_freq + iw] = s2;
+      inv[iw] = 1.0 / ((double)sM * (double)s1);
+      inv[n_freq + iw] = 1.0 / ((double)sM * (double)s2);
+      // small W2 part: three products and long chains (flag 16)
+      h2np[iw] = (fi <= ldexpf(fr, -6)) ? 3 + 16 : n_products;
+    } else {
+      // |Re W|, |Im W| <= 2 max|f| max|M|
+      const float sW = pow2_scale(2.f * fmaxf(fr, fi) * mM);
+      scale[1 + iw] = sW;
+      inv[iw] = 1.0 / ((double)sM * (double)sW);
+    }
   }
 }
 
@@ -126,7 +156,8 @@ __global__ void k_scales(const unsigned int* __restrict__ amax, int n_freq, floa
 template <bool BF16, int NT>
 __global__ void __launch_bounds__(256)
 k_pack(const float2* __restrict__ M, int nG, int64_t K, int nGp, int Kp, const double2* __restrict__ f,
-       int n_freq, const float* __restrict__ scale, uint32_t* __restrict__ Bp, uint32_t* __restrict__ Ap) {
+       int n_freq, int herm, const float* __restrict__ scale, const int* __restrict__ h2np,
+       uint32_t* __restrict__ Bp, uint32_t* __restrict__ Ap) {
   extern __shared__ __align__(16) unsigned char smem_pack[];
   float2* tile = reinterpret_cast<float2*>(smem_pack);          // [64][33]
   float2* fs = tile + 64 * 33;                                 // [n_freq][64]
@@ -146,8 +177,8 @@ k_pack(const float2* __restrict__ M, int nG, int64_t K, int nGp, int Kp, const d
     float2 v = make_float2(0.f, 0.f);
     if (p < K) {
       const double2 d = f[(int64_t)iw * K + p];
-      const float sW = scale[1 + iw];
-      v = make_float2((float)d.x * sW, (float)d.y * sW);
+      const float sW = scale[1 + iw], sW2 = herm ? scale[1 + n_freq + iw] : sW;
+      v = make_float2((float)d.x * sW, (float)d.y * sW2);
     }
     fs[e] = v;
   }
@@ -168,15 +199,35 @@ k_pack(const float2* __restrict__ M, int nG, int64_t K, int nGp, int Kp, const d
     for (int t = 0; t < NT; ++t) Bp[(NT + t) * plane + row] = w[t];
     for (int iw = 0; iw < n_freq; ++iw) {
       const float2 f0 = fs[iw * 64 + 2 * lane], f1 = fs[iw * 64 + 2 * lane + 1];
-      const float wr0 = f0.x * m0.x - f0.y * m0.y, wi0 = f0.x * m0.y + f0.y * m0.x;
-      const float wr1 = f1.x * m1.x - f1.y * m1.y, wi1 = f1.x * m1.y + f1.y * m1.x;
       uint32_t* a = Ap + (size_t)iw * 2 * NT * plane + row;
-      splitn<BF16, NT>(wr0, wr1, w);
+      if (herm) {
+        // W1 = Re(f) M into the frequency's planes, W2 = Im(f) M into the second half
+        splitn<BF16, NT>(f0.x * m0.x, f1.x * m1.x, w);
 #pragma unroll
-      for (int t = 0; t < NT; ++t) a[t * plane] = w[t];
-      splitn<BF16, NT>(wi0, wi1, w);
+        for (int t = 0; t < NT; ++t) a[t * plane] = w[t];
+        splitn<BF16, NT>(f0.x * m0.y, f1.x * m1.y, w);
 #pragma unroll
-      for (int t = 0; t < NT; ++t) a[(NT + t) * plane] = w[t];
+        for (int t = 0; t < NT; ++t) a[(NT + t) * plane] = w[t];
+        uint32_t* a2 = a + (size_t)n_freq * 2 * NT * plane;
+        const int nt2 = (NT == 3 && h2np[iw] != 6) ? 2 : NT;   // terms the W2 part reads
+        splitn<BF16, NT>(f0.y * m0.x, f1.y * m1.x, w);
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+          if (t < nt2) a2[t * plane] = w[t];
+        splitn<BF16, NT>(f0.y * m0.y, f1.y * m1.y, w);
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+          if (t < nt2) a2[(NT + t) * plane] = w[t];
+      } else {
+        const float wr0 = f0.x * m0.x - f0.y * m0.y, wi0 = f0.x * m0.y + f0.y * m0.x;
+        const float wr1 = f1.x * m1.x - f1.y * m1.y, wi1 = f1.x * m1.y + f1.y * m1.x;
+        splitn<BF16, NT>(wr0, wr1, w);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) a[t * plane] = w[t];
+        splitn<BF16, NT>(wi0, wi1, w);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) a[(NT + t) * plane] = w[t];
+      }
     }
   }
 }
@@ -219,7 +270,8 @@ __device__ __forceinline__ void issue_stage(const unsigned char* st, uint32_t d_
       for (int i = 0; i < NT; ++i) {
         const int j = order - i;
         if (j < 0 || j >= NT) continue;
-        const bool keep = (i + j < NT) || (NT == 2 && n_products == 4 && i == 1 && j == 1);
+        // 3: t0t0, t0t1, t1t0; 4: adds t1t1; 6: all t_i t_j with i + j <= 2
+        const bool keep = (i + j < 2) || (i + j == 2 && (n_products == 6 || (n_products == 4 && i == 1)));
         if (!keep) continue;
         // planes: Re terms 0..NT-1, Im terms NT..2NT-1; K step ks is +32 bytes
         const uint64_t ar = d0 + (uint64_t)i * kTile + (uint64_t)(ks * 2);
@@ -259,26 +311,52 @@ struct TcBatch {
   CUtensorMap tmA[MAXQ];
   CUtensorMap tmB[MAXQ];
   double2* chi[MAXQ];
-  const double* inv[MAXQ];
+  const double* inv[MAXQ];   // [n_parts * n_freq] inverse operand scales
+  const int* h2np[MAXQ];     // Hermitian mode: [n_freq] product count of the W2 part (+16 if small)
   int nG[MAXQ];
   int tiles_m[MAXQ];         // tiles along G (rows of chi0)
   int tiles_n[MAXQ];         // tiles along G' (columns)
+  int64_t tpf[MAXQ];         // tiles per frequency
   int64_t item0[MAXQ + 1];   // first item of each q-point
   int n_q, n_freq, nK, chain_k, n_products, group;
+  int n_parts;               // 1, or 2 in Hermitian mode (W1 then W2)
+  int rr;                    // tile height / tile width (1, or 2 for CTA-pair tiles)
   int64_t total_items;
 };
 
+// products of part `part` of an item, and its chain length in stages.  The W2
+// part of Hermitian mode with three products is below 2^-6 of chi0, so its
+// round-toward-zero bias allows chains eight times longer.
+__device__ __forceinline__ int part_products(const TcBatch& P, int q, int iw, int part) {
+  return part ? (P.h2np[q][iw] & 15) : P.n_products;
+}
+__device__ __forceinline__ int part_chain(const TcBatch& P, int q, int iw, int part) {
+  return (part && P.h2np[q][iw] >= 16) ? min(P.nK, 8 * P.chain_k) : P.chain_k;
+}
+
 // item -> (q, frequency, tile row, tile column); tiles are visited in groups of
 // `group` tile rows, column by column inside a group (keeps A and B tiles of
-// concurrently running CTAs close together in L2)
+// concurrently running CTAs close together in L2).  Hermitian mode visits the
+// tiles on or above the diagonal row by row: row tm starts at column rr * tm.
 __device__ __forceinline__ void decode_item(const TcBatch& P, int64_t item, int& q, int& iw, int& tm, int& tn) {
   q = 0;
   while (q + 1 < P.n_q && item >= P.item0[q + 1]) ++q;
   const int64_t r = item - P.item0[q];
   const int TM = P.tiles_m[q], TN = P.tiles_n[q];
-  const int64_t tt = (int64_t)TM * TN;
+  const int64_t tt = P.tpf[q];
   iw = (int)(r / tt);
-  const int t = (int)(r - (int64_t)iw * tt);
+  int t = (int)(r - (int64_t)iw * tt);
+  if (P.n_parts == 2) {
+    int row = 0, len = TN;
+    while (t >= len && row + 1 < TM) {
+      t -= len;
+      ++row;
+      len -= P.rr;
+    }
+    tm = row;
+    tn = P.rr * row + t;
+    return;
+  }
   const int g = min(P.group, TM);
   const int grp = t / (g * TN);
   const int first = grp * g;
@@ -286,6 +364,43 @@ __device__ __forceinline__ void decode_item(const TcBatch& P, int64_t item, int&
   const int within = t - grp * g * TN;
   tm = first + within % rows;
   tn = within / rows;
+}
+
+// Add one drained part of a tile row (row G, columns Hb..Hb+63) into chi0 of
+// one frequency.  Plain mode: chi[G][H] += s (re + i im).  Hermitian mode: part 0
+// holds H1(G, H), part 1 holds H2(G, H); chi[G][H] += H1 + i H2 for G <= H and
+// chi[H][G] += conj(H1) + i conj(H2) for G < H.
+__device__ __forceinline__ void merge_row(double2* __restrict__ chi_w, int nG, int G, int Hb, const float (&sre)[64],
+                                          const float (&sim)[64], double sc, bool herm, int part) {
+  double2* row = chi_w + (size_t)G * nG;
+  if (!herm) {
+#pragma unroll
+    for (int i = 0; i < 64; ++i) {
+      if (Hb + i < nG) {
+        double2 o = row[Hb + i];
+        o.x += (double)sre[i] * sc;
+        o.y += (double)sim[i] * sc;
+        row[Hb + i] = o;
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 64; ++i) {
+    const int H = Hb + i;
+    if (H < nG && G <= H) {
+      const double a = (double)sre[i] * sc, b = (double)sim[i] * sc;
+      double2 o = row[H];
+      if (part == 0) { o.x += a; o.y += b; } else { o.x -= b; o.y += a; }
+      row[H] = o;
+      if (G < H) {
+        double2* m = chi_w + (size_t)H * nG + G;
+        double2 u = *m;
+        if (part == 0) { u.x += a; u.y -= b; } else { u.x += b; u.y += a; }
+        *m = u;
+      }
+    }
+  }
 }
 
 template <bool BF16, int NT>
@@ -298,8 +413,7 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
       (reinterpret_cast<uintptr_t>(smem_tc) + 1023) & ~uintptr_t(1023));
   Barriers* bar = reinterpret_cast<Barriers*>(tiles + RING_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nK = P.nK, chain_k = P.chain_k;
-  const int nchains = (nK + chain_k - 1) / chain_k;
+  const int nK = P.nK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -334,18 +448,23 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
       for (int64_t item = blockIdx.x; item < P.total_items && ok; item += gridDim.x) {
         int q, iw, tm, tn;
         decode_item(P, item, q, iw, tm, tn);
-        for (int kc = 0; kc < nK; ++kc, ++gs) {
-          const int s = (int)(gs % STAGES);
-          const uint32_t u = (uint32_t)(gs / STAGES);
-          if (!tc::mbar_wait(&bar->empty[s], (u & 1) ^ 1, status, 1, WAIT_BUDGET_NS)) { ok = false; break; }
-          tc::mbar_arrive_expect_tx(&bar->full[s], STAGE_BYTES);
-          unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
+        for (int part = 0; part < P.n_parts && ok; ++part) {
+          // planes of the terms the part's products read (t2 only with six products)
+          const int nt = (NT == 3 && part_products(P, q, iw, part) != 6) ? 2 : NT;
+          const int plane0 = (part * P.n_freq + iw) * PL;
+          for (int kc = 0; kc < nK; ++kc, ++gs) {
+            const int s = (int)(gs % STAGES);
+            const uint32_t u = (uint32_t)(gs / STAGES);
+            if (!tc::mbar_wait(&bar->empty[s], (u & 1) ^ 1, status, 1, WAIT_BUDGET_NS)) { ok = false; break; }
+            tc::mbar_arrive_expect_tx(&bar->full[s], 4 * nt * TILE_BYTES);
+            unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
 #pragma unroll
-          for (int j = 0; j < PL; ++j)
-            tc::tma_load_3d(st + j * TILE_BYTES, &P.tmA[q], &bar->full[s], kc * BK, tm * BM, iw * PL + j);
-#pragma unroll
-          for (int j = 0; j < PL; ++j)
-            tc::tma_load_3d(st + (PL + j) * TILE_BYTES, &P.tmB[q], &bar->full[s], kc * BK, tn * BN, j);
+            for (int j = 0; j < PL; ++j) {
+              if (j % NT >= nt) continue;
+              tc::tma_load_3d(st + j * TILE_BYTES, &P.tmA[q], &bar->full[s], kc * BK, tm * BM, plane0 + j);
+              tc::tma_load_3d(st + (PL + j) * TILE_BYTES, &P.tmB[q], &bar->full[s], kc * BK, tn * BN, j);
+            }
+          }
         }
       }
       // copies still in flight must land before the CTA may exit
@@ -358,29 +477,34 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
       int64_t gs = 0, gc = 0;
       bool ok = true;
       for (int64_t item = blockIdx.x; item < P.total_items && ok; item += gridDim.x) {
-        for (int kc = 0; kc < nK; ++kc, ++gs) {
-          const int buf = (int)(gc & 1);
-          const bool first = (kc % chain_k) == 0;
-          if (first) {
-            if (!tc::mbar_wait(&bar->tempty[buf], (uint32_t)(((gc >> 1) & 1) ^ 1), status, 1, WAIT_BUDGET_NS)) {
+        int q, iw, tm, tn;
+        decode_item(P, item, q, iw, tm, tn);
+        for (int part = 0; part < P.n_parts && ok; ++part) {
+          const int np = part_products(P, q, iw, part), ck = part_chain(P, q, iw, part);
+          for (int kc = 0; kc < nK; ++kc, ++gs) {
+            const int buf = (int)(gc & 1);
+            const bool first = (kc % ck) == 0;
+            if (first) {
+              if (!tc::mbar_wait(&bar->tempty[buf], (uint32_t)(((gc >> 1) & 1) ^ 1), status, 1, WAIT_BUDGET_NS)) {
+                ok = false;
+                break;
+              }
+              tc::fence_after();
+            }
+            const int s = (int)(gs % STAGES);
+            if (!tc::mbar_wait(&bar->full[s], (uint32_t)((gs / STAGES) & 1), status, 1, WAIT_BUDGET_NS)) {
               ok = false;
               break;
             }
             tc::fence_after();
-          }
-          const int s = (int)(gs % STAGES);
-          if (!tc::mbar_wait(&bar->full[s], (uint32_t)((gs / STAGES) & 1), status, 1, WAIT_BUDGET_NS)) {
-            ok = false;
-            break;
-          }
-          tc::fence_after();
-          const unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
-          const uint32_t d_re = tbase + buf * 256, d_im = d_re + 128;
-          issue_stage<BF16, NT>(st, d_re, d_im, first, P.n_products);
-          tc::mma_commit(&bar->empty[s]);
-          if ((kc % chain_k) == chain_k - 1 || kc == nK - 1) {
-            tc::mma_commit(&bar->tfull[buf]);
-            ++gc;
+            const unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
+            const uint32_t d_re = tbase + buf * 256, d_im = d_re + 128;
+            issue_stage<BF16, NT>(st, d_re, d_im, first, np);
+            tc::mma_commit(&bar->empty[s]);
+            if ((kc % ck) == ck - 1 || kc == nK - 1) {
+              tc::mma_commit(&bar->tfull[buf]);
+              ++gc;
+            }
           }
         }
       }
@@ -396,10 +520,13 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
     for (int64_t item = blockIdx.x; item < P.total_items && ok; item += gridDim.x) {
       int q, iw, tm, tn;
       decode_item(P, item, q, iw, tm, tn);
+      for (int part = 0; part < P.n_parts && ok; ++part) {
+      const int ck = part_chain(P, q, iw, part);
+      const int nch = (nK + ck - 1) / ck;
       float sre[64], sim[64];
 #pragma unroll
       for (int i = 0; i < 64; ++i) { sre[i] = 0.f; sim[i] = 0.f; }
-      for (int c = 0; c < nchains; ++c, ++gc) {
+      for (int c = 0; c < nch; ++c, ++gc) {
         const int buf = (int)(gc & 1);
         if (!tc::mbar_wait(&bar->tfull[buf], (uint32_t)((gc >> 1) & 1), status, 1, WAIT_BUDGET_NS)) {
           ok = false;
@@ -430,19 +557,9 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
       }
       const int nG = P.nG[q];
       const int G = tm * BM + row;
-      if (ok && G < nG) {
-        const double sc = P.inv[q][iw];
-        const int Hb = tn * BN + half * 64;
-        double2* out = P.chi[q] + ((size_t)iw * nG + G) * nG + Hb;
-#pragma unroll
-        for (int i = 0; i < 64; ++i) {
-          if (Hb + i < nG) {
-            double2 o = out[i];
-            o.x += (double)sre[i] * sc;
-            o.y += (double)sim[i] * sc;
-            out[i] = o;
-          }
-        }
+      if (ok && G < nG)
+        merge_row(P.chi[q] + (size_t)iw * nG * nG, nG, G, tn * BN + half * 64, sre, sim,
+                  P.inv[q][part * P.n_freq + iw], P.n_parts == 2, part);
       }
     }
   }
@@ -490,8 +607,7 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
   const uint32_t rank = tc::cluster_rank();
   const bool leader = rank == 0;
   const int64_t pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
-  const int nK = P.nK, chain_k = P.chain_k;
-  const int nchains = (nK + chain_k - 1) / chain_k;
+  const int nK = P.nK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -529,19 +645,24 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
         decode_item(P, item, q, iw, tm, tn);
         const int arow = tm * 2 * BM + (int)rank * BM;     // this CTA's 128 rows of A
         const int brow = tn * BN + (int)rank * (BN / 2);   // this CTA's 64 rows of B
-        for (int kc = 0; kc < nK; ++kc, ++gs) {
-          const int s = (int)(gs % STAGES);
-          const uint32_t u = (uint32_t)(gs / STAGES);
-          if (!tc::mbar_wait(&bar->empty[s], (u & 1) ^ 1, status, 1, WAIT_BUDGET_NS)) { ok = false; break; }
-          if (leader) tc::mbar_arrive_expect_tx(&bar->full[s], 2 * STAGE_BYTES);
-          const uint32_t fb = tc::mapa(&bar->full[s], 0);
-          unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
+        for (int part = 0; part < P.n_parts && ok; ++part) {
+          const int nt = (NT == 3 && part_products(P, q, iw, part) != 6) ? 2 : NT;
+          const int plane0 = (part * P.n_freq + iw) * PL;
+          for (int kc = 0; kc < nK; ++kc, ++gs) {
+            const int s = (int)(gs % STAGES);
+            const uint32_t u = (uint32_t)(gs / STAGES);
+            if (!tc::mbar_wait(&bar->empty[s], (u & 1) ^ 1, status, 1, WAIT_BUDGET_NS)) { ok = false; break; }
+            // the first CTA's barrier counts the loads of both CTAs
+            if (leader) tc::mbar_arrive_expect_tx(&bar->full[s], 4 * nt * (RG::A_BYTES + RG::B_BYTES));
+            const uint32_t fb = tc::mapa(&bar->full[s], 0);
+            unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
 #pragma unroll
-          for (int j = 0; j < PL; ++j)
-            tc::tma_load_3d_pair(st + j * RG::A_BYTES, &P.tmA[q], fb, kc * BK, arow, iw * PL + j);
-#pragma unroll
-          for (int j = 0; j < PL; ++j)
-            tc::tma_load_3d_pair(st + PL * RG::A_BYTES + j * RG::B_BYTES, &P.tmB[q], fb, kc * BK, brow, j);
+            for (int j = 0; j < PL; ++j) {
+              if (j % NT >= nt) continue;
+              tc::tma_load_3d_pair(st + j * RG::A_BYTES, &P.tmA[q], fb, kc * BK, arow, plane0 + j);
+              tc::tma_load_3d_pair(st + PL * RG::A_BYTES + j * RG::B_BYTES, &P.tmB[q], fb, kc * BK, brow, j);
+            }
+          }
         }
       }
       // copies of this CTA still in flight land before it may exit: wait until the
@@ -555,29 +676,34 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
       int64_t gs = 0, gc = 0;
       bool ok = true;
       for (int64_t item = pair; item < P.total_items && ok; item += npairs) {
-        for (int kc = 0; kc < nK; ++kc, ++gs) {
-          const int buf = (int)(gc & 1);
-          const bool first = (kc % chain_k) == 0;
-          if (first) {
-            if (!tc::mbar_wait(&bar->tempty[buf], (uint32_t)(((gc >> 1) & 1) ^ 1), status, 1, WAIT_BUDGET_NS)) {
+        int q, iw, tm, tn;
+        decode_item(P, item, q, iw, tm, tn);
+        for (int part = 0; part < P.n_parts && ok; ++part) {
+          const int np = part_products(P, q, iw, part), ck = part_chain(P, q, iw, part);
+          for (int kc = 0; kc < nK; ++kc, ++gs) {
+            const int buf = (int)(gc & 1);
+            const bool first = (kc % ck) == 0;
+            if (first) {
+              if (!tc::mbar_wait(&bar->tempty[buf], (uint32_t)(((gc >> 1) & 1) ^ 1), status, 1, WAIT_BUDGET_NS)) {
+                ok = false;
+                break;
+              }
+              tc::fence_after();
+            }
+            const int s = (int)(gs % STAGES);
+            if (!tc::mbar_wait(&bar->full[s], (uint32_t)((gs / STAGES) & 1), status, 1, WAIT_BUDGET_NS)) {
               ok = false;
               break;
             }
             tc::fence_after();
-          }
-          const int s = (int)(gs % STAGES);
-          if (!tc::mbar_wait(&bar->full[s], (uint32_t)((gs / STAGES) & 1), status, 1, WAIT_BUDGET_NS)) {
-            ok = false;
-            break;
-          }
-          tc::fence_after();
-          const unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
-          const uint32_t d_re = tbase + buf * 256, d_im = d_re + 128;
-          issue_stage<BF16, NT, true>(st, d_re, d_im, first, P.n_products);
-          tc::mma_commit_pair(&bar->empty[s], 0x3);
-          if ((kc % chain_k) == chain_k - 1 || kc == nK - 1) {
-            tc::mma_commit_pair(&bar->tfull[buf], 0x3);
-            ++gc;
+            const unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
+            const uint32_t d_re = tbase + buf * 256, d_im = d_re + 128;
+            issue_stage<BF16, NT, true>(st, d_re, d_im, first, np);
+            tc::mma_commit_pair(&bar->empty[s], 0x3);
+            if ((kc % ck) == ck - 1 || kc == nK - 1) {
+              tc::mma_commit_pair(&bar->tfull[buf], 0x3);
+              ++gc;
+            }
           }
         }
       }
@@ -593,10 +719,13 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
     for (int64_t item = pair; item < P.total_items && ok; item += npairs) {
       int q, iw, tm, tn;
       decode_item(P, item, q, iw, tm, tn);
+      for (int part = 0; part < P.n_parts && ok; ++part) {
+      const int ck = part_chain(P, q, iw, part);
+      const int nch = (nK + ck - 1) / ck;
       float sre[64], sim[64];
 #pragma unroll
       for (int i = 0; i < 64; ++i) { sre[i] = 0.f; sim[i] = 0.f; }
-      for (int c = 0; c < nchains; ++c, ++gc) {
+      for (int c = 0; c < nch; ++c, ++gc) {
         const int buf = (int)(gc & 1);
         if (!tc::mbar_wait(&bar->tfull[buf], (uint32_t)((gc >> 1) & 1), status, 1, WAIT_BUDGET_NS)) {
           ok = false;
@@ -627,19 +756,9 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
       }
       const int nG = P.nG[q];
       const int G = tm * 2 * BM + (int)rank * BM + row;
-      if (ok && G < nG) {
-        const double sc = P.inv[q][iw];
-        const int Hb = tn * BN + half * 64;
-        double2* out = P.chi[q] + ((size_t)iw * nG + G) * nG + Hb;
-#pragma unroll
-        for (int i = 0; i < 64; ++i) {
-          if (Hb + i < nG) {
-            double2 o = out[i];
-            o.x += (double)sre[i] * sc;
-            o.y += (double)sim[i] * sc;
-            out[i] = o;
-          }
-        }
+      if (ok && G < nG)
+        merge_row(P.chi[q] + (size_t)iw * nG * nG, nG, G, tn * BN + half * 64, sre, sim,
+                  P.inv[q][part * P.n_freq + iw], P.n_parts == 2, part);
       }
     }
   }
@@ -719,33 +838,44 @@ bool tc_supported(std::string* why) {
 
 int n_terms(const chi0_plan_s* p) { return p->n_products == 6 ? 3 : 2; }
 
+// A planes per frequency and part: W (plain) or W1 and W2 (Hermitian mode)
+int n_parts(const chi0_plan_s* p) { return p->tc_herm ? 2 : 1; }
+
+size_t planes_bytes(const chi0_plan_s* p) {
+  const size_t nGp = (size_t)round_up_i(p->max_nG, 2 * BM);
+  const size_t Kp = (size_t)((p->max_pairs + 63) / 64 * 64);
+  return 2 * (size_t)n_terms(p) * (1 + (size_t)n_parts(p) * p->n_freq) * nGp * Kp * 2;
+}
+
 size_t tc_pack_bytes(const chi0_plan_s* p, int64_t max_pairs, int max_nG) {
   const size_t nGp = (size_t)round_up_i(max_nG, 2 * BM);
   const size_t Kp = (size_t)((max_pairs + 63) / 64 * 64);
-  const size_t planes = 2 * (size_t)n_terms(p) * (1 + (size_t)p->n_freq);
-  const size_t scal = 256 + 32 * (size_t)(p->n_freq + 1);   // amax, scales, inverse scales
+  const size_t planes = 2 * (size_t)n_terms(p) * (1 + (size_t)n_parts(p) * p->n_freq);
+  const size_t scal = 256 + 48 * (size_t)(p->n_freq + 1);   // amax, scales, inverse scales, W2 products
   return planes * nGp * Kp * 2 + scal;
 }
 
-// workspace of one q-point's split planes: B, A, then amax / scales / inverse scales
+// workspace of one q-point's split planes: B, A, then amax / scales / inverse
+// scales / W2 product counts (each part sized for two values per frequency)
 struct PackWs {
   uint16_t* Bp;
   uint16_t* Ap;
   unsigned int* amax;
   float* scale;
   double* inv;
+  int* h2np;
 };
 
 static PackWs pack_ws(const chi0_plan_s* p, void* base, int nGp, int Kp) {
-  const size_t planes_ws = 2 * (size_t)n_terms(p) * (1 + (size_t)p->n_freq) * (size_t)round_up_i(p->max_nG, 2 * BM) *
-                           (size_t)((p->max_pairs + 63) / 64 * 64) * 2;
+  const size_t nf1 = (size_t)(p->n_freq + 1);
   PackWs w;
   w.Bp = reinterpret_cast<uint16_t*>(base);
   w.Ap = w.Bp + (size_t)2 * n_terms(p) * nGp * Kp;
-  unsigned char* tail = reinterpret_cast<unsigned char*>(base) + planes_ws;
-  w.amax = reinterpret_cast<unsigned int*>(tail);
-  w.scale = reinterpret_cast<float*>(tail + 8 * (size_t)(p->n_freq + 1));
-  w.inv = reinterpret_cast<double*>(tail + 16 * (size_t)(p->n_freq + 1));
+  unsigned char* tail = reinterpret_cast<unsigned char*>(base) + planes_bytes(p);
+  w.amax = reinterpret_cast<unsigned int*>(tail);            // 1 + 2 n_freq words
+  w.scale = reinterpret_cast<float*>(tail + 8 * nf1);         // 1 + 2 n_freq floats
+  w.inv = reinterpret_cast<double*>(tail + 16 * nf1);         // 2 n_freq doubles
+  w.h2np = reinterpret_cast<int*>(tail + 32 * nf1);           // n_freq ints
   return w;
 }
 
@@ -753,16 +883,16 @@ template <bool BF16, int NT>
 static cudaError_t pack_one(chi0_plan_s* p, int nG, const float2* M, int64_t K, const double2* f, const PackWs& w,
                             int nGp, int Kp, cudaStream_t s) {
   ProfScope ps(p, CHI0_K_PACK, s, 3);
-  cudaError_t e = cudaMemsetAsync(w.amax, 0, sizeof(unsigned int) * (p->n_freq + 1), s);
+  cudaError_t e = cudaMemsetAsync(w.amax, 0, sizeof(unsigned int) * (2 * p->n_freq + 1), s);
   if (e != cudaSuccess) return e;
   k_absmax<<<2 * 152, 256, 0, s>>>(M, K * nG, f, K, p->n_freq, w.amax);
-  k_scales<<<1, 128, 0, s>>>(w.amax, p->n_freq, w.scale, w.inv);
+  k_scales<<<1, 128, 0, s>>>(w.amax, p->n_freq, p->tc_herm ? 1 : 0, p->n_products, w.scale, w.inv, w.h2np);
   dim3 gpk(nGp / 32, Kp / 64);
   const size_t smp = (size_t)(64 * 33 + 64 * p->n_freq) * sizeof(float2);
   e = cudaFuncSetAttribute(k_pack<BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
   if (e != cudaSuccess) return e;
-  k_pack<BF16, NT><<<gpk, 256, smp, s>>>(M, nG, K, nGp, Kp, f, p->n_freq, w.scale, (uint32_t*)w.Bp,
-                                         (uint32_t*)w.Ap);
+  k_pack<BF16, NT><<<gpk, 256, smp, s>>>(M, nG, K, nGp, Kp, f, p->n_freq, p->tc_herm ? 1 : 0, w.scale, w.h2np,
+                                         (uint32_t*)w.Bp, (uint32_t*)w.Ap);
   return cudaGetLastError();
 }
 
@@ -781,18 +911,24 @@ static cudaError_t run_tc(chi0_plan_s* p, const TcJob* jobs, int n_jobs, int64_t
     cudaError_t e = pack_one<BF16, NT>(p, jb.nG, jb.M, K, jb.f, w, nGp, Kp, s);
     if (e != cudaSuccess) { delete P; return e; }
     if (!encode_planes(&P->tmB[j], w.Bp, BF16, Kp, nGp, 2 * NT, why, pair ? BN / 2 : BN) ||
-        !encode_planes(&P->tmA[j], w.Ap, BF16, Kp, nGp, 2 * NT * p->n_freq, why, BM)) {
+        !encode_planes(&P->tmA[j], w.Ap, BF16, Kp, nGp, 2 * NT * n_parts(p) * p->n_freq, why, BM)) {
       delete P;
       return cudaErrorInvalidValue;
     }
     P->chi[j] = jb.chi;
     P->inv[j] = w.inv;
+    P->h2np[j] = w.h2np;
     P->nG[j] = jb.nG;
-    P->tiles_m[j] = nGp / (pair ? 2 * BM : BM);
-    P->tiles_n[j] = nGp / BN;
+    const int TM = nGp / (pair ? 2 * BM : BM), TN = nGp / BN;
+    P->tiles_m[j] = TM;
+    P->tiles_n[j] = TN;
+    // Hermitian mode: row tm holds the TN - rr tm tiles from column rr tm on
+    P->tpf[j] = p->tc_herm ? (int64_t)(TN / TM) * TM * (TM + 1) / 2 : (int64_t)TM * TN;
     P->item0[j] = items;
-    items += (int64_t)P->tiles_m[j] * P->tiles_n[j] * p->n_freq;
+    items += P->tpf[j] * p->n_freq;
   }
+  P->n_parts = n_parts(p);
+  P->rr = pair ? 2 : 1;
   P->item0[n_jobs] = items;
   P->n_q = n_jobs;
   P->n_freq = p->n_freq;

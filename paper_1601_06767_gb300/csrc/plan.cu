@@ -276,6 +276,8 @@ chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* d) {
   if (d->max_pairs < 0) return fail(nullptr, CHI0_ERR_INVALID, "max_pairs must be >= 0");
   if (d->n_products != 0 && d->n_products != 3 && d->n_products != 4 && d->n_products != 6)
     return fail(nullptr, CHI0_ERR_INVALID, "n_products must be 0, 3, 4 or 6");
+  if (d->hermitian < -1 || d->hermitian > 1)
+    return fail(nullptr, CHI0_ERR_INVALID, "hermitian must be -1, 0 or 1");
   for (int i = 0; i < d->n_q; ++i)
     if (d->n_G[i] < 1 || d->n_G[i] > 65536) return fail(nullptr, CHI0_ERR_INVALID, "n_G must be in [1, 65536]");
   if (env_fault("bad_shape")) return fail(nullptr, CHI0_ERR_INVALID, "injected fault: bad_shape");
@@ -294,6 +296,7 @@ chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* d) {
   p->om_re.assign(d->freq_re, d->freq_re + d->n_freq);
   p->om_im.assign(d->freq_im, d->freq_im + d->n_freq);
   p->chain_pairs = d->chain_pairs ? d->chain_pairs : 32;
+  p->tc_herm = chi0::is_split(p) && (d->hermitian == 1 || (d->hermitian == 0 && p->n_products == 6));
 
   chi0_status st = CHI0_OK;
   auto bail = [&](chi0_status s) {

@@ -49,8 +49,8 @@ std::string key_of(const chi0_plan_s* p, int iq) {
   if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) snprintf(name, sizeof(name), "sm%d%d", prop.major, prop.minor);
   cudaGetLastError();
   char buf[256];
-  snprintf(buf, sizeof(buf), "%s nG=%d nf=%d prec=%d np=%d maxpairs=%lld", name, p->q[iq].nG, p->n_freq, (int)p->prec,
-           p->n_products, (long long)p->max_pairs);
+  snprintf(buf, sizeof(buf), "%s nG=%d nf=%d prec=%d np=%d herm=%d maxpairs=%lld", name, p->q[iq].nG, p->n_freq,
+           (int)p->prec, p->n_products, p->tc_herm ? 1 : 0, (long long)p->max_pairs);
   return buf;
 }
 

@@ -21,7 +21,8 @@ def _dev(a):
     ("c1", [150 + 25 * j for j in range(8)], 3, 40, 3),     # 8 q-points, N_G 150..325
     ("c3", [2200, 2600], 2, 12, 1),                         # the batched workload's smallest / largest spheres
 ])
-def test_batched_matches_oracle_and_single_q(name, nG, nv, nc, n_imag):
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])    # bf16: Hermitian mode (upper tiles, H1 + i H2)
+def test_batched_matches_oracle_and_single_q(name, nG, nv, nc, n_imag, precision):
     import torch
     from paper_1601_06767_gb300 import Chi0Plan
     qf = [((i + 0.5) / 2, (j + 0.5) / 2, (l + 0.5) / 2) for i in range(2) for j in range(2) for l in range(2)]
@@ -32,7 +33,7 @@ def test_batched_matches_oracle_and_single_q(name, nG, nv, nc, n_imag):
     Ev, Ec = prob.E_v[:nv], prob.E_c[:nc]
     dE = (Ev[:, None] - Ec[None, :]).reshape(-1)
     f = freq_factor(dE, np.ones_like(dE), prob.omega, prob.delta)
-    with Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision="fp16", gw=prob.gw, max_pairs=64) as plan:
+    with Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision=precision, gw=prob.gw, max_pairs=64) as plan:
         psi_c = plan.wfn_to_grid(_dev(cc))
         psi_vs = [plan.wfn_to_grid(_dev(prob.coeff_v(q, np.arange(nv)))) for q in range(nq)]
         Evs = [_dev(Ev) for _ in range(nq)]

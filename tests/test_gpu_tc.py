@@ -141,9 +141,62 @@ def test_tc_edge_shapes(nG, nv, nc, pair, monkeypatch):
     Ev, Ec = prob.E_v[:nv], prob.E_c[:nc]
     dE = (Ev[:, None] - Ec[None, :]).reshape(-1)
     ref = chi0_from_pairs(M, freq_factor(dE, np.ones_like(dE), prob.omega, prob.delta))
-    for prec in ("fp16", "bf16"):
-        with _plan(prob, precision=prec, max_pairs=64) as plan:
+    for prec, herm in (("fp16", None), ("bf16", None), ("fp16", True), ("bf16", False)):
+        with _plan(prob, precision=prec, max_pairs=64, hermitian=herm) as plan:
             chi = plan.accumulate(0, _dev(M.astype(np.complex64)), nv, nc, _dev(Ev), _dev(Ec))
             plan.sync_status()
             chi = chi.cpu().numpy()
-        assert max(rel_fro(chi[i], ref[i]) for i in range(2)) < TOL, (prec, nG, nv, nc)
+        assert max(rel_fro(chi[i], ref[i]) for i in range(2)) < TOL, (prec, herm, nG, nv, nc)
+
+
+@pytest.mark.parametrize("pair", ["0", "1"])
+@pytest.mark.parametrize("precision,n_products", [("bf16", 6), ("fp16", 3), ("bf16", 4)])
+def test_hermitian_mode_matches_plain(precision, n_products, pair, monkeypatch):
+    """chi0 = H1 + i H2 from tiles on or above the diagonal (lower triangle
+    written as the conjugate transpose) against the oracle and against the
+    plain contraction of all tiles; ragged N_G = 350 and several pair blocks.
+    Off the real axis |Im f| / |Re f| <= delta / |E_v - E_c|, so H2 takes three
+    products."""
+    monkeypatch.setenv("CHI0_TC_PAIR", pair)
+    prob, cv, cc, uv, uc, M = _c1_pairs(n_imag=2)
+    nv, nc = prob.n_v, prob.n_c
+    dE = (prob.E_v[:, None] - prob.E_c[None, :]).reshape(-1)
+    ref = chi0_from_pairs(M, freq_factor(dE, np.ones_like(dE), prob.omega, prob.delta))
+    out = {}
+    for herm in (True, False):
+        with _plan(prob, precision=precision, n_products=n_products, max_pairs=1024, hermitian=herm) as plan:
+            chi = plan.accumulate(0, _dev(M.astype(np.complex64)), nv, nc, _dev(prob.E_v), _dev(prob.E_c))
+            plan.sync_status()
+            out[herm] = chi.cpu().numpy()
+    errs = [rel_fro(out[True][i], ref[i]) for i in range(prob.omega.size)]
+    diff = [rel_fro(out[True][i], out[False][i]) for i in range(prob.omega.size)]
+    print(f"\nhermitian {precision} x{n_products} pair={pair}: err {['%.2e' % e for e in errs]}"
+          f" vs plain {['%.2e' % e for e in diff]}")
+    bar = 4e-6 if n_products == 4 else TOL      # two BF16 terms: 16 bits (reported bar)
+    assert max(errs) < bar
+    assert max(diff) < 2 * bar
+
+
+@pytest.mark.parametrize("pair", ["0", "1"])
+def test_hermitian_mode_real_frequencies(pair, monkeypatch):
+    """Real frequencies inside the transition band with a wide broadening: Im f
+    is as large as Re f, so the H2 part keeps all six products and the short
+    chains."""
+    monkeypatch.setenv("CHI0_TC_PAIR", pair)
+    prob, cv, cc, uv, uc, M = _c1_pairs()
+    nv, nc = prob.n_v, prob.n_c
+    omega = np.array([0.4, 1.1, 0.05 + 0.3j])
+    delta = 5e-2
+    dE = (prob.E_v[:, None] - prob.E_c[None, :]).reshape(-1)
+    f = freq_factor(dE, np.ones_like(dE), omega, delta)
+    assert np.abs(f.imag).max() > 0.1 * np.abs(f.real).max()
+    ref = chi0_from_pairs(M, f)
+    from paper_1601_06767_gb300 import Chi0Plan
+    with Chi0Plan(prob.n, prob.gvec, omega, delta, precision="bf16", gw=prob.gw, max_pairs=1024,
+                  hermitian=True) as plan:
+        chi = plan.accumulate(0, _dev(M.astype(np.complex64)), nv, nc, _dev(prob.E_v), _dev(prob.E_c))
+        plan.sync_status()
+        chi = chi.cpu().numpy()
+    errs = [rel_fro(chi[i], ref[i]) for i in range(omega.size)]
+    print(f"\nhermitian real omega pair={pair}: {['%.2e' % e for e in errs]}")
+    assert max(errs) < TOL
