@@ -485,9 +485,10 @@ def run_case(args):
     K, nv, nc = 8192, 128, 64
     g = torch.Generator(device="cuda")
     g.manual_seed(0)
+    herm = {"auto": None, "on": True, "off": False}[args.hermitian]
     with pkg.Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision=args.precision, max_pairs=K,
-                      gw=prob.gw, n_products=args.n_products) as plan:
-        if args.case == "contract":
+                      gw=prob.gw, n_products=args.n_products, hermitian=herm) as plan:
+        if args.case == "contract" and not args.no_tune:
             plan.autotune(0)          # the variant the benchmark runs
         M = torch.randn(K, nG, dtype=torch.complex64, device="cuda", generator=g) * 4e-3
         if args.case == "contract":
@@ -783,6 +784,8 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["bf16", "fp16"], default="bf16")
     ap.add_argument("--n-products", type=int, default=0)
     ap.add_argument("--hermitian", choices=["auto", "on", "off"], default="auto")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="--case contract: keep the plan's default tiles (CHI0_TC_PAIR picks the variant)")
     ap.add_argument("--fp64-sample", type=int, default=32)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

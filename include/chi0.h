@@ -45,7 +45,8 @@ typedef enum {
   CHI0_ERR_OOM = 2,          /* device allocation failed */
   CHI0_ERR_CUDA = 3,         /* a CUDA runtime call failed */
   CHI0_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out */
-  CHI0_ERR_UNSUPPORTED = 5   /* no kernel for this device / shape */
+  CHI0_ERR_UNSUPPORTED = 5,  /* no kernel for this device / shape */
+  CHI0_ERR_SINGULAR = 6      /* chi0_epsilon_inverse met a zero pivot (reported by chi0_sync_status) */
 } chi0_status;
 
 typedef enum {
@@ -210,6 +211,9 @@ typedef enum {
   CHI0_K_PACK,           /* operand scaling + 16-bit split (split plans) */
   CHI0_K_CONTRACT_TC,    /* tcgen05 contraction + FP64 merge (split plans) */
   CHI0_K_CONTRACT_F64,   /* DFMA contraction (FP64 plans) */
+  CHI0_K_EPS,            /* dielectric matrix and precision conversions */
+  CHI0_K_INV_PANEL,      /* Gauss-Jordan panels, row swaps, column permutation */
+  CHI0_K_INV_UPDATE,     /* Gauss-Jordan trailing updates */
   CHI0_K_COUNT
 } chi0_kernel;
 
@@ -248,6 +252,42 @@ chi0_status chi0_accumulate_fp64_noalloc(int n_G, const void* M, int n_v, int n_
                                          const double* E_col, const double* w_col, int n_freq,
                                          const double* freq_re, const double* freq_im, double delta,
                                          void* chi0, void* stream);
+
+/* ---- Dielectric matrix (section II: eps = 1 - v chi0, W = eps^-1 v; Table III:
+ * eps_inf = 1 / [eps^-1]_{00}(q -> 0, omega = 0)).  Hartree atomic units. ---- */
+
+/* Bare Coulomb interaction on sphere iq (host computation):
+ *   v_out[j] = 4 pi / (Omega |q + G_j|^2),  q + G_j = (q_frac + g_j) . B,
+ * with B the reciprocal lattice (rows b_i, a_i . b_j = 2 pi delta_ij) of the
+ * direct lattice `lattice` (host [3][3], rows a_i in bohr) and Omega = |det A|.
+ * q_frac (host [3]) is q in reciprocal-lattice units; v_out (host) [n_G[iq]].
+ * CHI0_ERR_INVALID for a singular lattice or q + G_j = 0. */
+chi0_status chi0_coulomb(chi0_plan plan, int iq, const double* lattice, const double* q_frac, double* v_out);
+
+/* eps[w][G][G'] = delta_GG' - v[G] chi0[w][G][G']                     (symmetric = 0)
+ *             or delta_GG' - v[G]^1/2 chi0[w][G][G'] v[G']^1/2        (symmetric = 1; same
+ * eigenvalues and same diagonal of the inverse, Hermitian when chi0 is).
+ * chi0, eps: (device) [n_freq][n_G[iq]][n_G[iq]] complex128, may be the same buffer;
+ * v: (device) [n_G[iq]] FP64 (e.g. from chi0_coulomb). */
+chi0_status chi0_epsilon(chi0_plan plan, int iq, const void* chi0, const double* v, int symmetric, void* eps,
+                         void* stream);
+
+/* In-place inverse of the n_freq matrices eps[w] ((device) [n_freq][n_G[iq]][n_G[iq]]
+ * complex128, row-major) by blocked Gauss-Jordan elimination with partial
+ * pivoting (largest |re| + |im| in the column).  FP64 plans compute in FP64;
+ * split plans compute in FP32 on a complex64 copy and write the result back
+ * as complex128 (forward error about cond(eps) x 1e-7).  Workspace (the
+ * complex64 copy for split plans, panel buffers) is allocated at the first
+ * call for a sphere this large and kept by the plan.  A zero pivot (singular
+ * matrix) leaves non-finite values and makes the next chi0_sync_status return
+ * CHI0_ERR_SINGULAR. */
+chi0_status chi0_epsilon_inverse(chi0_plan plan, int iq, void* eps, void* stream);
+
+/* eps_inf[w] = 1 / eps_inv[w][i0][i0] with i0 the index of G = 0 in sphere iq.
+ * eps_inv: (device) as returned by chi0_epsilon_inverse; out: (host) [n_freq]
+ * complex128 (re, im interleaved).  Synchronises `stream`.  CHI0_ERR_INVALID
+ * if the sphere does not contain G = 0. */
+chi0_status chi0_eps_inf(chi0_plan plan, int iq, const void* eps_inv, double* out, void* stream);
 
 /* Band selection of Eq. 3 / Eq. 4 (host arrays, host computation).
  * E_c (host) [n_c] sorted ascending.  Columns 0..N0-1 are bands 0..N0-1 with

@@ -8,8 +8,9 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libchi0.so")
 
-CHI0_OK, CHI0_ERR_INVALID, CHI0_ERR_OOM, CHI0_ERR_CUDA, CHI0_ERR_TIMEOUT, CHI0_ERR_UNSUPPORTED = range(6)
-STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "UNSUPPORTED"}
+(CHI0_OK, CHI0_ERR_INVALID, CHI0_ERR_OOM, CHI0_ERR_CUDA, CHI0_ERR_TIMEOUT, CHI0_ERR_UNSUPPORTED,
+ CHI0_ERR_SINGULAR) = range(7)
+STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "UNSUPPORTED", 6: "SINGULAR"}
 CHI0_FP64, CHI0_SPLIT_BF16, CHI0_SPLIT_FP16 = 0, 1, 2
 PRECISIONS = {"fp64": CHI0_FP64, "bf16": CHI0_SPLIT_BF16, "fp16": CHI0_SPLIT_FP16}
 
@@ -50,6 +51,10 @@ SIGNATURES = [
     ("chi0_build_batched", _I, [_VP, _VP, _I, _VP, _VP, _VP, _I, _VP, _VP, _VP, _I, _VP]),
     ("chi0_backward", _I, [_VP, _I, _VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("chi0_selftest_wait", _I, [_VP, _D, _VP]),
+    ("chi0_coulomb", _I, [_VP, _I, _VP, _VP, _VP]),
+    ("chi0_epsilon", _I, [_VP, _I, _VP, _VP, _I, _VP, _VP]),
+    ("chi0_epsilon_inverse", _I, [_VP, _I, _VP, _VP]),
+    ("chi0_eps_inf", _I, [_VP, _I, _VP, _VP, _VP]),
     ("chi0_autotune", _I, [_VP, _I, _I, _VP, _VP]),
     ("chi0_get_tuning", _I, [_VP, _VP, _VP, _VP]),
     ("chi0_profile_enable", _I, [_VP, _I]),
@@ -57,7 +62,8 @@ SIGNATURES = [
     ("chi0_profile_read", _I, [_VP, _VP, _VP]),
     ("chi0_accumulate_fp64_noalloc", _I, [_I, _VP, _I, _I, _VP, _VP, _VP, _I, _VP, _VP, _D, _VP, _VP]),
 ]
-KERNELS = ["wfn", "pair_planes", "pair_gather", "weights", "pack", "contract_tc", "contract_f64"]
+KERNELS = ["wfn", "pair_planes", "pair_gather", "weights", "pack", "contract_tc", "contract_f64",
+           "epsilon", "inv_panel", "inv_update"]
 
 _lib = None
 

@@ -222,6 +222,37 @@ class Chi0Plan:
                                        n_c, _ptr(E_col), _ptr(w_col), _ptr(chi), _stream()))
         return chi
 
+    # -- dielectric matrix ---------------------------------------------------
+    def coulomb(self, iq: int, lattice, q_frac) -> np.ndarray:
+        """chi0_coulomb: v(q+G) = 4 pi / (Omega |q+G|^2) on sphere iq (host array)."""
+        A = _f64(lattice).reshape(3, 3)
+        q = _f64(q_frac).reshape(3)
+        v = np.empty(self.n_G[iq], np.float64)
+        self._check(L.lib().chi0_coulomb(self._h, iq, A.ctypes.data, q.ctypes.data, v.ctypes.data))
+        return v
+
+    def epsilon(self, iq: int, chi, v, symmetric: bool = False, out=None) -> torch.Tensor:
+        """chi0_epsilon: eps = 1 - v chi0 (or the symmetrised form); out may be chi."""
+        self._c(chi, "chi", torch.complex128)
+        self._c(v, "v", torch.float64)
+        out = torch.empty_like(chi) if out is None else self._c(out, "out", torch.complex128)
+        self._check(L.lib().chi0_epsilon(self._h, iq, _ptr(chi), _ptr(v), int(bool(symmetric)), _ptr(out),
+                                         _stream()))
+        return out
+
+    def epsilon_inverse(self, iq: int, eps) -> torch.Tensor:
+        """chi0_epsilon_inverse: eps is replaced by eps^-1 (and returned)."""
+        self._c(eps, "eps", torch.complex128)
+        self._check(L.lib().chi0_epsilon_inverse(self._h, iq, _ptr(eps), _stream()))
+        return eps
+
+    def eps_inf(self, iq: int, eps_inv) -> np.ndarray:
+        """chi0_eps_inf: 1 / [eps^-1]_00 per frequency (complex, host)."""
+        self._c(eps_inv, "eps_inv", torch.complex128)
+        out = np.empty(2 * self.n_freq, np.float64)
+        self._check(L.lib().chi0_eps_inf(self._h, iq, _ptr(eps_inv), out.ctypes.data, _stream()))
+        return out[0::2] + 1j * out[1::2]
+
 
 def select_accelerated(E_c, N0: int, dE: float, dos_A: float, dos_V0: float, E_max: float):
     """Columns of Eq. 3/4 from chi0_select_accelerated: (band index, energy, weight)."""

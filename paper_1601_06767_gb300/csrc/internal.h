@@ -21,6 +21,8 @@ struct SphereQ {
   int nk1 = 0, nk2 = 0, nk3 = 0;      // kept extents
   int nk2p = 0, nk3p = 0;             // padded to a multiple of 4 (twiddle tables)
   int64_t goff = 0;                   // offset of this sphere in the concatenated list
+  std::vector<int32_t> g_host;        // [nG][3] the caller's G vectors (Coulomb, G = 0 index)
+  int i0 = -1;                        // index of G = 0, or -1
   // device tables, sphere points sorted by (k2, k3, k1) ("column order")
   int* ent_box = nullptr;             // [nG] (k2-k2min)*nk3 + (k3-k3min)
   int* ent_k1 = nullptr;              // [nG] k1 - k1min
@@ -77,6 +79,8 @@ struct chi0_plan_s {
   std::vector<const void*> graph_key;
   int64_t graph_family[CHI0_K_COUNT] = {};   // kernel launches per family inside the captured graph
   double* d_bwd = nullptr;   // adjoint work: per-pair grad dE and per-tile partial sums
+  void* d_inv = nullptr;     // dielectric-inverse workspace (grown on demand)
+  size_t inv_bytes = 0;
   size_t ws_bytes = 0;
   std::string err;
   bool tc_ready = false;     // tensor-map encoder resolved
@@ -148,5 +152,10 @@ int bwd_max_freq();
 bool tune_apply_cached(chi0_plan_s* p, int iq);
 cudaError_t launch_wait_selftest(chi0_plan_s* p, double budget_ms, cudaStream_t s);
 bool tc_supported(std::string* why);
+// dielectric matrix: eps = 1 - v chi0 (plain or symmetrised) and its in-place inverse
+cudaError_t launch_epsilon(chi0_plan_s* p, int nG, const double2* chi, const double* v, int symmetric,
+                           double2* eps, cudaStream_t s);
+size_t eps_inverse_ws_bytes(const chi0_plan_s* p, int nG);
+cudaError_t launch_epsilon_inverse(chi0_plan_s* p, int nG, double2* eps, void* ws, cudaStream_t s);
 
 }  // namespace chi0

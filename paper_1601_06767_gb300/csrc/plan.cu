@@ -102,7 +102,7 @@ void free_plan(chi0_plan_s* p) {
   cudaFree(w.T1d); cudaFree(w.T1f); cudaFree(w.T2d); cudaFree(w.T2f);
   cudaFree(w.T3d); cudaFree(w.T3f);
   cudaFree(p->d_omega); cudaFree(p->d_D); cudaFree(p->d_M); cudaFree(p->d_f);
-  cudaFree(p->d_pack); cudaFree(p->d_status); cudaFree(p->d_bwd);
+  cudaFree(p->d_pack); cudaFree(p->d_status); cudaFree(p->d_bwd); cudaFree(p->d_inv);
   for (size_t i = 1; i < p->bq_M.size(); ++i) {
     cudaFree(p->bq_M[i]);
     cudaFree(p->bq_f[i]);
@@ -223,7 +223,8 @@ static cudaEvent_t pool_get(chi0_plan_s* p) {
 
 static const char* const kFamilyNames[CHI0_K_COUNT] = {"chi0.wfn_to_grid", "chi0.pair_planes", "chi0.pair_gather",
                                                        "chi0.weights", "chi0.pack", "chi0.contract_tc",
-                                                       "chi0.contract_f64"};
+                                                       "chi0.contract_f64", "chi0.epsilon", "chi0.inv_panel",
+                                                       "chi0.inv_update"};
 
 ProfScope::ProfScope(chi0_plan_s* plan, int kernel, cudaStream_t st, int launches) : p(plan), k(kernel), s(st) {
   nvtxRangePushA(kFamilyNames[k]);   // host-side range around the launches (visible to nsys / ncu)
@@ -324,6 +325,12 @@ chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* d) {
     st = analyse_sphere(p, d->gvec + 3 * off, d->n_G[i], &p->q[i]);
     if (st != CHI0_OK) return bail(st);
     p->q[i].goff = off;
+    p->q[i].g_host.assign(d->gvec + 3 * off, d->gvec + 3 * (off + d->n_G[i]));
+    for (int j = 0; j < d->n_G[i]; ++j)
+      if (d->gvec[3 * (off + j)] == 0 && d->gvec[3 * (off + j) + 1] == 0 && d->gvec[3 * (off + j) + 2] == 0) {
+        p->q[i].i0 = j;
+        break;
+      }
     off += d->n_G[i];
     p->max_nG = std::max(p->max_nG, d->n_G[i]);
   }
@@ -406,7 +413,96 @@ chi0_status chi0_sync_status(chi0_plan p, void* stream) {
   int h = 0;
   CK(p, cudaMemcpy(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   CK(p, cudaMemset(p->d_status, 0, sizeof(int)));
+  if (h & 0x100) return fail(p, CHI0_ERR_SINGULAR, "chi0_epsilon_inverse met a zero pivot");
   if (h) return fail(p, CHI0_ERR_TIMEOUT, "a bounded device-side wait ran out (status " + std::to_string(h) + ")");
+  return CHI0_OK;
+}
+
+// ---------------------------------------------------------------------------
+// dielectric matrix
+// ---------------------------------------------------------------------------
+chi0_status chi0_coulomb(chi0_plan p, int iq, const double* lattice, const double* q_frac, double* v_out) {
+  if (!p) return CHI0_ERR_INVALID;
+  if (iq < 0 || iq >= (int)p->q.size()) return fail(p, CHI0_ERR_INVALID, "iq out of range");
+  if (!lattice || !q_frac || !v_out) return fail(p, CHI0_ERR_INVALID, "NULL argument");
+  const double* a = lattice;   // rows a_i
+  // cofactor matrix of A: cof[i][j]; det = sum_j a[0][j] cof[0][j]; inv(A)^T = cof / det
+  double cof[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+      cof[i][j] = a[3 * i1 + j1] * a[3 * i2 + j2] - a[3 * i1 + j2] * a[3 * i2 + j1];
+    }
+  const double det = a[0] * cof[0][0] + a[1] * cof[0][1] + a[2] * cof[0][2];
+  if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return fail(p, CHI0_ERR_INVALID, "singular lattice");
+  double b[3][3];   // rows b_i = 2 pi (A^-T) rows
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) b[i][j] = 2.0 * M_PI * cof[i][j] / det;
+  const double omega_cell = std::fabs(det);
+  const chi0::SphereQ& sq = p->q[iq];
+  for (int jg = 0; jg < sq.nG; ++jg) {
+    double k[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < 3; ++i) {
+      const double c = (double)sq.g_host[3 * jg + i] + q_frac[i];
+      for (int x = 0; x < 3; ++x) k[x] += c * b[i][x];
+    }
+    const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+    if (!(k2 > 0.0)) return fail(p, CHI0_ERR_INVALID, "q + G = 0 at sphere point " + std::to_string(jg));
+    v_out[jg] = 4.0 * M_PI / (omega_cell * k2);
+  }
+  return CHI0_OK;
+}
+
+chi0_status chi0_epsilon(chi0_plan p, int iq, const void* chi, const double* v, int symmetric, void* eps,
+                         void* stream) {
+  chi0_status st = check_plan(p);
+  if (st != CHI0_OK) return st;
+  if (iq < 0 || iq >= (int)p->q.size()) return fail(p, CHI0_ERR_INVALID, "iq out of range");
+  if (!chi || !v || !eps) return fail(p, CHI0_ERR_INVALID, "NULL buffer");
+  if (symmetric != 0 && symmetric != 1) return fail(p, CHI0_ERR_INVALID, "symmetric must be 0 or 1");
+  CK(p, chi0::launch_epsilon(p, p->q[iq].nG, (const double2*)chi, v, symmetric, (double2*)eps,
+                             (cudaStream_t)stream));
+  return CHI0_OK;
+}
+
+chi0_status chi0_epsilon_inverse(chi0_plan p, int iq, void* eps, void* stream) {
+  chi0_status st = check_plan(p);
+  if (st != CHI0_OK) return st;
+  if (iq < 0 || iq >= (int)p->q.size()) return fail(p, CHI0_ERR_INVALID, "iq out of range");
+  if (!eps) return fail(p, CHI0_ERR_INVALID, "NULL buffer");
+  const int nG = p->q[iq].nG;
+  const size_t need = chi0::eps_inverse_ws_bytes(p, nG);
+  if (need > p->inv_bytes) {
+    CK(p, cudaStreamSynchronize((cudaStream_t)stream));
+    cudaFree(p->d_inv);
+    p->d_inv = nullptr;
+    p->inv_bytes = 0;
+    CK(p, cudaMalloc(&p->d_inv, need));
+    p->inv_bytes = need;
+    p->ws_bytes += need;
+  }
+  CK(p, chi0::launch_epsilon_inverse(p, nG, (double2*)eps, p->d_inv, (cudaStream_t)stream));
+  return CHI0_OK;
+}
+
+chi0_status chi0_eps_inf(chi0_plan p, int iq, const void* eps_inv, double* out, void* stream) {
+  chi0_status st = check_plan(p);
+  if (st != CHI0_OK) return st;
+  if (iq < 0 || iq >= (int)p->q.size()) return fail(p, CHI0_ERR_INVALID, "iq out of range");
+  if (!eps_inv || !out) return fail(p, CHI0_ERR_INVALID, "NULL buffer");
+  const int i0 = p->q[iq].i0;
+  if (i0 < 0) return fail(p, CHI0_ERR_INVALID, "the sphere has no G = 0");
+  const size_t nG = (size_t)p->q[iq].nG;
+  std::vector<double2> h((size_t)p->n_freq);
+  const double2* src = (const double2*)eps_inv + (size_t)i0 * nG + i0;
+  CK(p, cudaMemcpy2DAsync(h.data(), sizeof(double2), src, nG * nG * sizeof(double2), sizeof(double2),
+                          (size_t)p->n_freq, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  CK(p, cudaStreamSynchronize((cudaStream_t)stream));
+  for (int w = 0; w < p->n_freq; ++w) {
+    const double d = h[w].x * h[w].x + h[w].y * h[w].y;
+    out[2 * w] = h[w].x / d;
+    out[2 * w + 1] = -h[w].y / d;
+  }
   return CHI0_OK;
 }
 
