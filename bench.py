@@ -183,6 +183,72 @@ def h2_products(Ev, Ec, omega, delta, n_prod):
     return np.array(out)
 
 
+def dielectric(args, pkg, prob, plan, chi, chi_a, dev):
+    """eps = 1 - v^1/2 chi0 v^1/2, its inverse and eps_inf for the full and the
+    accelerated chi0 of the benchmark workload (section II, Table III): device
+    time of the inverse on the plan's path (FP32 for split plans) and on an FP64
+    plan, and the oracle's (LAPACK) inverse of one matrix of the same size on
+    the host cores for context."""
+    import torch
+    nG, nf = chi.shape[-1], chi.shape[0]
+    A = prob.a * np.eye(3)
+    v = torch.from_numpy(plan.coulomb(0, A, prob.q_frac[0])).to(dev)
+    flops = 8.0 * nG ** 3 * nf                 # Gauss-Jordan inverse: N^3 complex MACs per matrix
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed_inverse(p, src, reps):
+        eps = p.epsilon(0, src, v, symmetric=True)
+        p.epsilon_inverse(0, eps)              # first call allocates the workspace
+        torch.cuda.synchronize()
+        ts = []
+        p.profile(True)
+        p.profile_reset()
+        for _ in range(reps):
+            p.epsilon(0, src, v, symmetric=True, out=eps)
+            e0.record()
+            p.epsilon_inverse(0, eps)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        p.sync_status()
+        prof = p.profile_read()
+        p.profile(False)
+        kern = {k: round(prof[k][0] / reps, 3) for k in ("epsilon", "inv_panel", "inv_update")}
+        return eps, statistics.median(ts), kern
+
+    eps, ms, kern = timed_inverse(plan, chi, 3)
+    einf = plan.eps_inf(0, eps)
+    del eps
+    eps_a = plan.epsilon(0, chi_a, v, symmetric=True)
+    plan.epsilon_inverse(0, eps_a)
+    einf_a = plan.eps_inf(0, eps_a)
+    del eps_a
+    out = {"what": "eps = 1 - v^1/2 chi0 v^1/2 (v = 4 pi / (Omega |q+G|^2)), eps^-1 by blocked Gauss-Jordan "
+                   "with partial pivoting, eps_inf = 1/[eps^-1]_00",
+           "matrices": f"{nf} x {nG}^2", "ms_inverse": ms, "tflops": flops / ms / 1e9,
+           "precision": "FP32 elimination (split plan)" if plan.precision != "fp64" else "FP64",
+           "kernel_ms": kern,
+           "eps_inf_full": [round(float(x.real), 6) for x in einf[:3]],
+           "eps_inf_accelerated": [round(float(x.real), 6) for x in einf_a[:3]],
+           "eps_inf_rel_diff_static": float(abs(einf_a[0] - einf[0]) / abs(einf[0]))}
+    if plan.precision != "fp64" and not args.no_fp64:
+        p64 = pkg.Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision="fp64", max_pairs=64)
+        eps64, ms64, kern64 = timed_inverse(p64, chi, 1)
+        einf64 = p64.eps_inf(0, eps64)
+        out.update({"ms_inverse_fp64": ms64, "tflops_fp64": flops / ms64 / 1e9, "kernel_ms_fp64": kern64,
+                    "eps_inf_fp64_vs_split_rel": float(abs(einf64[0] - einf[0]) / abs(einf64[0]))})
+        del eps64, p64
+    if not args.no_cpu:
+        from oracle.dielectric import epsilon_inverse
+        rng = np.random.default_rng(0)
+        E = np.eye(nG) + 0.01 * (rng.standard_normal((nG, nG)) + 1j * rng.standard_normal((nG, nG)))
+        t0 = time.time()
+        epsilon_inverse(E[None])
+        out["cpu_oracle_ms_one_matrix"] = (time.time() - t0) * 1e3
+        out["cpu_cores"] = os.cpu_count()
+    return out
+
+
 def oracle_sample(prob, nv: int, nc: int, seed_offset: int = 0):
     """Time the FP64 oracle on nv x nc pairs of the workload (wavefunctions,
     pair elements, factors, contraction).  Returns (seconds, flops, chi, bands)."""
@@ -340,6 +406,9 @@ def run_ours(args):
     acc_ms = e0.elapsed_time(e1) / 3
     plan.sync_status()
     acc_pairs = prob.n_v * len(c_sel)
+
+    # ---- dielectric matrix of both builds: eps = 1 - v chi0 (symmetrised), eps^-1, eps_inf ----
+    eps_info = None if args.no_eps else dielectric(args, pkg, prob, plan, chi, chi_a, dev)
     del chi_a
 
     # ---- the other split precision on the same build (reported beside the headline) ----
@@ -443,7 +512,8 @@ def run_ours(args):
             "accelerated": {"ms": acc_ms, "pairs": acc_pairs, "columns": len(c_sel),
                             "pair_ratio": n_pairs / acc_pairs, "speedup_vs_full": ms_step / acc_ms,
                             "N0": prob.N0, "dE_eV": 2.0},
-            "fp64_gpu": fp64, "variants": variants, "tuning": tuning, "clocks": clk.summary(), "input_gen_s": gen_s}
+            "fp64_gpu": fp64, "variants": variants, "tuning": tuning, "clocks": clk.summary(), "input_gen_s": gen_s,
+            "dielectric": eps_info}
 
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(prob, plan, psi_v, psi_c, Ev, Ec)
@@ -790,6 +860,7 @@ def main(argv=None):
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-eps", action="store_true", help="skip the dielectric-matrix measurement")
     ap.add_argument("--case", choices=["contract", "pairs", "c3", "c4", "c5"], default=None,
                     help="run a small fixed case for profiling (contract, pairs) or the 256-atom-sized "
                          "measurement (c5) instead of the benchmark")

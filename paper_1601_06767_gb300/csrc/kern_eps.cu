@@ -6,9 +6,11 @@
 // Inverse: blocked Gauss-Jordan elimination with partial pivoting, in place, on
 // all n_freq matrices at once (grid dimension z / x = frequency).  For each
 // panel of NB columns C1 = [k0, k0 + kb):
-//   1. k_gj_panel: copy the panel columns of every row to Z, LU-factor rows
-//      >= k0 of the panel with partial pivoting (row swaps inside the panel
-//      and in Z), then T = A11^-1 = U11^-1 L11^-1 of the pivot block;
+//   1. pivot rows among rows >= k0 by tournament pivoting (k_tp_select: GEPP
+//      on blocks of candidate rows in shared memory, winners merged level by
+//      level); k_tp_final moves the winners to R1 = [k0, k0 + kb) (recorded as
+//      a swap sequence), copies the panel columns of every row to Z and forms
+//      T = A11^-1 by Gauss-Jordan with partial pivoting on the pivot block;
 //   2. k_gj_rows: apply the row swaps to the other columns and replace the
 //      pivot rows R1 = [k0, k0 + kb) there by T A10;
 //   3. k_gj_update: every other row i: A[i][j] = A[i][j] - Z[i] . R[:, j] for
@@ -25,7 +27,6 @@ namespace chi0 {
 namespace {
 
 constexpr int NB = 32;          // panel width
-constexpr int PANEL_THREADS = 1024;
 constexpr int SINGULAR_BIT = 0x100;
 
 template <typename C> __device__ __forceinline__ C csub(C a, C b) {
@@ -64,117 +65,213 @@ __global__ void k_from_c64(const float2* __restrict__ b, int64_t n, double2* __r
 }
 
 // ---------------------------------------------------------------------------
-// 1. panel: Z copy, LU with partial pivoting of rows >= k0, T = A11^-1
+// 1. panel: pivot rows by tournament (communication-avoiding) pivoting, then
+//    the swaps, the Z copy and T = A11^-1
 // ---------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(PANEL_THREADS)
-k_gj_panel(typename Cx<R>::T* __restrict__ A, int N, int k0, int kb, typename Cx<R>::T* __restrict__ Z,
-           typename Cx<R>::T* __restrict__ Tb, int* __restrict__ piv, int* __restrict__ status) {
-  using C = typename Cx<R>::T;
-  const int w = blockIdx.x;
-  C* a = A + (size_t)w * N * N;
-  C* z = Z + (size_t)w * N * NB;
-  C* tb = Tb + (size_t)w * NB * NB;
-  int* pv = piv + (size_t)w * N;
-  __shared__ C urow[NB];
-  __shared__ C lu[NB][NB + 1];
-  __shared__ R red_v[PANEL_THREADS / 32];
-  __shared__ int red_i[PANEL_THREADS / 32];
-  __shared__ int s_piv;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+// rows of one selection block: 128 (FP32) or 64 (FP64) candidate rows in shared memory
+template <typename R> struct SelRows { static constexpr int V = sizeof(R) == 4 ? 128 : 64; };
 
-  for (int64_t e = tid; e < (int64_t)N * kb; e += blockDim.x) {
-    const int i = (int)(e / kb), t = (int)(e - (int64_t)i * kb);
-    z[(size_t)i * NB + t] = a[(size_t)i * N + k0 + t];
+// Gaussian elimination with partial pivoting on up to ROWS candidate rows of
+// the panel (their current values); the first kb pivot rows are the block's
+// winners.  Leaf level (cand_in == NULL): block c holds rows k0 + c*ROWS ...;
+// merge levels: block c holds entries c*ROWS ... of the previous level's list
+// (NB slots per set, -1 = empty).  Writes NB slots per block to cand_out.
+template <typename R>
+__global__ void __launch_bounds__(SelRows<R>::V)
+k_tp_select(const typename Cx<R>::T* __restrict__ A, int N, int k0, int kb, const int* __restrict__ cand_in,
+            int n_in, int* __restrict__ cand_out, int ld) {
+  using C = typename Cx<R>::T;
+  constexpr int ROWS = SelRows<R>::V;
+  const int w = blockIdx.y, c = blockIdx.x, r = threadIdx.x;
+  const C* a = A + (size_t)w * N * N;
+  __shared__ C S[ROWS][NB + 1];
+  __shared__ int idx[ROWS];
+  __shared__ R red_v[ROWS / 32];
+  __shared__ int red_i[ROWS / 32];
+  __shared__ int s_n, s_p, wcnt[ROWS / 32];
+  int g = -1;
+  if (cand_in == nullptr) {
+    const int row = k0 + c * ROWS + r;
+    g = row < N ? row : -1;
+  } else {
+    const int e = c * ROWS + r;
+    g = e < n_in ? cand_in[(size_t)w * ld + e] : -1;
+  }
+  // compact the valid rows to the front, keeping their order (deterministic ties)
+  const unsigned bal = __ballot_sync(0xffffffffu, g >= 0);
+  if ((r & 31) == 0) wcnt[r >> 5] = __popc(bal);
+  __syncthreads();
+  if (r == 0) {
+    int acc = 0;
+    for (int q = 0; q < ROWS / 32; ++q) {
+      const int n = wcnt[q];
+      wcnt[q] = acc;
+      acc += n;
+    }
+    s_n = acc;
   }
   __syncthreads();
-
-  for (int j = 0; j < kb; ++j) {
-    const int col = k0 + j, r0 = k0 + j;
-    // pivot: largest |re| + |im| in column col over rows >= r0 (ties: lowest row)
-    R best = (R)-1;
-    int bi = N;
-    for (int i = r0 + tid; i < N; i += blockDim.x) {
-      const R m = cabs1(a[(size_t)i * N + col]);
-      if (m > best) { best = m; bi = i; }
-    }
+  if (g >= 0) idx[wcnt[r >> 5] + __popc(bal & ((1u << (r & 31)) - 1u))] = g;
+  __syncthreads();
+  const int nr = s_n;
+  if (r < nr) {
+    const C* src = a + (size_t)idx[r] * N + k0;
+    for (int t = 0; t < kb; ++t) S[r][t] = src[t];
+  }
+  __syncthreads();
+  const int steps = min(kb, nr);
+  for (int j = 0; j < steps; ++j) {
+    R best = (r >= j && r < nr) ? cabs1(S[r][j]) : (R)-1;
+    int bi = (r >= j && r < nr) ? r : ROWS;
     for (int o = 16; o; o >>= 1) {
       const R ob = __shfl_xor_sync(0xffffffffu, best, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
-    if (lane == 0) { red_v[wid] = best; red_i[wid] = bi; }
+    if ((r & 31) == 0) { red_v[r >> 5] = best; red_i[r >> 5] = bi; }
     __syncthreads();
-    if (wid == 0) {
-      const int nw = blockDim.x >> 5;
-      best = lane < nw ? red_v[lane] : (R)-1;
-      bi = lane < nw ? red_i[lane] : N;
+    if (r == 0) {
+      for (int q = 1; q < ROWS / 32; ++q)
+        if (red_v[q] > best || (red_v[q] == best && red_i[q] < bi)) { best = red_v[q]; bi = red_i[q]; }
+      s_p = (bi < nr) ? bi : j;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != j) {
+      if (r < kb) {
+        const C u = S[j][r];
+        S[j][r] = S[p][r];
+        S[p][r] = u;
+      }
+      if (r == 0) {
+        const int u = idx[j];
+        idx[j] = idx[p];
+        idx[p] = u;
+      }
+    }
+    __syncthreads();
+    if (r > j && r < nr) {
+      const C piv = S[j][j];
+      if (piv.x != (R)0 || piv.y != (R)0) {
+        const C l = cmul(S[r][j], crecip(piv));
+        for (int t = j + 1; t < kb; ++t) S[r][t] = csub(S[r][t], cmul(l, S[j][t]));
+      }
+    }
+    __syncthreads();
+  }
+  if (r < NB) cand_out[(size_t)w * ld + (size_t)c * NB + r] = (r < steps) ? idx[r] : -1;
+}
+
+// Move the winners to rows k0..k0+kb-1 (recorded as a swap sequence in piv),
+// copy the panel columns of every row to Z, invert the pivot block by
+// Gauss-Jordan with partial pivoting in shared memory: T = A11^-1 (also
+// written over the pivot block).
+template <typename R>
+__global__ void __launch_bounds__(1024)
+k_tp_final(typename Cx<R>::T* __restrict__ A, int N, int k0, int kb, const int* __restrict__ win, int ld,
+           typename Cx<R>::T* __restrict__ Z, typename Cx<R>::T* __restrict__ Tb, int* __restrict__ piv,
+           int* __restrict__ status) {
+  using C = typename Cx<R>::T;
+  const int w = blockIdx.x, tid = threadIdx.x;
+  C* a = A + (size_t)w * N * N;
+  C* z = Z + (size_t)w * N * NB;
+  int* pv = piv + (size_t)w * N;
+  __shared__ int sp[NB];
+  __shared__ C B[NB][2 * NB + 1];
+  __shared__ int s_p;
+  if (tid == 0) {
+    // swap sequence: step t exchanges row k0+t with the current row of winner t
+    int orig[2 * NB], cur[2 * NB], n = 0;
+    for (int t = 0; t < kb; ++t) {
+      const int x = win[(size_t)w * ld + t];
+      int px = x;
+      for (int q = 0; q < n; ++q)
+        if (orig[q] == x) px = cur[q];
+      const int y = k0 + t;
+      int oy = y;
+      for (int q = 0; q < n; ++q)
+        if (cur[q] == y) oy = orig[q];
+      if (x < 0) px = y;     // fewer candidates than columns (cannot happen for kb <= N - k0)
+      sp[t] = px;
+      pv[y] = px;
+      if (px != y) {
+        // the row now at y (original oy) moves to px, winner x moves to y
+        bool fo = false, fx = false;
+        for (int q = 0; q < n; ++q) {
+          if (orig[q] == oy) { cur[q] = px; fo = true; }
+          else if (orig[q] == x) { cur[q] = y; fx = true; }
+        }
+        if (!fo) { orig[n] = oy; cur[n] = px; ++n; }
+        if (!fx) { orig[n] = x; cur[n] = y; ++n; }
+      }
+    }
+  }
+  __syncthreads();
+  for (int t = 0; t < kb; ++t) {
+    const int y = k0 + t, p = sp[t];
+    if (p != y && tid < kb) {
+      const C u = a[(size_t)y * N + k0 + tid];
+      a[(size_t)y * N + k0 + tid] = a[(size_t)p * N + k0 + tid];
+      a[(size_t)p * N + k0 + tid] = u;
+    }
+    __syncthreads();
+  }
+  for (int64_t e = tid; e < (int64_t)N * kb; e += blockDim.x) {
+    const int i = (int)(e / kb), t = (int)(e - (int64_t)i * kb);
+    z[(size_t)i * NB + t] = a[(size_t)i * N + k0 + t];
+  }
+  // [A11 | I] -> [I | A11^-1]
+  for (int e = tid; e < NB * 2 * NB; e += blockDim.x) {
+    const int i = e / (2 * NB), c = e - i * 2 * NB;
+    C v = cz(C{});
+    if (i < kb && c < kb) v = a[(size_t)(k0 + i) * N + k0 + c];
+    else if (i < kb && c >= NB && c - NB == i) v.x = (R)1;
+    B[i][c] = v;
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    if (tid < 32) {
+      R best = (tid >= j && tid < kb) ? cabs1(B[tid][j]) : (R)-1;
+      int bi = (tid >= j && tid < kb) ? tid : NB;
       for (int o = 16; o; o >>= 1) {
         const R ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      if (lane == 0) {
-        if (!(best > (R)0) || bi >= N) {
+      if (tid == 0) {
+        if (!(best > (R)0) || bi >= kb) {
           atomicOr(status, SINGULAR_BIT);
-          bi = r0;
+          bi = j;
         }
-        s_piv = bi;
-        pv[r0] = bi;
+        s_p = bi;
       }
     }
     __syncthreads();
-    const int p = s_piv;
-    if (p != r0 && tid < kb) {
-      C t0 = a[(size_t)r0 * N + k0 + tid];
-      a[(size_t)r0 * N + k0 + tid] = a[(size_t)p * N + k0 + tid];
-      a[(size_t)p * N + k0 + tid] = t0;
-      C t1 = z[(size_t)r0 * NB + tid];
-      z[(size_t)r0 * NB + tid] = z[(size_t)p * NB + tid];
-      z[(size_t)p * NB + tid] = t1;
+    const int p = s_p;
+    if (p != j && tid < 2 * NB) {
+      const C u = B[j][tid];
+      B[j][tid] = B[p][tid];
+      B[p][tid] = u;
     }
     __syncthreads();
-    if (tid < kb) urow[tid] = a[(size_t)r0 * N + k0 + tid];
+    const C inv = crecip(B[j][j]);
     __syncthreads();
-    const C inv = crecip(urow[j]);
-    for (int i = r0 + 1 + tid; i < N; i += blockDim.x) {
-      C* row = a + (size_t)i * N + k0;
-      const C l = cmul(row[j], inv);
-      row[j] = l;
-      for (int c = j + 1; c < kb; ++c) row[c] = csub(row[c], cmul(l, urow[c]));
+    if (tid < 2 * NB) B[j][tid] = cmul(B[j][tid], inv);
+    __syncthreads();
+    // eliminate column j from every other row: thread (i, c)
+    for (int e = tid; e < NB * 2 * NB; e += blockDim.x) {
+      const int i = e / (2 * NB), c = e - i * 2 * NB;
+      if (i != j && i < kb && c != j) B[i][c] = csub(B[i][c], cmul(B[i][j], B[j][c]));
     }
+    __syncthreads();
+    if (tid < NB && tid != j) B[tid][j] = cz(C{});
     __syncthreads();
   }
-
-  // T = U11^-1 L11^-1 of the kb x kb pivot block (thread t: column t)
   for (int e = tid; e < kb * kb; e += blockDim.x) {
     const int i = e / kb, c = e - i * kb;
-    lu[i][c] = a[(size_t)(k0 + i) * N + k0 + c];
-  }
-  __syncthreads();
-  if (tid < kb) {
-    const int t = tid;
-    C x[NB];
-    // x = L^-1 e_t (L unit lower triangular): x_i = 0 (i < t), 1 (i = t), -sum_{t<=q<i} L_iq x_q
-    for (int i = 0; i < kb; ++i) {
-      C s = cz(C{});
-      if (i == t) s.x = (R)1;
-      for (int q = t; q < i; ++q) s = csub(s, cmul(lu[i][q], x[q]));
-      x[i] = s;
-    }
-    // x = U^-1 x (back substitution)
-    for (int i = kb - 1; i >= 0; --i) {
-      C s = x[i];
-      for (int q = i + 1; q < kb; ++q) s = csub(s, cmul(lu[i][q], x[q]));
-      x[i] = cmul(s, crecip(lu[i][i]));
-    }
-    for (int i = 0; i < kb; ++i) tb[i * NB + t] = x[i];
-  }
-  __syncthreads();
-  // the pivot block becomes T
-  for (int e = tid; e < kb * kb; e += blockDim.x) {
-    const int i = e / kb, c = e - i * kb;
-    a[(size_t)(k0 + i) * N + k0 + c] = tb[i * NB + c];
+    const C t = B[i][NB + c];
+    Tb[(size_t)w * NB * NB + i * NB + c] = t;
+    a[(size_t)(k0 + i) * N + k0 + c] = t;
   }
 }
 
@@ -299,15 +396,31 @@ __global__ void k_gj_colperm(typename Cx<R>::T* __restrict__ A, int N, const int
   }
 }
 
+// candidate-list slots per matrix for an N-row panel (ping-pong pair)
+template <typename R> int64_t tp_ld(int N) { return (int64_t)((N + SelRows<R>::V - 1) / SelRows<R>::V) * NB; }
+
 template <typename R>
 cudaError_t gj_invert(chi0_plan_s* p, typename Cx<R>::T* A, int N, int nf, void* Z, void* Tb, int* piv,
-                      cudaStream_t s) {
+                      int* cand, cudaStream_t s) {
   using C = typename Cx<R>::T;
+  constexpr int ROWS = SelRows<R>::V;
+  const int ld = (int)tp_ld<R>(N);
+  int* cbuf[2] = {cand, cand + (size_t)nf * ld};
   for (int k0 = 0; k0 < N; k0 += NB) {
     const int kb = min(NB, N - k0);
     {
-      ProfScope ps(p, CHI0_K_INV_PANEL, s, 2);
-      k_gj_panel<R><<<nf, PANEL_THREADS, 0, s>>>(A, N, k0, kb, (C*)Z, (C*)Tb, piv, p->d_status);
+      // tournament: leaf blocks of ROWS rows, then merges of ROWS / NB sets until one is left
+      int nblk = (N - k0 + ROWS - 1) / ROWS, levels = 1, cur = 0;
+      for (int b = nblk; b > 1; b = (b * NB + ROWS - 1) / ROWS) ++levels;
+      ProfScope ps(p, CHI0_K_INV_PANEL, s, levels + 2);
+      k_tp_select<R><<<dim3(nblk, nf), ROWS, 0, s>>>(A, N, k0, kb, nullptr, 0, cbuf[0], ld);
+      while (nblk > 1) {
+        const int n_in = nblk * NB;
+        nblk = (n_in + ROWS - 1) / ROWS;
+        k_tp_select<R><<<dim3(nblk, nf), ROWS, 0, s>>>(A, N, k0, kb, cbuf[cur], n_in, cbuf[cur ^ 1], ld);
+        cur ^= 1;
+      }
+      k_tp_final<R><<<nf, 1024, 0, s>>>(A, N, k0, kb, cbuf[cur], ld, (C*)Z, (C*)Tb, piv, p->d_status);
       k_gj_rows<R><<<dim3((N + 127) / 128, nf), 128, 0, s>>>(A, N, k0, kb, (const C*)Tb, piv);
     }
     {
@@ -335,12 +448,15 @@ cudaError_t launch_epsilon(chi0_plan_s* p, int nG, const double2* chi, const dou
   return cudaGetLastError();
 }
 
-// Workspace (bytes): complex64 copy of the matrices (split plans), Z [nf][N][NB], T [nf][NB][NB], piv [nf][N].
+// Workspace (bytes): complex64 copy of the matrices (split plans), Z [nf][N][NB], T [nf][NB][NB],
+// piv [nf][N], two candidate lists [nf][tp_ld].
 size_t eps_inverse_ws_bytes(const chi0_plan_s* p, int nG) {
   const size_t nf = (size_t)p->n_freq, c = is_split(p) ? sizeof(float2) : sizeof(double2);
   const size_t copy = is_split(p) ? nf * nG * nG * sizeof(float2) : 0;
+  const size_t ld = (size_t)(is_split(p) ? tp_ld<float>(nG) : tp_ld<double>(nG));
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-  return al(copy) + al(nf * nG * NB * c) + al(nf * NB * NB * c) + al(nf * nG * sizeof(int));
+  return al(copy) + al(nf * nG * NB * c) + al(nf * NB * NB * c) + al(nf * nG * sizeof(int)) +
+         al(2 * nf * ld * sizeof(int));
 }
 
 cudaError_t launch_epsilon_inverse(chi0_plan_s* p, int nG, double2* eps, void* ws, cudaStream_t s) {
@@ -355,12 +471,14 @@ cudaError_t launch_epsilon_inverse(chi0_plan_s* p, int nG, double2* eps, void* w
     void* Tb = b;
     b += al(nf * NB * NB * sizeof(float2));
     int* piv = reinterpret_cast<int*>(b);
+    b += al(nf * nG * sizeof(int));
+    int* cand = reinterpret_cast<int*>(b);
     const int64_t n = (int64_t)nf * nG * nG;
     {
       ProfScope ps(p, CHI0_K_EPS, s, 1);
       k_to_c64<<<4 * 152, 256, 0, s>>>(eps, n, a32);
     }
-    cudaError_t e = gj_invert<float>(p, a32, nG, (int)nf, Z, Tb, piv, s);
+    cudaError_t e = gj_invert<float>(p, a32, nG, (int)nf, Z, Tb, piv, cand, s);
     if (e != cudaSuccess) return e;
     ProfScope ps(p, CHI0_K_EPS, s, 1);
     k_from_c64<<<4 * 152, 256, 0, s>>>(a32, n, eps);
@@ -371,7 +489,9 @@ cudaError_t launch_epsilon_inverse(chi0_plan_s* p, int nG, double2* eps, void* w
   void* Tb = b;
   b += al(nf * NB * NB * sizeof(double2));
   int* piv = reinterpret_cast<int*>(b);
-  return gj_invert<double>(p, eps, nG, (int)nf, Z, Tb, piv, s);
+  b += al(nf * nG * sizeof(int));
+  int* cand = reinterpret_cast<int*>(b);
+  return gj_invert<double>(p, eps, nG, (int)nf, Z, Tb, piv, cand, s);
 }
 
 }  // namespace chi0
