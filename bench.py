@@ -546,7 +546,8 @@ def cpu_baseline(prob, plan, psi_v, psi_c, Ev, Ec):
 def run_case(args):
     """Small fixed cases for ncu captures (no JSON line): 'contract' = two
     accumulate calls of 8192 pairs on the 2500-vector sphere with 9
-    frequencies; 'pairs' = two pair-element calls of 128 x 64 pairs on 48^3."""
+    frequencies; 'pairs' = two pair-element calls of 128 x 64 pairs on 48^3;
+    'eps' = two dielectric inverses of 9 matrices of the 2500-vector sphere."""
     import torch
     import paper_1601_06767_gb300 as pkg
     from synth import make_problem
@@ -560,6 +561,18 @@ def run_case(args):
                       gw=prob.gw, n_products=args.n_products, hermitian=herm) as plan:
         if args.case == "contract" and not args.no_tune:
             plan.autotune(0)          # the variant the benchmark runs
+        if args.case == "eps":
+            # 9 dielectric matrices of the 2500-vector sphere from a rank-600 static-like chi0
+            R = torch.randn(600, nG, dtype=torch.complex128, device="cuda", generator=g) / (2 * nG) ** 0.5
+            u = torch.rand(600, dtype=torch.float64, device="cuda", generator=g) * 0.9 + 0.1
+            chi1 = -(R.T * u) @ R.conj()
+            chi = chi1.unsqueeze(0).repeat(prob.omega.size, 1, 1).contiguous()
+            v = torch.from_numpy(plan.coulomb(0, prob.a * np.eye(3), prob.q_frac[0])).cuda()
+            for _ in range(2):
+                eps = plan.epsilon(0, chi, v, symmetric=True)
+                plan.epsilon_inverse(0, eps)
+            plan.sync_status()
+            return 0
         M = torch.randn(K, nG, dtype=torch.complex64, device="cuda", generator=g) * 4e-3
         if args.case == "contract":
             Ev = torch.tensor(prob.E_v[:nv], device="cuda")
@@ -861,7 +874,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-eps", action="store_true", help="skip the dielectric-matrix measurement")
-    ap.add_argument("--case", choices=["contract", "pairs", "c3", "c4", "c5"], default=None,
+    ap.add_argument("--case", choices=["contract", "pairs", "eps", "c3", "c4", "c5"], default=None,
                     help="run a small fixed case for profiling (contract, pairs) or the 256-atom-sized "
                          "measurement (c5) instead of the benchmark")
     ap.add_argument("--c5-frac", type=float, default=1.0, help="fraction of conduction bands timed in --case c5")
