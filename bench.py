@@ -183,6 +183,38 @@ def h2_products(Ev, Ec, omega, delta, n_prod):
     return np.array(out)
 
 
+def quadrature_study(pkg, prob, plan, chi, psi_v, psi_c, Ev, cv, cc, dev):
+    """Eq. 3 with different quadratures of its integral (same N0 and dE): build
+    time and relative Frobenius distance of the static chi0 from the full sum
+    (both from this GPU path).  With random synthetic wavefunctions M is not
+    smooth in energy, so the distance is dominated by the sampling of M, which
+    several states per node reduce."""
+    import torch
+    plan.wfn_to_grid(cv, out=psi_v)
+    plan.wfn_to_grid(cc, out=psi_c)
+    ref = chi[0]
+    ref_norm = float(torch.linalg.vector_norm(ref))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = []
+    for grid, rule, states in (("uniform", "midpoint", 1), ("quantile", "midpoint", 1), ("uniform", "simpson", 1),
+                               ("uniform", "gauss2", 1), ("uniform", "midpoint", 4), ("quantile", "simpson", 2)):
+        c_sel, E_sel, w_sel = pkg.select_quadrature(prob.E_c, prob.N0, prob.dE, prob.dos_A, prob.dos_V0,
+                                                    prob.E_max, grid, rule, states)
+        c_idx = torch.from_numpy(c_sel).to(dev)
+        Ecol, wcol = torch.from_numpy(E_sel).to(dev), torch.from_numpy(w_sel).to(dev)
+        chi_q = plan.new_chi(0)
+        e0.record()
+        plan.build(0, psi_v, Ev, psi_c, Ecol, w_col=wcol, c_idx=c_idx, chi=chi_q)
+        e1.record()
+        torch.cuda.synchronize()
+        plan.sync_status()
+        err = float(torch.linalg.vector_norm(chi_q[0] - ref)) / ref_norm
+        out.append({"grid": grid, "rule": rule, "states": states, "columns": int(c_sel.size),
+                    "ms": e0.elapsed_time(e1), "rel_err_static_vs_full": err})
+        del chi_q
+    return out
+
+
 def dielectric(args, pkg, prob, plan, chi, chi_a, dev):
     """eps = 1 - v^1/2 chi0 v^1/2, its inverse and eps_inf for the full and the
     accelerated chi0 of the benchmark workload (section II, Table III): device
@@ -411,6 +443,9 @@ def run_ours(args):
     eps_info = None if args.no_eps else dielectric(args, pkg, prob, plan, chi, chi_a, dev)
     del chi_a
 
+    # ---- quadrature variants of the accelerated sum: error against the full sum vs cost ----
+    quad_info = None if args.no_quad else quadrature_study(pkg, prob, plan, chi, psi_v, psi_c, Ev, cv, cc, dev)
+
     # ---- the other split precision on the same build (reported beside the headline) ----
     variants = {}
     if not args.no_variants:
@@ -513,7 +548,7 @@ def run_ours(args):
                             "pair_ratio": n_pairs / acc_pairs, "speedup_vs_full": ms_step / acc_ms,
                             "N0": prob.N0, "dE_eV": 2.0},
             "fp64_gpu": fp64, "variants": variants, "tuning": tuning, "clocks": clk.summary(), "input_gen_s": gen_s,
-            "dielectric": eps_info}
+            "dielectric": eps_info, "quadrature": quad_info}
 
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(prob, plan, psi_v, psi_c, Ev, Ec)
@@ -874,6 +909,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-eps", action="store_true", help="skip the dielectric-matrix measurement")
+    ap.add_argument("--no-quad", action="store_true", help="skip the quadrature variants of Eq. 3")
     ap.add_argument("--case", choices=["contract", "pairs", "eps", "c3", "c4", "c5"], default=None,
                     help="run a small fixed case for profiling (contract, pairs) or the 256-atom-sized "
                          "measurement (c5) instead of the benchmark")

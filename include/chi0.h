@@ -253,6 +253,30 @@ chi0_status chi0_accumulate_fp64_noalloc(int n_G, const void* M, int n_v, int n_
                                          const double* freq_re, const double* freq_im, double delta,
                                          void* chi0, void* stream);
 
+/* Non-uniform and higher-order quadrature of the Eq. 3 integral (the text
+ * after Eq. 4 allows uniform or non-uniform grids and higher-order rules), with
+ * several states per node (host arrays, host computation).  Columns
+ * 0..N0-1 are the explicit bands (own energy, weight 1).  The interval
+ * [E_0, E_max], E_0 = E_c[N0-1], is cut into N_E = ceil((E_max-E_0)/dE) bins:
+ *   grid 0: edges E_0 + k dE, the last clipped at E_max (Eq. 4);
+ *   grid 1: equal counts of g between neighbouring edges, i.e.
+ *           A c (e_k - V0)^(3/2) = A c (E_0 - V0)^(3/2) + k/N_E [A c (E_max - V0)^(3/2) - A c (E_0 - V0)^(3/2)],
+ *           c = 2 sqrt(2)/3, the integral of g(E) = A sqrt(2 (E - V0)).
+ * Nodes and raw weights per bin [a, b], h = b - a:
+ *   rule 0: midpoint (a+b)/2, h (Eq. 4);
+ *   rule 1: Simpson a, (a+b)/2, b with h/6, 4h/6, h/6 (shared ends merged into one node);
+ *   rule 2: two-point Gauss-Legendre (a+b)/2 -+ h/(2 sqrt 3), h/2 each.
+ * Each node E_k with weight W_k = g(E_k) x raw weight contributes `states`
+ * columns: the bands above N0 nearest in energy to E_k (ties to the lower
+ * index, in order of distance), each with energy E_k and weight W_k / states
+ * (all bands above N0 if there are fewer).  grid 0, rule 0, states 1 gives
+ * exactly chi0_select_accelerated.  Returns the number of columns written to
+ * c_sel (host int32), E_sel, w_sel (host double), or -1 for bad arguments,
+ * unsorted E_c or more than cap columns. */
+int chi0_select_quadrature(const double* E_c, int n_c, int N0, double dE, double dos_A, double dos_V0,
+                           double E_max, int grid, int rule, int states, int32_t* c_sel, double* E_sel,
+                           double* w_sel, int cap);
+
 /* ---- Dielectric matrix (section II: eps = 1 - v chi0, W = eps^-1 v; Table III:
  * eps_inf = 1 / [eps^-1]_{00}(q -> 0, omega = 0)).  Hartree atomic units. ---- */
 

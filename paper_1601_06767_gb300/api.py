@@ -254,6 +254,28 @@ class Chi0Plan:
         return out[0::2] + 1j * out[1::2]
 
 
+QUAD_GRIDS = {"uniform": 0, "quantile": 1}
+QUAD_RULES = {"midpoint": 0, "simpson": 1, "gauss2": 2}
+
+
+def select_quadrature(E_c, N0: int, dE: float, dos_A: float, dos_V0: float, E_max: float,
+                      grid: str = "uniform", rule: str = "midpoint", states: int = 1):
+    """Columns of Eq. 3 with a non-uniform / higher-order quadrature and several
+    states per node (chi0_select_quadrature): (band index, energy, weight)."""
+    E_c = _f64(E_c)
+    n_bins = int(np.ceil(max(E_max - E_c[min(max(N0, 1), E_c.size) - 1], 0) / dE)) + 1 if E_c.size else 0
+    cap = int(N0) + (2 * n_bins + 1) * max(int(states), 1) + 2
+    c_sel = np.empty(cap, np.int32)
+    E_sel = np.empty(cap, np.float64)
+    w_sel = np.empty(cap, np.float64)
+    n = L.lib().chi0_select_quadrature(E_c.ctypes.data, E_c.size, int(N0), float(dE), float(dos_A),
+                                       float(dos_V0), float(E_max), QUAD_GRIDS[grid], QUAD_RULES[rule],
+                                       int(states), c_sel.ctypes.data, E_sel.ctypes.data, w_sel.ctypes.data, cap)
+    if n < 0:
+        raise L.Chi0Error(L.CHI0_ERR_INVALID, "chi0_select_quadrature rejected its input")
+    return c_sel[:n].copy(), E_sel[:n].copy(), w_sel[:n].copy()
+
+
 def select_accelerated(E_c, N0: int, dE: float, dos_A: float, dos_V0: float, E_max: float):
     """Columns of Eq. 3/4 from chi0_select_accelerated: (band index, energy, weight)."""
     E_c = _f64(E_c)

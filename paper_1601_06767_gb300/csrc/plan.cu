@@ -804,4 +804,76 @@ int chi0_select_accelerated(const double* E_c, int n_c, int N0, double dE, doubl
   return n;
 }
 
+int chi0_select_quadrature(const double* E_c, int n_c, int N0, double dE, double dos_A, double dos_V0,
+                           double E_max, int grid, int rule, int states, int32_t* c_sel, double* E_sel,
+                           double* w_sel, int cap) {
+  if (!E_c || n_c < 0 || N0 < 0 || !(dE > 0.0) || !c_sel || !E_sel || !w_sel || cap < 0) return -1;
+  if (grid < 0 || grid > 1 || rule < 0 || rule > 2 || states < 1) return -1;
+  for (int i = 1; i < n_c; ++i)
+    if (E_c[i] < E_c[i - 1]) return -1;
+  N0 = std::min(N0, n_c);
+  int n = 0;
+  for (int c = 0; c < N0; ++c) {            // explicit part of Eq. 3
+    if (n >= cap) return -1;
+    c_sel[n] = c; E_sel[n] = E_c[c]; w_sel[n] = 1.0; ++n;
+  }
+  if (N0 == 0 || N0 >= n_c) return n;
+  const double E0 = E_c[N0 - 1];
+  int NE = (int)ceil((E_max - E0) / dE - 1e-12);
+  if (NE <= 0) return n;
+  // bin edges: uniform steps of dE (Eq. 4), or equal counts of g(E) = A sqrt(2 (E - V0))
+  std::vector<double> edge(NE + 1);
+  if (grid == 0) {
+    for (int k = 0; k <= NE; ++k) edge[k] = std::min(E0 + dE * k, E_max);
+  } else {
+    const double c3 = 2.0 * sqrt(2.0) / 3.0;   // int_V0^E g = A c3 (E - V0)^(3/2)
+    const double G0 = dos_A * c3 * pow(std::max(E0 - dos_V0, 0.0), 1.5);
+    const double G1 = dos_A * c3 * pow(std::max(E_max - dos_V0, 0.0), 1.5);
+    for (int k = 0; k <= NE; ++k) {
+      const double Gk = G0 + (G1 - G0) * (double)k / (double)NE;
+      edge[k] = dos_V0 + pow(Gk / (dos_A * c3), 2.0 / 3.0);
+    }
+    edge[0] = E0;
+    edge[NE] = E_max;
+  }
+  // nodes and raw weights of the composite rule (ascending)
+  std::vector<double> node, raw;
+  for (int k = 0; k < NE; ++k) {
+    const double a = edge[k], b = edge[k + 1], h = b - a, m = 0.5 * (a + b);
+    if (rule == 0) {                        // midpoint
+      node.push_back(m); raw.push_back(h);
+    } else if (rule == 2) {                 // two-point Gauss-Legendre
+      const double d = h / (2.0 * sqrt(3.0));
+      node.push_back(m - d); raw.push_back(0.5 * h);
+      node.push_back(m + d); raw.push_back(0.5 * h);
+    } else {                                // Simpson, shared ends merged
+      if (k == 0) { node.push_back(a); raw.push_back(0.0); }
+      raw.back() += h / 6.0;
+      node.push_back(m); raw.push_back(4.0 * h / 6.0);
+      node.push_back(b); raw.push_back(h / 6.0);
+    }
+  }
+  const int avail = n_c - N0, take = std::min(states, avail);
+  std::vector<char> used((size_t)avail);
+  for (size_t k = 0; k < node.size(); ++k) {
+    const double Ek = node[k];
+    const double g = (Ek > dos_V0) ? dos_A * sqrt(2.0 * (Ek - dos_V0)) : 0.0;
+    const double W = g * raw[k];
+    std::fill(used.begin(), used.end(), 0);
+    for (int t = 0; t < take; ++t) {        // next nearest band above N0 (ties: lower index)
+      int best = -1;
+      double bd = 0.0;
+      for (int c = N0; c < n_c; ++c) {
+        if (used[c - N0]) continue;
+        const double d = fabs(E_c[c] - Ek);
+        if (best < 0 || d < bd) { best = c; bd = d; }
+      }
+      used[best - N0] = 1;
+      if (n >= cap) return -1;
+      c_sel[n] = best; E_sel[n] = Ek; w_sel[n] = W / take; ++n;
+    }
+  }
+  return n;
+}
+
 }  // extern "C"

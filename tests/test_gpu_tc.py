@@ -200,3 +200,34 @@ def test_hermitian_mode_real_frequencies(pair, monkeypatch):
     errs = [rel_fro(chi[i], ref[i]) for i in range(omega.size)]
     print(f"\nhermitian real omega pair={pair}: {['%.2e' % e for e in errs]}")
     assert max(errs) < TOL
+
+
+@pytest.mark.parametrize("precision,tol", [("bf16", TOL), ("fp64", 1e-12)])
+@pytest.mark.parametrize("grid,rule,states", [("quantile", "midpoint", 1), ("uniform", "simpson", 2),
+                                              ("quantile", "gauss2", 3)])
+def test_build_quadrature_selection(precision, tol, grid, rule, states):
+    """Eq. 3 with a non-uniform / higher-order quadrature and several states
+    per node: the library's selection feeds chi0_build, the oracle's selection
+    feeds the oracle contraction."""
+    from oracle.quadrature import select_quadrature as oracle_select
+    from paper_1601_06767_gb300 import Chi0Plan, select_quadrature
+    prob = make_problem("c1", N0=40, dE_eV=3.0, n_imag=1)
+    ref_sel = oracle_select(prob.E_c, prob.N0, prob.dE, prob.dos_A, prob.dos_V0, prob.E_max, grid, rule, states)
+    c_sel, E_sel, w_sel = select_quadrature(prob.E_c, prob.N0, prob.dE, prob.dos_A, prob.dos_V0, prob.E_max,
+                                            grid, rule, states)
+    cv, cc = prob.coeff_v(0), prob.coeff_c()
+    uv, uc = wfn_to_grid(cv, prob.gw, prob.n), wfn_to_grid(cc, prob.gw, prob.n)
+    M = pair_elements(uv, uc[ref_sel["cols"]], prob.gvec[0], prob.n)
+    dE = (prob.E_v[:, None] - ref_sel["E_col"][None, :]).reshape(-1)
+    w = np.broadcast_to(ref_sel["w_col"][None, :], (prob.n_v, ref_sel["cols"].size)).reshape(-1)
+    ref = chi0_from_pairs(M, freq_factor(dE, w, prob.omega, prob.delta))
+    with Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision=precision, gw=prob.gw,
+                  max_pairs=512) as plan:
+        psi_v = plan.wfn_to_grid(_dev(cv))
+        psi_c = plan.wfn_to_grid(_dev(cc))
+        chi = plan.build(0, psi_v, _dev(prob.E_v), psi_c, _dev(E_sel), w_col=_dev(w_sel),
+                         c_idx=_dev(c_sel.astype(np.int32)))
+        plan.sync_status()
+        chi = chi.cpu().numpy()
+    for iw in range(prob.omega.size):
+        assert rel_fro(chi[iw], ref[iw]) < tol
