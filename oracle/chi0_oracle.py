@@ -186,6 +186,22 @@ def chi0_full(prob, iq: int = 0, coeff_v=None, coeff_c=None, v_bands=None, c_ban
     return chi0_from_pairs(M, f)
 
 
+def chi0_k_points(prob, iq: int = 0, n_k: int = 2, v_bands=None, c_bands=None):
+    """Eq. 1 with its sum over k written out: chi0 = sum_k chi0_k, where chi0_k
+    pairs the valence set at k + q with the conduction set at k (energies
+    prob.E_v and prob.E_c_k(k))."""
+    v_bands = np.arange(prob.n_v) if v_bands is None else np.asarray(v_bands)
+    c_bands = np.arange(prob.n_c) if c_bands is None else np.asarray(c_bands)
+    total = 0
+    for ik in range(n_k):
+        u_v = wfn_to_grid(prob.coeff_v(iq, v_bands, ik=ik), prob.gw, prob.n)
+        u_c = wfn_to_grid(prob.coeff_c(c_bands, ik=ik), prob.gw, prob.n)
+        M = pair_elements(u_v, u_c, prob.gvec[iq], prob.n)
+        dE = (prob.E_v[v_bands][:, None] - prob.E_c_k(ik)[c_bands][None, :]).reshape(-1)
+        total = total + chi0_from_pairs(M, freq_factor(dE, np.ones_like(dE), prob.omega, prob.delta))
+    return total
+
+
 def chi0_accelerated(prob, iq: int = 0, N0=None, dE=None, coeff_v=None):
     """chi0 of Eq. 3 with the integral done by Eq. 4 (frequency factor of Eq. 1
     with E_c replaced by the grid energy E_i for the integration states)."""

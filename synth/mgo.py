@@ -24,7 +24,10 @@ the same shapes stands in for them):
   A = N_c / (sqrt(2) * (2/3) * 2.03^(3/2)) so that g integrates to N_c on
   [V0, E_max];
 * frequencies: omega = 0 plus n_imag imaginary frequencies i*w, w log-spaced
-  from 0.01 to 2 Ha; broadening delta = 1e-3 Ha.
+  from 0.01 to 2 Ha; broadening delta = 1e-3 Ha;
+* k-points (the sum over k of Eq. 1): k-point ik has its own conduction and
+  valence streams and conduction energies E_c + 0.004 ik Ha; k-point 0 is the
+  single-k workload.
 """
 from __future__ import annotations
 
@@ -149,13 +152,32 @@ class Problem:
     def n_q(self) -> int:
         return len(self.gvec)
 
-    def coeff_c(self, bands=None) -> np.ndarray:
+    def coeff_c(self, bands=None, ik: int = 0) -> np.ndarray:
         bands = np.arange(self.n_c) if bands is None else bands
-        return band_coefficients(self.seed, 0, bands, self.npw)
+        return band_coefficients(self.seed, _stream_c(ik), bands, self.npw)
 
-    def coeff_v(self, iq: int = 0, bands=None) -> np.ndarray:
+    def coeff_v(self, iq: int = 0, bands=None, ik: int = 0) -> np.ndarray:
         bands = np.arange(self.n_v) if bands is None else bands
-        return band_coefficients(self.seed, 1 + iq, bands, self.npw)
+        return band_coefficients(self.seed, _stream_v(ik, iq), bands, self.npw)
+
+    def E_c_k(self, ik: int = 0) -> np.ndarray:
+        """Conduction energies at k-point ik: E_c shifted by K_SHIFT_HA * ik."""
+        return self.E_c + K_SHIFT_HA * ik
+
+
+# k-points: k-point 0 uses the streams above (0 = conduction at k, 1 + iq =
+# valence at k + q); k-point ik > 0 draws from its own streams; its conduction
+# energies are shifted by K_SHIFT_HA * ik (a small dispersion), the valence
+# energies are shared.
+K_SHIFT_HA = 0.004
+
+
+def _stream_c(ik: int) -> int:
+    return 0 if ik == 0 else 100000 + 1000 * ik
+
+
+def _stream_v(ik: int, iq: int) -> int:
+    return 1 + iq if ik == 0 else 100000 + 1000 * ik + 1 + iq
 
 
 def make_problem(name: str = "custom", *, n_v=None, n_c=None, n=None, n_G=None,

@@ -105,3 +105,29 @@ def test_linearity_over_pair_blocks(block):
     whole = chi0_from_pairs(M, f, block=block)
     parts = chi0_from_pairs(M[:11], f[:, :11]) + chi0_from_pairs(M[11:], f[:, 11:])
     assert rel_fro(parts, whole) < 1e-14
+
+
+def test_k_point_sum_is_the_triple_loop():
+    """Eq. 1's sum over k: chi0_k_points equals the direct loop over (k, v, c)
+    on a tiny case, and its k = 0 term is the single-k chi0."""
+    from oracle import chi0_full, chi0_k_points, pair_elements, wfn_to_grid
+    from synth import make_problem
+    prob = make_problem("c1", n_G=[20], n_imag=1)
+    vb, cb = np.arange(2), np.arange(3)
+    got = chi0_k_points(prob, 0, 2, v_bands=vb, c_bands=cb)
+    ref = np.zeros_like(got)
+    for ik in range(2):
+        u_v = wfn_to_grid(prob.coeff_v(0, vb, ik=ik), prob.gw, prob.n)
+        u_c = wfn_to_grid(prob.coeff_c(cb, ik=ik), prob.gw, prob.n)
+        M = pair_elements(u_v, u_c, prob.gvec[0], prob.n).reshape(2, 3, -1)
+        for iv in range(2):
+            for ic in range(3):
+                dE = prob.E_v[iv] - prob.E_c_k(ik)[ic]
+                for iw, om in enumerate(prob.omega):
+                    f = 0.5 * (1 / (dE - om + 1j * prob.delta) + 1 / (dE + om + 1j * prob.delta))
+                    ref[iw] += f * np.outer(M[iv, ic], M[iv, ic].conj())
+    assert rel_fro(got, ref) < 1e-14
+    one = chi0_k_points(prob, 0, 1, v_bands=vb, c_bands=cb)
+    assert rel_fro(one, chi0_full(prob, 0, v_bands=vb, c_bands=cb)) < 1e-15
+    # the second k-point brings different states (not a copy of the first)
+    assert rel_fro(got - one, one) > 0.1
