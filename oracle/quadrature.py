@@ -115,3 +115,55 @@ def select_quadrature(E_c: np.ndarray, N0: int, dE: float, A: float, V0: float, 
     out.update(cols=np.asarray(cols, dtype=np.int64), E_col=np.asarray(Ecol, dtype=np.float64),
                w_col=np.asarray(wcol, dtype=np.float64), N0=N0)
     return out
+
+
+def bin_error(E_c: np.ndarray, sens: np.ndarray, N0: int, a: float, b: float, last: bool) -> float:
+    """First-order change of a loss L when the bands above N0 with energy in
+    [a, b) (or [a, b] for the last bin) take the bin's midpoint energy:
+    |sum_c dL/dE_c (m - E_c)|, the per-bin share of the energy-substitution
+    estimate computed with the adjoint of Eq. 1 (sens = dL/dE_c)."""
+    E = E_c[N0:]
+    s = sens[N0:]
+    inside = (E >= a) & ((E <= b) if last else (E < b))
+    m = 0.5 * (a + b)
+    return float(abs(np.sum(s[inside] * (m - E[inside]))))
+
+
+def adaptive_edges(E_c: np.ndarray, sens: np.ndarray, N0: int, dE: float, E_max: float, n_split: int) -> np.ndarray:
+    """Start from the uniform Eq. 4 grid of step dE on [E_0, E_max] and split,
+    n_split times, the bin with the largest bin_error at its midpoint (ties: the
+    lowest bin)."""
+    E_c = np.asarray(E_c, dtype=np.float64)
+    sens = np.asarray(sens, dtype=np.float64)
+    E0 = E_c[N0 - 1]
+    edges = list(bin_edges(E0, E_max, dE, 1.0, 0.0, "uniform"))
+    for _ in range(n_split):
+        nb = len(edges) - 1
+        if nb <= 0:
+            break
+        errs = [bin_error(E_c, sens, N0, edges[k], edges[k + 1], k == nb - 1) for k in range(nb)]
+        k = int(np.argmax(errs))                      # first maximum = lowest bin on ties
+        edges.insert(k + 1, 0.5 * (edges[k] + edges[k + 1]))
+    return np.asarray(edges)
+
+
+def select_adaptive(E_c: np.ndarray, sens: np.ndarray, N0: int, dE: float, A: float, V0: float, E_max: float,
+                    n_split: int, states: int = 1) -> dict:
+    """Columns of Eq. 3 on the adaptive grid (midpoint rule, `states` states per node)."""
+    E_c = np.asarray(E_c, dtype=np.float64)
+    n_c = E_c.size
+    N0 = int(min(max(N0, 0), n_c))
+    cols, Ecol, wcol = list(range(N0)), list(E_c[:N0]), [1.0] * N0
+    edges = np.zeros(0)
+    if N0 > 0 and N0 < n_c and dE > 0:
+        edges = adaptive_edges(E_c, sens, N0, dE, E_max, n_split)
+        nodes, raw = quadrature_nodes(edges, "midpoint")
+        W = dos(nodes, A, V0) * raw
+        for Ek, Wk in zip(nodes, W):
+            bands = nearest_bands(E_c, N0, Ek, states)
+            for c in bands:
+                cols.append(int(c))
+                Ecol.append(float(Ek))
+                wcol.append(float(Wk) / bands.size)
+    return dict(cols=np.asarray(cols, dtype=np.int64), E_col=np.asarray(Ecol), w_col=np.asarray(wcol),
+                edges=edges, N0=N0)

@@ -97,3 +97,48 @@ def test_states_share_the_node_weight():
     # no integration part when N0 covers every band or is zero
     assert select_quadrature(prob.E_c, 0, 0.1, 1.0, 0.17, 2.2)["cols"].size == 0
     assert select_quadrature(prob.E_c, prob.n_c, 0.1, 1.0, 0.17, 2.2)["cols"].size == prob.n_c
+
+
+def test_bin_error_brute_force_and_adaptive_splits():
+    """The per-bin first-order estimate against a plain loop, and the greedy
+    refinement: each split halves the bin with the largest estimate (the
+    estimate is a signed sum, so a half can exceed its parent), and with zero
+    sensitivity above some energy nothing there is split."""
+    from oracle.quadrature import adaptive_edges, bin_error
+    rng = np.random.default_rng(5)
+    E_c = np.sort(rng.uniform(0.17, 2.2, 400))
+    N0, dE, Emax = 50, 0.25, 2.2
+    sens = rng.standard_normal(400) * np.exp(-3.0 * (E_c - E_c[N0 - 1]))   # large just above E_0
+    a, b = 0.9, 1.15
+    want = 0.0
+    for c in range(N0, 400):
+        if a <= E_c[c] < b:
+            want += sens[c] * (0.5 * (a + b) - E_c[c])
+    assert abs(bin_error(E_c, sens, N0, a, b, False) - abs(want)) < 1e-13
+    prev = None
+    for n_split in range(0, 12):
+        e = adaptive_edges(E_c, sens, N0, dE, Emax, n_split)
+        assert e.size == math.ceil((Emax - E_c[N0 - 1]) / dE - 1e-12) + 1 + n_split
+        assert np.all(np.diff(e) > 0) and e[0] == E_c[N0 - 1] and e[-1] == Emax
+        if prev is not None:
+            errs = [bin_error(E_c, sens, N0, prev[k], prev[k + 1], k == prev.size - 2) for k in range(prev.size - 1)]
+            k = int(np.argmax(errs))
+            added = np.setdiff1d(e, prev)
+            assert added.size == 1 and added[0] == 0.5 * (prev[k] + prev[k + 1])
+        prev = e
+    # zero sensitivity above 1.5 Ha: every split lands below it
+    s2 = np.where(E_c < 1.5, sens, 0.0)
+    base = adaptive_edges(E_c, s2, N0, dE, Emax, 0)
+    e = adaptive_edges(E_c, s2, N0, dE, Emax, 8)
+    new = np.setdiff1d(e, base)
+    assert new.size == 8 and np.all(new < 1.5)
+
+
+def test_select_adaptive_reduces_to_eq4_without_splits():
+    from oracle.quadrature import select_adaptive
+    prob = make_problem("c2")
+    sens = np.random.default_rng(6).standard_normal(prob.n_c)
+    got = select_adaptive(prob.E_c, sens, prob.N0, prob.dE, prob.dos_A, prob.dos_V0, prob.E_max, 0)
+    ref = select_quadrature(prob.E_c, prob.N0, prob.dE, prob.dos_A, prob.dos_V0, prob.E_max)
+    assert np.array_equal(got["cols"], ref["cols"])
+    assert np.allclose(got["w_col"], ref["w_col"], rtol=1e-15, atol=0)
