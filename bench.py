@@ -213,6 +213,33 @@ def quadrature_study(pkg, prob, plan, chi, psi_v, psi_c, Ev, cv, cc, dev):
         out.append({"grid": grid, "rule": rule, "states": states, "columns": int(c_sel.size),
                     "ms": e0.elapsed_time(e1), "rel_err_static_vs_full": err})
         del chi_q
+    # adjoint-driven grid: dL/dE_c of L = sum_G Re(w_G chi0_GG(omega = 0)) from chi0_backward on a proxy
+    # (8 valence bands x every conduction band), then as many splits as the uniform grid has bins
+    g = torch.Generator(device="cpu").manual_seed(4)
+    nv_p = 8
+    M = plan.pairs(0, psi_v[:nv_p].contiguous(), psi_c)
+    diag = torch.zeros((prob.omega.size, prob.gvec[0].shape[0]), dtype=torch.float64)
+    diag[0] = torch.rand(prob.gvec[0].shape[0], generator=g, dtype=torch.float64)
+    Ec_d = torch.from_numpy(prob.E_c).to(dev)
+    t0 = time.time()
+    _, _, gEc = plan.backward(0, M, nv_p, prob.n_c, Ev[:nv_p].contiguous(), Ec_d, diag_g=diag.to(dev))
+    sens = gEc.cpu().numpy()
+    sens_s = time.time() - t0
+    del M
+    n_uniform = int(np.ceil((prob.E_max - prob.E_c[prob.N0 - 1]) / prob.dE - 1e-12))
+    c_sel, E_sel, w_sel = pkg.select_adaptive(prob.E_c, sens, prob.N0, prob.dE, prob.dos_A, prob.dos_V0,
+                                              prob.E_max, n_uniform, 1)
+    chi_q = plan.new_chi(0)
+    e0.record()
+    plan.build(0, psi_v, Ev, psi_c, torch.from_numpy(E_sel).to(dev), w_col=torch.from_numpy(w_sel).to(dev),
+               c_idx=torch.from_numpy(c_sel).to(dev), chi=chi_q)
+    e1.record()
+    torch.cuda.synchronize()
+    plan.sync_status()
+    out.append({"grid": "adaptive (adjoint)", "rule": "midpoint", "states": 1, "columns": int(c_sel.size),
+                "ms": e0.elapsed_time(e1), "sensitivity_s": sens_s,
+                "rel_err_static_vs_full": float(torch.linalg.vector_norm(chi_q[0] - ref)) / ref_norm})
+    del chi_q
     return out
 
 

@@ -277,6 +277,21 @@ int chi0_select_quadrature(const double* E_c, int n_c, int N0, double dE, double
                            double E_max, int grid, int rule, int states, int32_t* c_sel, double* E_sel,
                            double* w_sel, int cap);
 
+/* Adaptive grid for the Eq. 3 integral driven by the adjoint (host arrays,
+ * host computation).  sens (host) [n_c] holds dL/dE_c for some loss L (e.g.
+ * grad_Ecol of chi0_backward on a cheap proxy of the workload).  Starting
+ * from the uniform grid of step dE on [E_0, E_max] (as chi0_select_accelerated),
+ * the bin [a, b) with the largest first-order estimate of the error of Eq. 4's
+ * energy substitution,  |sum_{N0 <= c, a <= E_c < b} sens[c] ((a+b)/2 - E_c)|
+ * (the last bin closed at E_max), is halved, n_split times (ties: the lowest
+ * bin).  Each bin then contributes the midpoint node with weight g(E_k) (b - a)
+ * shared by its `states` nearest bands above N0, as chi0_select_quadrature.
+ * n_split = 0 gives chi0_select_accelerated.  Returns the number of columns,
+ * or -1 for bad arguments, unsorted E_c or more than cap columns. */
+int chi0_select_adaptive(const double* E_c, int n_c, int N0, const double* sens, double dE, double dos_A,
+                         double dos_V0, double E_max, int n_split, int states, int32_t* c_sel, double* E_sel,
+                         double* w_sel, int cap);
+
 /* ---- Dielectric matrix (section II: eps = 1 - v chi0, W = eps^-1 v; Table III:
  * eps_inf = 1 / [eps^-1]_{00}(q -> 0, omega = 0)).  Hartree atomic units. ---- */
 

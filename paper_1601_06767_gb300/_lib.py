@@ -49,6 +49,7 @@ SIGNATURES = [
     ("chi0_build", _I, [_VP, _I, _VP, _I, _VP, _VP, _VP, _I, _VP, _VP, _VP, _VP]),
     ("chi0_select_accelerated", _I, [_VP, _I, _I, _D, _D, _D, _D, _VP, _VP, _VP, _I]),
     ("chi0_select_quadrature", _I, [_VP, _I, _I, _D, _D, _D, _D, _I, _I, _I, _VP, _VP, _VP, _I]),
+    ("chi0_select_adaptive", _I, [_VP, _I, _I, _VP, _D, _D, _D, _D, _I, _I, _VP, _VP, _VP, _I]),
     ("chi0_build_batched", _I, [_VP, _VP, _I, _VP, _VP, _VP, _I, _VP, _VP, _VP, _I, _VP]),
     ("chi0_backward", _I, [_VP, _I, _VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("chi0_selftest_wait", _I, [_VP, _D, _VP]),

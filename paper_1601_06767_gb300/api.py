@@ -276,6 +276,28 @@ def select_quadrature(E_c, N0: int, dE: float, dos_A: float, dos_V0: float, E_ma
     return c_sel[:n].copy(), E_sel[:n].copy(), w_sel[:n].copy()
 
 
+def select_adaptive(E_c, sens, N0: int, dE: float, dos_A: float, dos_V0: float, E_max: float,
+                    n_split: int, states: int = 1):
+    """Columns of Eq. 3 on a grid refined where the adjoint's first-order
+    estimate of the energy-substitution error is largest (chi0_select_adaptive);
+    sens = dL/dE_c, e.g. grad_E_col from Chi0Plan.backward."""
+    E_c = _f64(E_c)
+    sens = _f64(sens)
+    if sens.shape != E_c.shape:
+        raise ValueError("one sensitivity per conduction band")
+    n_bins = int(np.ceil(max(E_max - E_c[min(max(N0, 1), E_c.size) - 1], 0) / dE)) + 1 if E_c.size else 0
+    cap = int(N0) + (n_bins + int(n_split)) * max(int(states), 1) + 2
+    c_sel = np.empty(cap, np.int32)
+    E_sel = np.empty(cap, np.float64)
+    w_sel = np.empty(cap, np.float64)
+    n = L.lib().chi0_select_adaptive(E_c.ctypes.data, E_c.size, int(N0), sens.ctypes.data, float(dE),
+                                     float(dos_A), float(dos_V0), float(E_max), int(n_split), int(states),
+                                     c_sel.ctypes.data, E_sel.ctypes.data, w_sel.ctypes.data, cap)
+    if n < 0:
+        raise L.Chi0Error(L.CHI0_ERR_INVALID, "chi0_select_adaptive rejected its input")
+    return c_sel[:n].copy(), E_sel[:n].copy(), w_sel[:n].copy()
+
+
 def select_accelerated(E_c, N0: int, dE: float, dos_A: float, dos_V0: float, E_max: float):
     """Columns of Eq. 3/4 from chi0_select_accelerated: (band index, energy, weight)."""
     E_c = _f64(E_c)

@@ -876,4 +876,68 @@ int chi0_select_quadrature(const double* E_c, int n_c, int N0, double dE, double
   return n;
 }
 
+// |sum_c s_c (m - E_c)| over the bands c >= N0 with a <= E_c < b (<= b for the last bin)
+static double bin_error_c(const double* E_c, const double* sens, int N0, int n_c, double a, double b, bool last) {
+  int lo = N0, hi = n_c;                     // first band with E_c >= a
+  while (lo < hi) { int m = (lo + hi) / 2; if (E_c[m] < a) lo = m + 1; else hi = m; }
+  const double mid = 0.5 * (a + b);
+  double acc = 0.0;
+  for (int c = lo; c < n_c && (last ? E_c[c] <= b : E_c[c] < b); ++c) acc += sens[c] * (mid - E_c[c]);
+  return fabs(acc);
+}
+
+int chi0_select_adaptive(const double* E_c, int n_c, int N0, const double* sens, double dE, double dos_A,
+                         double dos_V0, double E_max, int n_split, int states, int32_t* c_sel, double* E_sel,
+                         double* w_sel, int cap) {
+  if (!E_c || !sens || n_c < 0 || N0 < 0 || !(dE > 0.0) || n_split < 0 || states < 1 || !c_sel || !E_sel ||
+      !w_sel || cap < 0)
+    return -1;
+  for (int i = 1; i < n_c; ++i)
+    if (E_c[i] < E_c[i - 1]) return -1;
+  N0 = std::min(N0, n_c);
+  int n = 0;
+  for (int c = 0; c < N0; ++c) {            // explicit part of Eq. 3
+    if (n >= cap) return -1;
+    c_sel[n] = c; E_sel[n] = E_c[c]; w_sel[n] = 1.0; ++n;
+  }
+  if (N0 == 0 || N0 >= n_c) return n;
+  const double E0 = E_c[N0 - 1];
+  const int NE = (int)ceil((E_max - E0) / dE - 1e-12);
+  if (NE <= 0) return n;
+  std::vector<double> edge(NE + 1);
+  for (int k = 0; k <= NE; ++k) edge[k] = std::min(E0 + dE * k, E_max);
+  std::vector<double> err(NE);
+  for (int k = 0; k < NE; ++k) err[k] = bin_error_c(E_c, sens, N0, n_c, edge[k], edge[k + 1], k == NE - 1);
+  for (int t = 0; t < n_split; ++t) {       // split the bin with the largest estimate (lowest on ties)
+    int kb = 0;
+    for (int k = 1; k < (int)err.size(); ++k)
+      if (err[k] > err[kb]) kb = k;
+    const bool last = kb == (int)err.size() - 1;
+    const double mid = 0.5 * (edge[kb] + edge[kb + 1]);
+    edge.insert(edge.begin() + kb + 1, mid);
+    err[kb] = bin_error_c(E_c, sens, N0, n_c, edge[kb], edge[kb + 1], false);
+    err.insert(err.begin() + kb + 1, bin_error_c(E_c, sens, N0, n_c, edge[kb + 1], edge[kb + 2], last));
+  }
+  const int avail = n_c - N0, take = std::min(states, avail);
+  std::vector<char> used((size_t)avail);
+  for (size_t k = 0; k + 1 < edge.size(); ++k) {
+    const double Ek = 0.5 * (edge[k] + edge[k + 1]), h = edge[k + 1] - edge[k];
+    const double W = ((Ek > dos_V0) ? dos_A * sqrt(2.0 * (Ek - dos_V0)) : 0.0) * h;
+    std::fill(used.begin(), used.end(), 0);
+    for (int t = 0; t < take; ++t) {        // next nearest band above N0 (ties: lower index)
+      int best = -1;
+      double bd = 0.0;
+      for (int c = N0; c < n_c; ++c) {
+        if (used[c - N0]) continue;
+        const double d = fabs(E_c[c] - Ek);
+        if (best < 0 || d < bd) { best = c; bd = d; }
+      }
+      used[best - N0] = 1;
+      if (n >= cap) return -1;
+      c_sel[n] = best; E_sel[n] = Ek; w_sel[n] = W / take; ++n;
+    }
+  }
+  return n;
+}
+
 }  // extern "C"

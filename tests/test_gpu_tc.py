@@ -231,3 +231,32 @@ def test_build_quadrature_selection(precision, tol, grid, rule, states):
         chi = chi.cpu().numpy()
     for iw in range(prob.omega.size):
         assert rel_fro(chi[iw], ref[iw]) < tol
+
+
+@pytest.mark.parametrize("precision,tol", [("bf16", TOL), ("fp64", 1e-12)])
+def test_build_adaptive_selection(precision, tol):
+    """Eq. 3 on the adaptive grid (bins split where a sensitivity-weighted
+    estimate of the energy-substitution error is largest); seeded
+    sensitivities feed both sides."""
+    from oracle.quadrature import select_adaptive as oracle_adaptive
+    from paper_1601_06767_gb300 import Chi0Plan, select_adaptive
+    prob = make_problem("c1", N0=40, dE_eV=3.0, n_imag=1)
+    sens = np.random.default_rng(3).standard_normal(prob.n_c)
+    ref_sel = oracle_adaptive(prob.E_c, sens, prob.N0, prob.dE, prob.dos_A, prob.dos_V0, prob.E_max, 6, 2)
+    c_sel, E_sel, w_sel = select_adaptive(prob.E_c, sens, prob.N0, prob.dE, prob.dos_A, prob.dos_V0,
+                                          prob.E_max, 6, 2)
+    assert np.array_equal(c_sel, ref_sel["cols"])
+    cv, cc = prob.coeff_v(0), prob.coeff_c()
+    uv, uc = wfn_to_grid(cv, prob.gw, prob.n), wfn_to_grid(cc, prob.gw, prob.n)
+    M = pair_elements(uv, uc[ref_sel["cols"]], prob.gvec[0], prob.n)
+    dE = (prob.E_v[:, None] - ref_sel["E_col"][None, :]).reshape(-1)
+    w = np.broadcast_to(ref_sel["w_col"][None, :], (prob.n_v, ref_sel["cols"].size)).reshape(-1)
+    ref = chi0_from_pairs(M, freq_factor(dE, w, prob.omega, prob.delta))
+    with Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision=precision, gw=prob.gw,
+                  max_pairs=512) as plan:
+        chi = plan.build(0, plan.wfn_to_grid(_dev(cv)), _dev(prob.E_v), plan.wfn_to_grid(_dev(cc)), _dev(E_sel),
+                         w_col=_dev(w_sel), c_idx=_dev(c_sel.astype(np.int32)))
+        plan.sync_status()
+        chi = chi.cpu().numpy()
+    for iw in range(prob.omega.size):
+        assert rel_fro(chi[iw], ref[iw]) < tol

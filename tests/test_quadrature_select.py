@@ -40,3 +40,20 @@ def test_quadrature_selection_ties_and_arguments():
         P.select_quadrature(E_c[::-1], 25, 0.037, 80.0, 0.17, 2.2)
     with pytest.raises(KeyError):
         P.select_quadrature(E_c, 25, 0.037, 80.0, 0.17, 2.2, rule="trapezoid")
+
+
+@pytest.mark.parametrize("n_split,states", [(0, 1), (5, 1), (40, 2)])
+def test_adaptive_selection_matches_oracle(n_split, states):
+    import paper_1601_06767_gb300 as P
+    from oracle.quadrature import select_adaptive as oracle_adaptive
+    pr = make_problem("c2")
+    rng = np.random.default_rng(n_split)
+    sens = rng.standard_normal(pr.n_c) * np.exp(-2.0 * (pr.E_c - pr.E_c[pr.N0 - 1]).clip(0))
+    c, E, w = P.select_adaptive(pr.E_c, sens, pr.N0, pr.dE, pr.dos_A, pr.dos_V0, pr.E_max, n_split, states)
+    ref = oracle_adaptive(pr.E_c, sens, pr.N0, pr.dE, pr.dos_A, pr.dos_V0, pr.E_max, n_split, states)
+    assert np.array_equal(c, ref["cols"])
+    assert np.allclose(E, ref["E_col"], rtol=1e-15, atol=0)
+    assert np.allclose(w, ref["w_col"], rtol=1e-14, atol=0)
+    if n_split == 0:
+        a = P.select_accelerated(pr.E_c, pr.N0, pr.dE, pr.dos_A, pr.dos_V0, pr.E_max)
+        assert all(np.array_equal(x, y) for x, y in zip((c, E, w), a))
