@@ -328,6 +328,38 @@ chi0_status chi0_epsilon_inverse(chi0_plan plan, int iq, void* eps, void* stream
  * if the sphere does not contain G = 0. */
 chi0_status chi0_eps_inf(chi0_plan plan, int iq, const void* eps_inv, double* out, void* stream);
 
+/* ---- Coulomb-hole self-energy of Eq. 2 with the Hybertsen-Louie plasmon-pole
+ * model (the paper's extension of the static eps^-1 to finite frequencies). ---- */
+
+/* Plasmon-pole parameters of sphere iq:
+ *   Omega2[G][G'] = w_p^2 [(q+G).(q+G') / |q+G|^2] rho(G - G') / rho(0),  w_p^2 = 4 pi n_el / Omega,
+ *   wt[G][G']     = sqrt(Omega2 / (delta_GG' - eps_inv[G][G']))  (principal branch; 0 where the
+ *                   denominator vanishes),
+ * with rho(d) the Fourier coefficient exp(-i d.r) of the density 2 sum_v |psi_v(r)|^2 at the
+ * distinct differences d = G - G' (a direct transform over the grid; axes up to 128 points).
+ * psi_v: (device) [n_v][N_r] valence grids (plan complex type); eps_inv: (device) [N_G][N_G]
+ * complex128, the inverse of the plain static eps (chi0_epsilon with symmetric = 0);
+ * lattice, q_frac (host) as for chi0_coulomb; n_el electrons per cell; Omega2, wt: (device)
+ * [N_G][N_G] complex128 outputs.  Allocates temporaries and synchronises `stream`. */
+chi0_status chi0_gpp(chi0_plan plan, int iq, const void* psi_v, int n_v, const void* eps_inv,
+                     const double* lattice, const double* q_frac, double n_el, void* Omega2, void* wt,
+                     void* stream);
+
+/* Diagonal COH self-energy of target bands t with the plasmon-pole model (Eq. 2 with its
+ * frequency integral done in closed form):
+ *   sigma[t] = sum_b w[b] sum_{G,G'} m[t][b][G] K_GG'(x[t][b]) conj(m[t][b][G']),
+ *   K_GG'(x) = Omega2[G][G'] v[G'] / (2 wt[G][G'] (x - wt[G][G'] + i delta)),  0 where wt or Omega2 is 0,
+ * m: (device) [n_t * n_b][N_G] complex, the pair elements <t| e^{iG.r} |b> of chi0_pairs with the
+ * targets as the first band set and the bands b (explicit, or the columns of an Eq. 3 selection)
+ * as the second; x: (device) [n_t][n_b] FP64, E_t - E_b (E_b the grid energy for an energy-grid
+ * state); w: (device) [n_b] FP64 or NULL (= 1); Omega2, wt from chi0_gpp; v: (device) [N_G] FP64;
+ * sigma: (host) [n_t] complex128.  Split plans compute the terms in FP32 and sum them in FP64,
+ * FP64 plans in FP64; the tile sums are added on the host in a fixed order.  Allocates a
+ * workspace (two N_G x N_G tables) and synchronises `stream`. */
+chi0_status chi0_sigma_coh(chi0_plan plan, int iq, const void* m, int n_t, int n_b, const double* x,
+                           const double* w, const void* Omega2, const void* wt, const double* v,
+                           double* sigma, void* stream);
+
 /* Band selection of Eq. 3 / Eq. 4 (host arrays, host computation).
  * E_c (host) [n_c] sorted ascending.  Columns 0..N0-1 are bands 0..N0-1 with
  * their own energy and weight 1.  E_0 = E_c[N0-1]; the interval (E_0, E_max]

@@ -57,6 +57,8 @@ SIGNATURES = [
     ("chi0_epsilon", _I, [_VP, _I, _VP, _VP, _I, _VP, _VP]),
     ("chi0_epsilon_inverse", _I, [_VP, _I, _VP, _VP]),
     ("chi0_eps_inf", _I, [_VP, _I, _VP, _VP, _VP]),
+    ("chi0_gpp", _I, [_VP, _I, _VP, _I, _VP, _VP, _VP, _D, _VP, _VP, _VP]),
+    ("chi0_sigma_coh", _I, [_VP, _I, _VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("chi0_autotune", _I, [_VP, _I, _I, _VP, _VP]),
     ("chi0_get_tuning", _I, [_VP, _VP, _VP, _VP]),
     ("chi0_profile_enable", _I, [_VP, _I]),

@@ -246,6 +246,33 @@ class Chi0Plan:
         self._check(L.lib().chi0_epsilon_inverse(self._h, iq, _ptr(eps), _stream()))
         return eps
 
+    # -- COH self-energy with the plasmon-pole model ---------------------------
+    def gpp(self, iq: int, psi_v, eps_inv0, lattice, q_frac, n_el: float):
+        """chi0_gpp: (Omega2, wt) [N_G][N_G] complex128 of sphere iq."""
+        self._c(psi_v, "psi_v")
+        self._c(eps_inv0, "eps_inv0", torch.complex128)
+        nG = self.n_G[iq]
+        A = _f64(lattice).reshape(3, 3)
+        q = _f64(q_frac).reshape(3)
+        Om2 = torch.empty((nG, nG), dtype=torch.complex128, device=self.device)
+        wt = torch.empty_like(Om2)
+        self._check(L.lib().chi0_gpp(self._h, iq, _ptr(psi_v), int(psi_v.shape[0]), _ptr(eps_inv0), A.ctypes.data,
+                                     q.ctypes.data, float(n_el), _ptr(Om2), _ptr(wt), _stream()))
+        return Om2, wt
+
+    def sigma_coh(self, iq: int, m, n_t: int, n_b: int, x, Om2, wt, v, w=None) -> np.ndarray:
+        """chi0_sigma_coh: diagonal COH self-energy of n_t target bands (host, complex)."""
+        self._c(m, "m")
+        for t, nm in ((x, "x"), (v, "v"), (w, "w")):
+            if t is not None:
+                self._c(t, nm, torch.float64)
+        self._c(Om2, "Omega2", torch.complex128)
+        self._c(wt, "wt", torch.complex128)
+        out = np.empty(2 * n_t, np.float64)
+        self._check(L.lib().chi0_sigma_coh(self._h, iq, _ptr(m), int(n_t), int(n_b), _ptr(x), _ptr(w), _ptr(Om2),
+                                           _ptr(wt), _ptr(v), out.ctypes.data, _stream()))
+        return out[0::2] + 1j * out[1::2]
+
     def eps_inf(self, iq: int, eps_inv) -> np.ndarray:
         """chi0_eps_inf: 1 / [eps^-1]_00 per frequency (complex, host)."""
         self._c(eps_inv, "eps_inv", torch.complex128)

@@ -156,6 +156,16 @@ bool tc_supported(std::string* why);
 cudaError_t launch_epsilon(chi0_plan_s* p, int nG, const double2* chi, const double* v, int symmetric,
                            double2* eps, cudaStream_t s);
 size_t eps_inverse_ws_bytes(const chi0_plan_s* p, int nG);
+// COH self-energy with the plasmon-pole model
+cudaError_t launch_density(const chi0_plan_s* p, const void* psi_v, int n_v, double* dens, cudaStream_t s);
+cudaError_t launch_density_ft(const chi0_plan_s* p, const double* dens, const int* dvec, int nd, double2* rho,
+                              cudaStream_t s);
+cudaError_t launch_gpp(int nG, const double2* eps_inv, const double2* rho, const int* idx, const double* kvec,
+                       double wp2, double2* Om2, double2* wt, cudaStream_t s);
+size_t sigma_coh_ws_bytes(const chi0_plan_s* p, int nG, int n_t);
+cudaError_t launch_sigma_coh(const chi0_plan_s* p, int nG, const void* m, int n_t, int n_b, const double* x,
+                             const double* w, const double2* Om2, const double2* wt, const double* v, double delta,
+                             void* ws, double2* partial, int* n_tiles, cudaStream_t s);
 cudaError_t launch_epsilon_inverse(chi0_plan_s* p, int nG, double2* eps, void* ws, cudaStream_t s);
 
 }  // namespace chi0

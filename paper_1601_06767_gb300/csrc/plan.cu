@@ -485,6 +485,140 @@ chi0_status chi0_epsilon_inverse(chi0_plan p, int iq, void* eps, void* stream) {
   return CHI0_OK;
 }
 
+// reciprocal lattice rows b_i = 2 pi (A^-T) rows and |det A|; false for a singular lattice
+static bool recip_lattice(const double* a, double b[3][3], double* omega_cell) {
+  double cof[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+      cof[i][j] = a[3 * i1 + j1] * a[3 * i2 + j2] - a[3 * i1 + j2] * a[3 * i2 + j1];
+    }
+  const double det = a[0] * cof[0][0] + a[1] * cof[0][1] + a[2] * cof[0][2];
+  if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return false;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) b[i][j] = 2.0 * M_PI * cof[i][j] / det;
+  *omega_cell = std::fabs(det);
+  return true;
+}
+
+chi0_status chi0_gpp(chi0_plan p, int iq, const void* psi_v, int n_v, const void* eps_inv, const double* lattice,
+                     const double* q_frac, double n_el, void* Omega2, void* wt, void* stream) {
+  chi0_status st = check_plan(p);
+  if (st != CHI0_OK) return st;
+  if (iq < 0 || iq >= (int)p->q.size()) return fail(p, CHI0_ERR_INVALID, "iq out of range");
+  if (!psi_v || n_v < 1 || !eps_inv || !lattice || !q_frac || !Omega2 || !wt || !(n_el > 0.0))
+    return fail(p, CHI0_ERR_INVALID, "bad argument");
+  if (p->n1 > 128 || p->n2 > 128 || p->n3 > 128) return fail(p, CHI0_ERR_UNSUPPORTED, "grid axes above 128");
+  double b[3][3], omega_cell = 0.0;
+  if (!recip_lattice(lattice, b, &omega_cell)) return fail(p, CHI0_ERR_INVALID, "singular lattice");
+  const chi0::SphereQ& sq = p->q[iq];
+  const int nG = sq.nG;
+  // distinct differences G_i - G_j through a box index, and the (i, j) -> difference table
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int j = 0; j < nG; ++j)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], sq.g_host[3 * j + a]);
+      hi[a] = std::max(hi[a], sq.g_host[3 * j + a]);
+    }
+  const int ext[3] = {2 * (hi[0] - lo[0]) + 1, 2 * (hi[1] - lo[1]) + 1, 2 * (hi[2] - lo[2]) + 1};
+  std::vector<int> box((size_t)ext[0] * ext[1] * ext[2], -1);
+  std::vector<int> dvec, idx((size_t)nG * nG);
+  for (int i = 0; i < nG; ++i)
+    for (int j = 0; j < nG; ++j) {
+      int d[3], o[3];
+      for (int a = 0; a < 3; ++a) {
+        d[a] = sq.g_host[3 * i + a] - sq.g_host[3 * j + a];
+        o[a] = d[a] + (hi[a] - lo[a]);
+      }
+      int& slot = box[((size_t)o[0] * ext[1] + o[1]) * ext[2] + o[2]];
+      if (slot < 0) {
+        slot = (int)(dvec.size() / 3);
+        dvec.insert(dvec.end(), d, d + 3);
+      }
+      idx[(size_t)i * nG + j] = slot;
+    }
+  const int nd = (int)(dvec.size() / 3);
+  std::vector<double> kvec((size_t)3 * nG);
+  for (int j = 0; j < nG; ++j)
+    for (int x = 0; x < 3; ++x) {
+      double k = 0.0;
+      for (int a = 0; a < 3; ++a) k += ((double)sq.g_host[3 * j + a] + q_frac[a]) * b[a][x];
+      kvec[3 * j + x] = k;
+    }
+  for (int j = 0; j < nG; ++j)
+    if (!(kvec[3 * j] * kvec[3 * j] + kvec[3 * j + 1] * kvec[3 * j + 1] + kvec[3 * j + 2] * kvec[3 * j + 2] > 0.0))
+      return fail(p, CHI0_ERR_INVALID, "q + G = 0 at sphere point " + std::to_string(j));
+  const double wp2 = 4.0 * M_PI * n_el / omega_cell;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* dens = nullptr;
+  int *d_dvec = nullptr, *d_idx = nullptr;
+  double2* rho = nullptr;
+  double* d_k = nullptr;
+  auto cleanup = [&]() { cudaFree(dens); cudaFree(d_dvec); cudaFree(d_idx); cudaFree(rho); cudaFree(d_k); };
+  cudaError_t e;
+  if ((e = cudaMalloc((void**)&dens, sizeof(double) * p->nr)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&d_dvec, sizeof(int) * dvec.size())) != cudaSuccess ||
+      (e = cudaMalloc((void**)&d_idx, sizeof(int) * idx.size())) != cudaSuccess ||
+      (e = cudaMalloc((void**)&rho, sizeof(double2) * nd)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&d_k, sizeof(double) * kvec.size())) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_dvec, dvec.data(), sizeof(int) * dvec.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_k, kvec.data(), sizeof(double) * kvec.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = chi0::launch_density(p, psi_v, n_v, dens, s)) != cudaSuccess ||
+      (e = chi0::launch_density_ft(p, dens, d_dvec, nd, rho, s)) != cudaSuccess ||
+      (e = chi0::launch_gpp(nG, (const double2*)eps_inv, rho, d_idx, d_k, wp2, (double2*)Omega2, (double2*)wt, s)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    cleanup();
+    cudaGetLastError();
+    return fail(p, e == cudaErrorMemoryAllocation ? CHI0_ERR_OOM : CHI0_ERR_CUDA,
+                std::string("chi0_gpp: ") + cudaGetErrorString(e));
+  }
+  cleanup();
+  return CHI0_OK;
+}
+
+chi0_status chi0_sigma_coh(chi0_plan p, int iq, const void* m, int n_t, int n_b, const double* x, const double* w,
+                           const void* Omega2, const void* wt, const double* v, double* sigma, void* stream) {
+  chi0_status st = check_plan(p);
+  if (st != CHI0_OK) return st;
+  if (iq < 0 || iq >= (int)p->q.size()) return fail(p, CHI0_ERR_INVALID, "iq out of range");
+  if (n_t < 0 || n_b < 0 || !sigma || ((n_t > 0 && n_b > 0) && (!m || !x || !Omega2 || !wt || !v)))
+    return fail(p, CHI0_ERR_INVALID, "bad argument");
+  if (n_t > 65535) return fail(p, CHI0_ERR_INVALID, "at most 65535 target bands per call");
+  for (int t = 0; t < 2 * n_t; ++t) sigma[t] = 0.0;
+  if (n_t == 0 || n_b == 0) return CHI0_OK;
+  const int nG = p->q[iq].nG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = chi0::sigma_coh_ws_bytes(p, nG, n_t);
+  void* ws = nullptr;
+  cudaError_t e = cudaMalloc(&ws, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(p, CHI0_ERR_OOM, "chi0_sigma_coh: workspace");
+  }
+  const size_t cb = chi0::is_split(p) ? sizeof(float2) : sizeof(double2);
+  double2* partial = reinterpret_cast<double2*>(reinterpret_cast<unsigned char*>(ws) + 2 * (size_t)nG * nG * cb);
+  int tiles = 0;
+  e = chi0::launch_sigma_coh(p, nG, m, n_t, n_b, x, w, (const double2*)Omega2, (const double2*)wt, v, p->delta, ws,
+                             partial, &tiles, s);
+  std::vector<double2> h((size_t)n_t * tiles);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h.data(), partial, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(ws);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(p, CHI0_ERR_CUDA, std::string("chi0_sigma_coh: ") + cudaGetErrorString(e));
+  }
+  for (int t = 0; t < n_t; ++t)
+    for (int k = 0; k < tiles; ++k) {   // fixed order: deterministic
+      sigma[2 * t] += h[(size_t)t * tiles + k].x;
+      sigma[2 * t + 1] += h[(size_t)t * tiles + k].y;
+    }
+  return CHI0_OK;
+}
+
 chi0_status chi0_eps_inf(chi0_plan p, int iq, const void* eps_inv, double* out, void* stream) {
   chi0_status st = check_plan(p);
   if (st != CHI0_OK) return st;
