@@ -93,6 +93,18 @@ def sigma_coh(m: np.ndarray, x: np.ndarray, w: np.ndarray, Omega2: np.ndarray, w
     return total
 
 
+def sigma_coh_abs(m: np.ndarray, x: np.ndarray, w: np.ndarray, Omega2: np.ndarray, wt: np.ndarray,
+                  v: np.ndarray, delta: float) -> float:
+    """sum_{n''} |w_{n''}| |m_{n''}|^T |K(x_{n''})| |m_{n''}|: the sum of the magnitudes of
+    the terms of sigma_coh, the scale against which its rounding errors are measured
+    (the terms cancel strongly, so |Sigma| itself can be much smaller)."""
+    total = 0.0
+    for a in range(m.shape[0]):
+        K = np.abs(coh_kernel(Omega2, wt, v, float(x[a]), delta))
+        total += abs(w[a]) * (np.abs(m[a]) @ K @ np.abs(m[a]))
+    return float(total)
+
+
 def difference_table(gvec: np.ndarray):
     """The distinct integer vectors G_i - G_j of a sphere and, for each (i, j),
     the index of G_i - G_j in that list (sorted lexicographically)."""
@@ -130,8 +142,9 @@ def sigma_coh_problem(prob, targets, eps_inv0: np.ndarray, A: np.ndarray, n_el: 
     E_b = np.concatenate([prob.E_v, np.asarray(E_cols)])
     w_b = np.concatenate([np.ones(prob.n_v), np.asarray(w_cols)])
     u_t = wfn_to_grid(prob.coeff_c(np.asarray(targets)), prob.gw, prob.n)
-    out = []
+    out, mag = [], []
     for it, t in enumerate(targets):
         m = pair_elements(u_t[it:it + 1], u_b, gvec, prob.n)
         out.append(sigma_coh(m, prob.E_c[t] - E_b, w_b, Omega2, wt, v, prob.delta))
-    return np.asarray(out), dict(Omega2=Omega2, wt=wt, v=v, rho_ratio=rho_ratio)
+        mag.append(sigma_coh_abs(m, prob.E_c[t] - E_b, w_b, Omega2, wt, v, prob.delta))
+    return np.asarray(out), dict(Omega2=Omega2, wt=wt, v=v, rho_ratio=rho_ratio, abs_sum=np.asarray(mag))

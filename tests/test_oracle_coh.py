@@ -87,6 +87,15 @@ def test_sigma_coh_brute_force():
                 want += w[a] * m[a, i] * np.conj(m[a, j]) * Omega2[i, j] * v[j] / (
                     2 * wt[i, j] * (x[a] - wt[i, j] + 1j * delta))
     assert abs(sigma_coh(m, x, w, Omega2, wt, v, delta) - want) < 1e-13 * abs(want)
+    from oracle.coh import sigma_coh_abs
+    mag = 0.0
+    for a in range(4):
+        for i in range(5):
+            for j in range(5):
+                mag += abs(w[a] * m[a, i] * np.conj(m[a, j]) * Omega2[i, j] * v[j] / (
+                    2 * wt[i, j] * (x[a] - wt[i, j] + 1j * delta)))
+    assert abs(sigma_coh_abs(m, x, w, Omega2, wt, v, delta) - mag) < 1e-13 * mag
+    assert mag >= abs(want)
 
 
 def test_difference_table_and_problem_pipeline():
