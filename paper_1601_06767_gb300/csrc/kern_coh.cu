@@ -164,7 +164,7 @@ k_sigma_coh(const typename Cx<R>::T* __restrict__ m, int n_b, int nG, const doub
   const int i0 = blockIdx.y * CT, j0 = blockIdx.x * CT;
   __shared__ C cs[CT][CT + 1], ws[CT][CT + 1];
   __shared__ C mi[CB][CT + 1], mj[CB][CT + 1];
-  __shared__ R xs[CB], wsb[CB];
+  __shared__ R xs[CB];
   __shared__ double2 red[8];
   for (int e = threadIdx.x; e < CT * CT; e += blockDim.x) {
     const int a = e / CT, b = e - a * CT;
@@ -181,13 +181,17 @@ k_sigma_coh(const typename Cx<R>::T* __restrict__ m, int n_b, int nG, const doub
       const int bb = e / CT, g = e - bb * CT;
       const int b = b0 + bb;
       const bool okb = b < n_b;
-      mi[bb][g] = (okb && i0 + g < nG) ? mt[(size_t)b * nG + i0 + g] : cz(C{});
+      // the band weight rides on the G side: w_b m(G)
+      const R wgt = okb ? (R)(wb ? wb[b] : 1.0) : (R)0;
+      C u = (okb && i0 + g < nG) ? mt[(size_t)b * nG + i0 + g] : cz(C{});
+      u.x *= wgt;
+      u.y *= wgt;
+      mi[bb][g] = u;
       mj[bb][g] = (okb && j0 + g < nG) ? mt[(size_t)b * nG + j0 + g] : cz(C{});
     }
     if (threadIdx.x < CB) {
       const int b = b0 + threadIdx.x;
       xs[threadIdx.x] = b < n_b ? (R)x[(size_t)t * n_b + b] : (R)0;
-      wsb[threadIdx.x] = b < n_b ? (R)(wb ? wb[b] : 1.0) : (R)0;
     }
     __syncthreads();
     C part = cz(C{});
@@ -196,19 +200,23 @@ k_sigma_coh(const typename Cx<R>::T* __restrict__ m, int n_b, int nG, const doub
       const int a = e / CT, bcol = e - a * CT;
       const C cc = cs[a][bcol], w = ws[a][bcol];
       if (cc.x == (R)0 && cc.y == (R)0) continue;
+      const R dy = (R)delta - w.y;
+#pragma unroll 4
       for (int bb = 0; bb < CB; ++bb) {
-        // 1 / (x - wt + i delta) = conj(d) / |d|^2
-        const R dx = xs[bb] - w.x, dy = (R)delta - w.y;
-        const R inv = (R)1 / (dx * dx + dy * dy);
-        C r;
-        r.x = dx * inv;
-        r.y = -dy * inv;
-        const C mm = cconjmul(mj[bb][bcol], mi[bb][a]);   // m(G) conj(m(G'))
-        C term = cmul(cmul(mm, cc), r);
-        term.x *= wsb[bb];
-        term.y *= wsb[bb];
-        part.x += term.x;
-        part.y += term.y;
+        // c / (x - wt + i delta) = c conj(d) / |d|^2,  d = dx + i dy
+        const R dx = xs[bb] - w.x;
+        R inv;
+        if constexpr (sizeof(R) == 4)
+          inv = __fdividef(1.0f, dx * dx + dy * dy);     // 2-ulp reciprocal: terms carry FP32 errors anyway
+        else
+          inv = (R)1 / (dx * dx + dy * dy);
+        C cr;                                             // c conj(d)
+        cr.x = fma(cc.x, dx, cc.y * dy);
+        cr.y = fma(cc.y, dx, -(cc.x * dy));
+        const C mm = cconjmul(mj[bb][bcol], mi[bb][a]);   // w_b m(G) conj(m(G'))
+        const C t2 = cmul(mm, cr);
+        part.x = fma(t2.x, inv, part.x);
+        part.y = fma(t2.y, inv, part.y);
       }
     }
     acc.x += (double)part.x;
