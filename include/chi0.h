@@ -336,7 +336,7 @@ chi0_status chi0_eps_inf(chi0_plan plan, int iq, const void* eps_inv, double* ou
  *   wt[G][G']     = sqrt(Omega2 / (delta_GG' - eps_inv[G][G']))  (principal branch; 0 where the
  *                   denominator vanishes),
  * with rho(d) the Fourier coefficient exp(-i d.r) of the density 2 sum_v |psi_v(r)|^2 at the
- * distinct differences d = G - G' (a direct transform over the grid; axes up to 128 points).
+ * distinct differences d = G - G' (a transform pruned to the offsets they span).
  * psi_v: (device) [n_v][N_r] valence grids (plan complex type); eps_inv: (device) [N_G][N_G]
  * complex128, the inverse of the plain static eps (chi0_epsilon with symmetric = 0);
  * lattice, q_frac (host) as for chi0_coulomb; n_el electrons per cell; Omega2, wt: (device)

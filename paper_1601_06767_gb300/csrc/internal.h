@@ -158,8 +158,9 @@ cudaError_t launch_epsilon(chi0_plan_s* p, int nG, const double2* chi, const dou
 size_t eps_inverse_ws_bytes(const chi0_plan_s* p, int nG);
 // COH self-energy with the plasmon-pole model
 cudaError_t launch_density(const chi0_plan_s* p, const void* psi_v, int n_v, double* dens, cudaStream_t s);
-cudaError_t launch_density_ft(const chi0_plan_s* p, const double* dens, const int* dvec, int nd, double2* rho,
-                              cudaStream_t s);
+size_t density_ft_ws_bytes(const chi0_plan_s* p, int s2, int s3);
+cudaError_t launch_density_ft(const chi0_plan_s* p, const double* dens, const int* dvec, int nd, int s2, int s3,
+                              void* ws, double2* rho, cudaStream_t s);
 cudaError_t launch_gpp(int nG, const double2* eps_inv, const double2* rho, const int* idx, const double* kvec,
                        double wp2, double2* Om2, double2* wt, cudaStream_t s);
 size_t sigma_coh_ws_bytes(const chi0_plan_s* p, int nG, int n_t);

@@ -9,7 +9,8 @@
 //
 // with m_tb(G) = <t| e^{iG.r} |b> (pair elements, target band first) and
 // x_tb = E_t - E_b.  rho(d) is the Fourier coefficient of the density
-// 2 sum_v |u_v(r)|^2 at the distinct differences d = G - G' of the sphere.
+// 2 sum_v |u_v(r)|^2 at the distinct differences d = G - G' of the sphere,
+// computed by a transform pruned to the offsets those differences span.
 #include <cuda_runtime.h>
 
 #include "cplx.cuh"
@@ -34,55 +35,59 @@ __global__ void k_density(const typename Cx<R>::T* __restrict__ psi, int n_v, in
   }
 }
 
-// rho(d_j) = (1/N_r) sum_r dens(r) exp(-2 pi i (d1 i1/n1 + d2 i2/n2 + d3 i3/n3)); one CTA per d_j.
-__global__ void __launch_bounds__(256)
-k_density_ft(const double* __restrict__ dens, int n1, int n2, int n3, const int* __restrict__ dvec,
-             double2* __restrict__ rho) {
-  __shared__ double2 t1[128], t2[128], t3[128];
-  __shared__ double2 red[8];
-  const int j = blockIdx.x;
-  const int d1 = dvec[3 * j], d2 = dvec[3 * j + 1], d3 = dvec[3 * j + 2];
-  // exp(-2 pi i (d_a i_a mod n_a) / n_a), phases reduced exactly in integers
-  for (int i = threadIdx.x; i < n1; i += blockDim.x) {
-    double s, c;
-    sincospi(-2.0 * (double)((((long long)d1 * i) % n1 + n1) % n1) / n1, &s, &c);
-    t1[i] = make_double2(c, s);
-  }
-  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-    double s, c;
-    sincospi(-2.0 * (double)((((long long)d2 * i) % n2 + n2) % n2) / n2, &s, &c);
-    t2[i] = make_double2(c, s);
-  }
-  for (int i = threadIdx.x; i < n3; i += blockDim.x) {
-    double s, c;
-    sincospi(-2.0 * (double)((((long long)d3 * i) % n3 + n3) % n3) / n3, &s, &c);
-    t3[i] = make_double2(c, s);
-  }
-  __syncthreads();
-  const int64_t nr = (int64_t)n1 * n2 * n3;
-  double2 acc = make_double2(0.0, 0.0);
-  for (int64_t r = threadIdx.x; r < nr; r += blockDim.x) {
-    const int i3 = (int)(r % n3);
-    const int64_t q = r / n3;
-    const int i2 = (int)(q % n2), i1 = (int)(q / n2);
-    const double2 e = cmul(cmul(t1[i1], t2[i2]), t3[i3]);
-    const double f = dens[r];
-    acc.x += f * e.x;
-    acc.y += f * e.y;
-  }
-  for (int o = 16; o; o >>= 1) {
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-  }
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      s.x += red[w].x;
-      s.y += red[w].y;
+// exp(-2 pi i (k j mod n) / n) with the phase reduced exactly in integers
+__device__ __forceinline__ double2 twid(long long k, long long j, int n) {
+  const long long m = ((k * j) % n + n) % n;
+  double sn, cs;
+  sincospi(-2.0 * (double)m / (double)n, &sn, &cs);
+  return make_double2(cs, sn);
+}
+
+// rho(d) = (1/N_r) sum_r dens(r) exp(-2 pi i (d1 i1/n1 + d2 i2/n2 + d3 i3/n3)) for the
+// distinct differences d, as three pruned passes over the offsets d_a in [-s_a, s_a]:
+//   A1[i1][i2][k3] = sum_i3 dens * e3,  A2[i1][k2][k3] = sum_i2 A1 * e2,  rho(d) = sum_i1 A2 * e1 / N_r.
+__global__ void k_dft_axis3(const double* __restrict__ dens, int n1, int n2, int n3, int s3,
+                            double2* __restrict__ A1) {
+  const int K3 = 2 * s3 + 1;
+  const int64_t total = (int64_t)n1 * n2 * K3;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int k3 = (int)(e % K3);
+    const int64_t line = e / K3;                    // i1 * n2 + i2
+    const double* row = dens + line * n3;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int i3 = 0; i3 < n3; ++i3) {
+      const double2 t = twid(k3 - s3, i3, n3);
+      acc.x += row[i3] * t.x;
+      acc.y += row[i3] * t.y;
     }
-    rho[j] = make_double2(s.x / (double)nr, s.y / (double)nr);
+    A1[e] = acc;
+  }
+}
+
+__global__ void k_dft_axis2(const double2* __restrict__ A1, int n1, int n2, int s2, int s3,
+                            double2* __restrict__ A2) {
+  const int K2 = 2 * s2 + 1, K3 = 2 * s3 + 1;
+  const int64_t total = (int64_t)n1 * K2 * K3;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int k3 = (int)(e % K3);
+    const int k2 = (int)((e / K3) % K2);
+    const int i1 = (int)(e / ((int64_t)K3 * K2));
+    double2 acc = make_double2(0.0, 0.0);
+    for (int i2 = 0; i2 < n2; ++i2)
+      cfma(acc, A1[((int64_t)i1 * n2 + i2) * K3 + k3], twid(k2 - s2, i2, n2));
+    A2[e] = acc;
+  }
+}
+
+__global__ void k_dft_axis1(const double2* __restrict__ A2, int n1, int n2, int n3, int s2, int s3,
+                            const int* __restrict__ dvec, int nd, double2* __restrict__ rho) {
+  const int K2 = 2 * s2 + 1, K3 = 2 * s3 + 1;
+  const double inv = 1.0 / ((double)n1 * n2 * n3);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nd; j += gridDim.x * blockDim.x) {
+    const int d1 = dvec[3 * j], k2 = dvec[3 * j + 1] + s2, k3 = dvec[3 * j + 2] + s3;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int i1 = 0; i1 < n1; ++i1) cfma(acc, A2[((int64_t)i1 * K2 + k2) * K3 + k3], twid(d1, i1, n1));
+    rho[j] = make_double2(acc.x * inv, acc.y * inv);
   }
 }
 
@@ -248,10 +253,19 @@ cudaError_t launch_density(const chi0_plan_s* p, const void* psi_v, int n_v, dou
   return cudaGetLastError();
 }
 
-cudaError_t launch_density_ft(const chi0_plan_s* p, const double* dens, const int* dvec, int nd, double2* rho,
-                              cudaStream_t s) {
+size_t density_ft_ws_bytes(const chi0_plan_s* p, int s2, int s3) {
+  const size_t K2 = 2 * (size_t)s2 + 1, K3 = 2 * (size_t)s3 + 1;
+  return ((size_t)p->n1 * p->n2 * K3 + (size_t)p->n1 * K2 * K3) * sizeof(double2);
+}
+
+cudaError_t launch_density_ft(const chi0_plan_s* p, const double* dens, const int* dvec, int nd, int s2, int s3,
+                              void* ws, double2* rho, cudaStream_t s) {
   if (nd <= 0) return cudaSuccess;
-  k_density_ft<<<nd, 256, 0, s>>>(dens, p->n1, p->n2, p->n3, dvec, rho);
+  double2* A1 = reinterpret_cast<double2*>(ws);
+  double2* A2 = A1 + (size_t)p->n1 * p->n2 * (2 * s3 + 1);
+  k_dft_axis3<<<4 * 152, 256, 0, s>>>(dens, p->n1, p->n2, p->n3, s3, A1);
+  k_dft_axis2<<<4 * 152, 256, 0, s>>>(A1, p->n1, p->n2, s2, s3, A2);
+  k_dft_axis1<<<(nd + 255) / 256, 256, 0, s>>>(A2, p->n1, p->n2, p->n3, s2, s3, dvec, nd, rho);
   return cudaGetLastError();
 }
 

@@ -508,7 +508,6 @@ chi0_status chi0_gpp(chi0_plan p, int iq, const void* psi_v, int n_v, const void
   if (iq < 0 || iq >= (int)p->q.size()) return fail(p, CHI0_ERR_INVALID, "iq out of range");
   if (!psi_v || n_v < 1 || !eps_inv || !lattice || !q_frac || !Omega2 || !wt || !(n_el > 0.0))
     return fail(p, CHI0_ERR_INVALID, "bad argument");
-  if (p->n1 > 128 || p->n2 > 128 || p->n3 > 128) return fail(p, CHI0_ERR_UNSUPPORTED, "grid axes above 128");
   double b[3][3], omega_cell = 0.0;
   if (!recip_lattice(lattice, b, &omega_cell)) return fail(p, CHI0_ERR_INVALID, "singular lattice");
   const chi0::SphereQ& sq = p->q[iq];
@@ -550,13 +549,19 @@ chi0_status chi0_gpp(chi0_plan p, int iq, const void* psi_v, int n_v, const void
       return fail(p, CHI0_ERR_INVALID, "q + G = 0 at sphere point " + std::to_string(j));
   const double wp2 = 4.0 * M_PI * n_el / omega_cell;
   cudaStream_t s = (cudaStream_t)stream;
+  // offsets spanned by the differences along axes 2 and 3 (the transform is pruned to them)
+  const int s2 = hi[1] - lo[1], s3 = hi[2] - lo[2];
   double* dens = nullptr;
   int *d_dvec = nullptr, *d_idx = nullptr;
   double2* rho = nullptr;
   double* d_k = nullptr;
-  auto cleanup = [&]() { cudaFree(dens); cudaFree(d_dvec); cudaFree(d_idx); cudaFree(rho); cudaFree(d_k); };
+  void* ftw = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(dens); cudaFree(d_dvec); cudaFree(d_idx); cudaFree(rho); cudaFree(d_k); cudaFree(ftw);
+  };
   cudaError_t e;
-  if ((e = cudaMalloc((void**)&dens, sizeof(double) * p->nr)) != cudaSuccess ||
+  if ((e = cudaMalloc(&ftw, chi0::density_ft_ws_bytes(p, s2, s3))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&dens, sizeof(double) * p->nr)) != cudaSuccess ||
       (e = cudaMalloc((void**)&d_dvec, sizeof(int) * dvec.size())) != cudaSuccess ||
       (e = cudaMalloc((void**)&d_idx, sizeof(int) * idx.size())) != cudaSuccess ||
       (e = cudaMalloc((void**)&rho, sizeof(double2) * nd)) != cudaSuccess ||
@@ -565,7 +570,7 @@ chi0_status chi0_gpp(chi0_plan p, int iq, const void* psi_v, int n_v, const void
       (e = cudaMemcpyAsync(d_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_k, kvec.data(), sizeof(double) * kvec.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = chi0::launch_density(p, psi_v, n_v, dens, s)) != cudaSuccess ||
-      (e = chi0::launch_density_ft(p, dens, d_dvec, nd, rho, s)) != cudaSuccess ||
+      (e = chi0::launch_density_ft(p, dens, d_dvec, nd, s2, s3, ftw, rho, s)) != cudaSuccess ||
       (e = chi0::launch_gpp(nG, (const double2*)eps_inv, rho, d_idx, d_k, wp2, (double2*)Omega2, (double2*)wt, s)) !=
           cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess) {
