@@ -199,26 +199,35 @@ k_sigma_coh(const typename Cx<R>::T* __restrict__ m, int n_b, int nG, const doub
       xs[threadIdx.x] = b < n_b ? (R)x[(size_t)t * n_b + b] : (R)0;
     }
     __syncthreads();
+    // the thread's four elements share the column G' (rows a = tid/32 + 8q): m(G') and x are
+    // read once per band
     C part = cz(C{});
+    const int bcol = threadIdx.x & (CT - 1), a0 = threadIdx.x >> 5;
+    C cc[4], wv[4];
+    R dy[4];
+#pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int e = threadIdx.x + q * 256;
-      const int a = e / CT, bcol = e - a * CT;
-      const C cc = cs[a][bcol], w = ws[a][bcol];
-      if (cc.x == (R)0 && cc.y == (R)0) continue;
-      const R dy = (R)delta - w.y;
-#pragma unroll 4
-      for (int bb = 0; bb < CB; ++bb) {
-        // c / (x - wt + i delta) = c conj(d) / |d|^2,  d = dx + i dy
-        const R dx = xs[bb] - w.x;
+      cc[q] = cs[a0 + 8 * q][bcol];
+      wv[q] = ws[a0 + 8 * q][bcol];
+      dy[q] = (R)delta - wv[q].y;
+    }
+#pragma unroll 2
+    for (int bb = 0; bb < CB; ++bb) {
+      const C mjv = mj[bb][bcol];
+      const R xb = xs[bb];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        // c / (x - wt + i delta) = c conj(d) / |d|^2,  d = dx + i dy (c = 0: no pole, adds 0)
+        const R dx = xb - wv[q].x;
         R inv;
         if constexpr (sizeof(R) == 4)
-          inv = __fdividef(1.0f, dx * dx + dy * dy);     // 2-ulp reciprocal: terms carry FP32 errors anyway
+          inv = __fdividef(1.0f, dx * dx + dy[q] * dy[q]);   // 2-ulp reciprocal: terms carry FP32 errors anyway
         else
-          inv = (R)1 / (dx * dx + dy * dy);
-        C cr;                                             // c conj(d)
-        cr.x = fma(cc.x, dx, cc.y * dy);
-        cr.y = fma(cc.y, dx, -(cc.x * dy));
-        const C mm = cconjmul(mj[bb][bcol], mi[bb][a]);   // w_b m(G) conj(m(G'))
+          inv = (R)1 / (dx * dx + dy[q] * dy[q]);
+        C cr;                                                 // c conj(d)
+        cr.x = fma(cc[q].x, dx, cc[q].y * dy[q]);
+        cr.y = fma(cc[q].y, dx, -(cc[q].x * dy[q]));
+        const C mm = cconjmul(mjv, mi[bb][a0 + 8 * q]);       // w_b m(G) conj(m(G'))
         const C t2 = cmul(mm, cr);
         part.x = fma(t2.x, inv, part.x);
         part.y = fma(t2.y, inv, part.y);
