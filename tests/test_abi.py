@@ -83,3 +83,50 @@ def test_select_rejects_unsorted_and_small_capacity():
     E = np.sort(E)
     assert lib.chi0_select_accelerated(E.ctypes.data, 3, 1, 0.1, 1.0, 0.17, 2.2, out_c.ctypes.data,
                                        out_e.ctypes.data, out_w.ctypes.data, 2) == -1
+
+
+def test_create_rejects_bad_hermitian_flag_without_a_device():
+    import numpy as np
+    lib = P.lib()
+    g = np.zeros((1, 3), np.int32)
+    nG = np.ones(1, np.int32)
+    fr = np.zeros(1)
+    d = L.Chi0PlanDesc()
+    d.n1 = d.n2 = d.n3 = 24
+    d.n_q = 1
+    d.n_G = nG.ctypes.data_as(C.POINTER(C.c_int32))
+    d.gvec = g.ctypes.data_as(C.POINTER(C.c_int32))
+    d.n_freq = 1
+    d.freq_re = fr.ctypes.data_as(C.POINTER(C.c_double))
+    d.freq_im = fr.ctypes.data_as(C.POINTER(C.c_double))
+    d.delta = 1e-3
+    d.precision = L.CHI0_SPLIT_BF16
+    d.hermitian = 5
+    h = C.c_void_p()
+    assert lib.chi0_plan_create(C.byref(h), C.byref(d)) == L.CHI0_ERR_INVALID
+    assert b"hermitian" in lib.chi0_last_error(None)
+    assert h.value is None
+
+
+def test_host_selection_entry_points_reject_bad_arguments():
+    import numpy as np
+    lib = P.lib()
+    E = np.array([0.2, 0.3, 0.5, 0.9])
+    s = np.ones(4)
+    c = np.empty(256, np.int32)
+    e = np.empty(256)
+    w = np.empty(256)
+    ok = lib.chi0_select_quadrature(E.ctypes.data, 4, 2, 0.1, 1.0, 0.17, 2.2, 1, 1, 2, c.ctypes.data, e.ctypes.data,
+                                    w.ctypes.data, 256)
+    assert ok == 2 + 2 * 39                 # 19 bins, 39 Simpson nodes, 2 states each
+    for grid, rule, states in ((2, 0, 1), (0, 3, 1), (0, 0, 0)):
+        assert lib.chi0_select_quadrature(E.ctypes.data, 4, 2, 0.1, 1.0, 0.17, 2.2, grid, rule, states,
+                                          c.ctypes.data, e.ctypes.data, w.ctypes.data, 64) == -1
+    assert lib.chi0_select_quadrature(E.ctypes.data, 4, 2, 0.1, 1.0, 0.17, 2.2, 0, 0, 1, c.ctypes.data,
+                                      e.ctypes.data, w.ctypes.data, 3) == -1          # capacity
+    assert lib.chi0_select_adaptive(E.ctypes.data, 4, 2, s.ctypes.data, 0.1, 1.0, 0.17, 2.2, 3, 1,
+                                    c.ctypes.data, e.ctypes.data, w.ctypes.data, 64) > 2
+    assert lib.chi0_select_adaptive(E.ctypes.data, 4, 2, None, 0.1, 1.0, 0.17, 2.2, 3, 1,
+                                    c.ctypes.data, e.ctypes.data, w.ctypes.data, 64) == -1
+    assert lib.chi0_select_adaptive(E.ctypes.data, 4, 2, s.ctypes.data, 0.1, 1.0, 0.17, 2.2, -1, 1,
+                                    c.ctypes.data, e.ctypes.data, w.ctypes.data, 64) == -1
