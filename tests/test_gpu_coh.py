@@ -97,3 +97,40 @@ def test_sigma_coh_whole_chain_fp64():
     # eps^-1 of the FP64 chain differs from the oracle's by 5e-16 x cond(eps) (5e4)
     assert np.max(np.abs(sig - sig_ref) / parts["abs_sum"]) < 1e-10
     assert rel_fro(sig, sig_ref) < 1e-10
+
+
+def test_arguments_are_checked():
+    import ctypes as C
+
+    import paper_1601_06767_gb300._lib as L
+    from paper_1601_06767_gb300 import Chi0Plan
+    prob = make_problem("c1", n_G=[27])
+    A = prob.a * np.eye(3)
+    with Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision="bf16", gw=prob.gw) as plan:
+        lib = L.lib()
+        eye = _dev(np.eye(27, dtype=np.complex128))
+        psi_v = plan.wfn_to_grid(_dev(prob.coeff_v(0, np.arange(2))))
+        q = np.ascontiguousarray(prob.q_frac[0], dtype=np.float64)
+        Af = np.ascontiguousarray(A)
+        assert lib.chi0_gpp(plan._h, 3, _ptr_of(psi_v), 2, _ptr_of(eye), Af.ctypes.data, q.ctypes.data, 4.0,
+                            _ptr_of(eye), _ptr_of(eye), C.c_void_p(0)) == L.CHI0_ERR_INVALID   # no sphere 3
+        with pytest.raises(L.Chi0Error):
+            plan.gpp(0, psi_v, eye, np.zeros((3, 3)), prob.q_frac[0], 4.0)          # singular lattice
+        with pytest.raises(L.Chi0Error):
+            plan.gpp(0, psi_v, eye, A, prob.q_frac[0], -1.0)                        # no electrons
+        Om2, wt = plan.gpp(0, psi_v, eye, A, prob.q_frac[0], 4.0)
+        # eps^-1 = I: delta - eps^-1 vanishes on the diagonal, so those elements carry no pole
+        assert float(wt.diagonal().abs().max()) == 0.0
+        v = _dev(plan.coulomb(0, A, prob.q_frac[0]))
+        out = np.ones(4)
+        assert lib.chi0_sigma_coh(plan._h, 0, None, 2, 0, None, None, None, None, None, out.ctypes.data,
+                                  C.c_void_p(0)) == L.CHI0_OK
+        assert np.all(out == 0.0)                                                   # no bands: zero
+        assert lib.chi0_epsilon(plan._h, 0, _ptr_of(eye), _ptr_of(v), 2, _ptr_of(eye), C.c_void_p(0)) == \
+            L.CHI0_ERR_INVALID
+        plan.sync_status()
+
+
+def _ptr_of(t):
+    import ctypes as C
+    return C.c_void_p(t.data_ptr())
