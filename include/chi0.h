@@ -190,10 +190,11 @@ chi0_status chi0_selftest_wait(chi0_plan plan, double budget_ms, void* stream);
  * persistent work list (1, 2, 4, 8, 16 or all tile rows) and the pairs per
  * launch (2048, 4096, ... up to max_pairs) on synthetic operands
  * written into the plan's workspace for sphere iq (a scratch chi0 is
- * allocated and freed), keeps the fastest in the plan and appends it to the
+ * allocated and freed; every candidate over two launches, the three fastest
+ * again over four), keeps the fastest in the plan and appends it to the
  * text cache named by the environment variable CHI0_TUNE_CACHE (default
  * $HOME/.cache/chi0_tune.txt).  Unless flags & 1, a cached entry for the same
- * device, sphere size, frequency count, precision and products is applied
+ * device, sphere size, frequency count, precision, products and Hermitian mode is applied
  * instead of timing; chi0_plan_create applies one for sphere 0.  Before tuning,
  * the environment variable CHI0_TC_PAIR (0 or 1) read at plan creation selects
  * the variant.

@@ -133,34 +133,46 @@ extern "C" chi0_status chi0_autotune(chi0_plan p, int iq, int flags, double* bes
   int best_g = saved_group, best_pair = saved_pair;
   int64_t best_b = saved_block;
   std::string why;
-  for (int pair = 0; pair < 2; ++pair)
-  for (int64_t b : blocks)
-    for (int g : groups) {
-      p->tc_pair = pair;
-      p->tc_group = g;
-      p->block_pairs = b;
-      const int nc = (int)(b / nv);
-      float ms = 0.f;
-      cudaError_t le = cudaSuccess;
-      for (int rep = 0; rep < 3 && le == cudaSuccess; ++rep) {
-        if (rep == 1) cudaEventRecord(e0, s);
-        le = launch_weights(p, 0, b, nc, Ev, Ec, nullptr, p->d_f, s);
-        if (le == cudaSuccess) le = launch_contract_tc(p, nG, (const float2*)p->d_M, b, p->d_f, chi, s, &why);
-      }
-      cudaEventRecord(e1, s);
-      if (le != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
-        cudaGetLastError();
-        continue;
-      }
-      cudaEventElapsedTime(&ms, e0, e1);
-      const double us = 1e3 * ms / 2.0 / (double)b;
-      if (us < best) {
-        best = us;
-        best_g = g;
-        best_b = b;
-        best_pair = pair;
-      }
+  // time one candidate: one untimed launch, then `reps` timed ones; microseconds per pair or < 0 on failure
+  auto time_candidate = [&](int pair, int64_t b, int g, int reps) -> double {
+    p->tc_pair = pair;
+    p->tc_group = g;
+    p->block_pairs = b;
+    const int nc = (int)(b / nv);
+    float ms = 0.f;
+    cudaError_t le = cudaSuccess;
+    for (int rep = 0; rep <= reps && le == cudaSuccess; ++rep) {
+      if (rep == 1) cudaEventRecord(e0, s);
+      le = launch_weights(p, 0, b, nc, Ev, Ec, nullptr, p->d_f, s);
+      if (le == cudaSuccess) le = launch_contract_tc(p, nG, (const float2*)p->d_M, b, p->d_f, chi, s, &why);
     }
+    cudaEventRecord(e1, s);
+    if (le != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      cudaGetLastError();
+      return -1.0;
+    }
+    cudaEventElapsedTime(&ms, e0, e1);
+    return 1e3 * ms / (double)reps / (double)b;
+  };
+  // pass 1: every candidate over two launches; pass 2: the three fastest again over four launches
+  struct Cand { double us; int pair; int64_t b; int g; };
+  std::vector<Cand> cands;
+  for (int pair = 0; pair < 2; ++pair)
+    for (int64_t b : blocks)
+      for (int g : groups) {
+        const double us = time_candidate(pair, b, g, 2);
+        if (us > 0.0) cands.push_back({us, pair, b, g});
+      }
+  std::sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) { return x.us < y.us; });
+  for (size_t k = 0; k < cands.size() && k < 3; ++k) {
+    const double us = time_candidate(cands[k].pair, cands[k].b, cands[k].g, 4);
+    if (us > 0.0 && us < best) {
+      best = us;
+      best_g = cands[k].g;
+      best_b = cands[k].b;
+      best_pair = cands[k].pair;
+    }
+  }
   p->prof_timing = timing;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
