@@ -208,7 +208,8 @@ k_pair_gather(const typename Cx<R>::T* __restrict__ D, int nc, int64_t row0, int
 // so each line transform only needs its first nk outputs:
 //   sum_i x(i) e^{2 pi i kk i/n} = sum_{a<P} e^{2 pi i a kk/n} F_a(kk mod Q),
 //   F_a(m) = sum_{b<Q} x(a + P b) e^{2 pi i b m/Q}   (Q-point FFT in registers).
-// Shared memory: Uv'[TV][n][ld], Uc[NCB][n][ld], X[NCB][TV][n][ldx], tables.
+// Shared memory: Uv'[TV][n][ld], Uc[NCB][n][ld], X[NCB][TV][n][ldx], tables
+// (the twiddles copied from the plan's table of n-th roots of unity).
 // ---------------------------------------------------------------------------
 constexpr int NKMAX = 28;
 
@@ -298,15 +299,16 @@ __global__ void __launch_bounds__(192, (TV * NCB >= 4) ? 2 : 1)
 k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ v_idx, int v0, int nv,
                   const float2* __restrict__ psi_c, const int32_t* __restrict__ c_idx, int c0, int nc, int c_per_cta,
                   int nk2, int nk3, int nk2p, int nk3p, const float2* __restrict__ T2, const float2* __restrict__ T3,
-                  float2* __restrict__ D) {
+                  const float2* __restrict__ Tn, float2* __restrict__ D) {
   constexpr int n = P * Q;
   constexpr int ld = n | 1;
+  constexpr int NP = NCB * TV;                               // pairs per iteration
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ldx = nk3 | 1;
   float2* Uv = reinterpret_cast<float2*>(smem_raw);          // [TV][n][ld]
   float2* Uc = Uv + TV * n * ld;                             // [NCB][n][ld]
-  const int ldx = nk3 | 1;
-  float2* X = Uc + NCB * n * ld;                             // [NCB][TV][n][ldx]
-  float2* ow = X + NCB * TV * n * ldx;                       // [P][NKMAX] e^{2 pi i a kk/n}
+  float2* X = Uc + NCB * n * ld;                             // [NP][n][ldx]
+  float2* ow = X + NP * n * ldx;                             // [P][NKMAX] e^{2 pi i a kk/n}
   float2* tw = ow + P * NKMAX;                               // [Q/2]      e^{2 pi i j/Q}
   const int i1 = blockIdx.x;
   const int jv0 = blockIdx.y * TV;
@@ -319,15 +321,9 @@ k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
 
   for (int e = threadIdx.x; e < P * NKMAX; e += blockDim.x) {
     const int a = e / NKMAX, kk = e - a * NKMAX;
-    double sn, cs;
-    sincospi(2.0 * (double)((a * kk) % n) / (double)n, &sn, &cs);
-    ow[e] = make_float2((float)cs, (float)sn);
+    ow[e] = Tn[(a * kk) % n];
   }
-  for (int e = threadIdx.x; e < Q / 2; e += blockDim.x) {
-    double sn, cs;
-    sincospi(2.0 * (double)e / (double)Q, &sn, &cs);
-    tw[e] = make_float2((float)cs, (float)sn);
-  }
+  for (int e = threadIdx.x; e < Q / 2; e += blockDim.x) tw[e] = Tn[e * P];
   for (int j = 0; j < TV; ++j) {
     const int jv = jv0 + j;
     const bool ok = jv < nv;
@@ -345,8 +341,8 @@ k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
       Uv[(j * n + i2) * ld + i3] = v;
     }
   }
-  const int items1 = NCB * TV * n;
-  const int items2 = NCB * TV * nk3;
+  const int items1 = NP * n;
+  const int items2 = NP * nk3;
   for (int jc0 = jc_begin; jc0 < jc_end; jc0 += NCB) {
 #pragma unroll
     for (int cb = 0; cb < NCB; ++cb) {
@@ -402,7 +398,7 @@ k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
 template <int P, int Q, int NK, int TV, int NCB>
 size_t fft_planes_smem(int nk3) {
   constexpr int n = P * Q, ld = n | 1;
-  const int ldx = nk3 | 1;
+  const size_t ldx = nk3 | 1;
   return ((size_t)TV * n * ld + (size_t)NCB * n * ld + (size_t)NCB * TV * n * ldx + P * NKMAX + Q / 2) *
          sizeof(float2);
 }
@@ -420,7 +416,7 @@ cudaError_t launch_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void
   while (cpc > NCB && (int64_t)p->n1 * vt * ((nc + cpc - 1) / cpc) < 4 * 152) cpc >>= 1;
   dim3 grid(p->n1, vt, (nc + cpc - 1) / cpc);
   kern<<<grid, 192, sm, st>>>((const float2*)psi_v, v_idx, v0, nv, (const float2*)psi_c, c_idx, c0, nc, cpc, s.nk2,
-                              s.nk3, s.nk2p, s.nk3p, s.T2f, s.T3f, (float2*)D);
+                              s.nk3, s.nk2p, s.nk3p, s.T2f, s.T3f, p->Tnf, (float2*)D);
   return cudaGetLastError();
 }
 
