@@ -27,6 +27,9 @@ struct SphereQ {
   int* ent_box = nullptr;             // [nG] (k2-k2min)*nk3 + (k3-k3min)
   int* ent_k1 = nullptr;              // [nG] k1 - k1min
   int* ent_j = nullptr;               // [nG] index of the point in the caller's order
+  int ncol = 0;                       // distinct (k2, k3) columns holding sphere points
+  int* col_off = nullptr;             // [ncol] (k2-k2min)*nk3 + (k3-k3min) of each column
+  int* col_start = nullptr;           // [ncol + 1] first entry of each column (entries in column order)
   double2* T1d = nullptr; float2* T1f = nullptr;   // [n1][nk1]   exp(+2 pi i k1 i1/n1)
   double2* T2d = nullptr; float2* T2f = nullptr;   // [n2][nk2p]  exp(+2 pi i k2 i2/n2)
   double2* T3d = nullptr; float2* T3f = nullptr;   // [n3][nk3p]  exp(+2 pi i k3 i3/n3)

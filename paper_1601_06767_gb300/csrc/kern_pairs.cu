@@ -443,6 +443,85 @@ cudaError_t try_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void* p
 }
 
 // ---------------------------------------------------------------------------
+// Stage 3 with register FFTs (FP32, cubic grids n = P*Q): one thread per
+// (pair, column (k2, k3) of the sphere).  The thread reads the column's n
+// values D_p(i1, k2, k3) (consecutive threads: neighbouring columns, so the
+// loads of a warp are contiguous), shifts them by e^{2 pi i k1min i1/n},
+// transforms along i1 keeping the first nk1 outputs and writes the column's
+// sphere points to M.
+// ---------------------------------------------------------------------------
+template <int P, int Q, int NK>
+__global__ void __launch_bounds__(kThreads)
+k_pair_gather_fft(const float2* __restrict__ D, int nc, int64_t row0, int64_t ldv, int64_t box, int nG,
+                  int ncol, int64_t n_items, const int* __restrict__ col_off, const int* __restrict__ col_start,
+                  const int* __restrict__ ent_k1, const int* __restrict__ ent_j, const float2* __restrict__ T1,
+                  int nk1, const float2* __restrict__ Tn, float scale, float2* __restrict__ M) {
+  constexpr int n = P * Q;
+  __shared__ float2 ow[P * NKMAX];   // e^{2 pi i a kk/n}
+  __shared__ float2 tw[Q / 2];       // e^{2 pi i j/Q}
+  __shared__ float2 sh[n];           // e^{2 pi i k1min i1/n}
+  for (int e = threadIdx.x; e < P * NKMAX; e += blockDim.x) {
+    const int a = e / NKMAX, kk = e - a * NKMAX;
+    ow[e] = Tn[(a * kk) % n];
+  }
+  for (int e = threadIdx.x; e < Q / 2; e += blockDim.x) tw[e] = Tn[e * P];
+  for (int e = threadIdx.x; e < n; e += blockDim.x) sh[e] = T1[(size_t)e * nk1];
+  __syncthreads();
+  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (item >= n_items) return;
+  const int pl = (int)(item / ncol), c = (int)(item - (int64_t)pl * ncol);
+  const int jv = pl / nc, jc = pl - jv * nc;
+  const float2* Dp = D + (int64_t)pl * n * box + col_off[c];
+  float2 acc[NK];
+  line_transform<P, Q, NK>([&](int i1) { return cmul(Dp[(int64_t)i1 * box], sh[i1]); }, nk1, ow, tw, acc);
+  float2* out = M + (row0 + (int64_t)jv * ldv + jc) * nG;
+  int t = col_start[c];
+  const int t_end = col_start[c + 1];
+  int k = t < t_end ? ent_k1[t] : NK;
+  // entries of a column are sorted by k1; the loop over kk is unrolled so acc stays in registers
+#pragma unroll
+  for (int kk = 0; kk < NK; ++kk) {
+    while (k == kk) {
+      out[ent_j[t]] = make_float2(acc[kk].x * scale, acc[kk].y * scale);
+      ++t;
+      k = t < t_end ? ent_k1[t] : NK;
+    }
+  }
+}
+
+template <int P, int Q, int NK>
+cudaError_t launch_gather_fft(const chi0_plan_s* p, const SphereQ& s, const void* D, int nv, int nc, int64_t row0,
+                              int64_t ldv, void* M, cudaStream_t st) {
+  const int64_t items = (int64_t)nv * nc * s.ncol;
+  const int64_t blocks = (items + kThreads - 1) / kThreads;
+  if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+  k_pair_gather_fft<P, Q, NK><<<(unsigned)blocks, kThreads, 0, st>>>(
+      (const float2*)D, nc, row0, ldv, (int64_t)s.nk2 * s.nk3, s.nG, s.ncol, items, s.col_off, s.col_start,
+      s.ent_k1, s.ent_j, s.T1f, s.nk1, p->Tnf, (float)(1.0 / (double)p->nr), (float2*)M);
+  return cudaGetLastError();
+}
+
+// FP32 stage 3 with register FFTs when the grid is cubic, n = P*Q is supported
+// and nk1 fits NKMAX; returns cudaErrorNotSupported otherwise.
+cudaError_t try_gather_fft(const chi0_plan_s* p, const SphereQ& s, const void* D, int nv, int nc, int64_t row0,
+                           int64_t ldv, void* M, cudaStream_t st) {
+  if (!(p->n1 == p->n2 && p->n2 == p->n3) || s.nk1 > NKMAX || s.ncol <= 0) return cudaErrorNotSupported;
+#define CHI0_GATHER_CASE(P, Q)                                                                         \
+  if (s.nk1 <= 12) return launch_gather_fft<P, Q, 12>(p, s, D, nv, nc, row0, ldv, M, st);               \
+  if (s.nk1 <= 16) return launch_gather_fft<P, Q, 16>(p, s, D, nv, nc, row0, ldv, M, st);               \
+  if (s.nk1 <= 20) return launch_gather_fft<P, Q, 20>(p, s, D, nv, nc, row0, ldv, M, st);               \
+  return launch_gather_fft<P, Q, 28>(p, s, D, nv, nc, row0, ldv, M, st);
+  switch (p->n1) {
+    case 24: { CHI0_GATHER_CASE(3, 8) }
+    case 36: { CHI0_GATHER_CASE(9, 4) }
+    case 48: { CHI0_GATHER_CASE(3, 16) }
+    case 96: { CHI0_GATHER_CASE(3, 32) }
+    default: return cudaErrorNotSupported;
+  }
+#undef CHI0_GATHER_CASE
+}
+
+// ---------------------------------------------------------------------------
 // Stages 1+2 for planes too large for shared memory (FP64 on large grids):
 // stage 1 runs over chunks of ROWS rows (i2) of the plane, reading the valence
 // and conduction rows of each chunk; stage 2 follows once X holds every row.
@@ -646,6 +725,8 @@ cudaError_t launch_pair_gather(const chi0_plan_s* p, int iq, const void* D, int 
   const int npl = nv * nc;
   if (npl == 0) return cudaSuccess;
   if (is_split(p)) {
+    cudaError_t e = try_gather_fft(p, sq, D, nv, nc, row0, ldv, M, s);
+    if (e != cudaErrorNotSupported) return e;
     size_t sm = (size_t)p->n1 * sq.nk1 * sizeof(float2);
     k_pair_gather<float><<<npl, kThreads, sm, s>>>((const float2*)D, nc, row0, ldv, p->n1, box, sq.nG, sq.nk1,
                                                    sq.ent_box, sq.ent_k1, sq.ent_j, sq.T1f,

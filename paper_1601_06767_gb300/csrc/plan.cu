@@ -86,7 +86,7 @@ cudaError_t make_table_t(int n, int kmin, int nk, double2** dd, float2** df) {
 }
 
 void free_sphere(SphereQ& s) {
-  cudaFree(s.ent_box); cudaFree(s.ent_k1); cudaFree(s.ent_j);
+  cudaFree(s.ent_box); cudaFree(s.ent_k1); cudaFree(s.ent_j); cudaFree(s.col_off); cudaFree(s.col_start);
   cudaFree(s.T1d); cudaFree(s.T1f); cudaFree(s.T2d); cudaFree(s.T2f);
   cudaFree(s.T3d); cudaFree(s.T3f);
   s = SphereQ();
@@ -146,9 +146,20 @@ chi0_status analyse_sphere(chi0_plan_s* p, const int32_t* g, int nG, SphereQ* s)
     k1[t] = g[3 * j] - s->k1min;
     jj[t] = j;
   }
+  // columns: runs of equal box offset in column order
+  std::vector<int> col_off, col_start;
+  for (int t = 0; t < nG; ++t)
+    if (t == 0 || box[t] != box[t - 1]) {
+      col_off.push_back(box[t]);
+      col_start.push_back(t);
+    }
+  col_start.push_back(nG);
+  s->ncol = (int)col_off.size();
   CK(p, upload(&s->ent_box, box));
   CK(p, upload(&s->ent_k1, k1));
   CK(p, upload(&s->ent_j, jj));
+  CK(p, upload(&s->col_off, col_off));
+  CK(p, upload(&s->col_start, col_start));
   CK(p, make_table(p->n1, s->k1min, s->nk1, s->nk1, &s->T1d, &s->T1f));
   CK(p, make_table(p->n2, s->k2min, s->nk2, s->nk2p, &s->T2d, &s->T2f));
   CK(p, make_table(p->n3, s->k3min, s->nk3, s->nk3p, &s->T3d, &s->T3f));
