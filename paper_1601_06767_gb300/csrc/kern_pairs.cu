@@ -343,13 +343,14 @@ k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
   }
   const int items1 = NP * n;
   const int items2 = NP * nk3;
-  for (int jc0 = jc_begin; jc0 < jc_end; jc0 += NCB) {
+  // asynchronous copies of the NCB conduction planes starting at jc0, one row per
+  // warp: the whole plane is in flight at once
+  auto load_conduction = [&](int jc0) {
 #pragma unroll
     for (int cb = 0; cb < NCB; ++cb) {
       const int jc = jc0 + cb;
       const int64_t band = jc < jc_end ? (c_idx ? c_idx[c0 + jc] : c0 + jc) : -1;
       const float2* src = psi_c + (band < 0 ? 0 : band) * nr + (int64_t)i1 * plane;
-      // asynchronous copies, one row per warp: the whole plane is in flight at once
       for (int i2 = warp; i2 < n; i2 += nwarp) {
         float2* dst = Uc + (cb * n + i2) * ld;
         const float2* sr = src + i2 * n;
@@ -362,6 +363,9 @@ k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
         }
       }
     }
+  };
+  if (jc_begin < jc_end) load_conduction(jc_begin);
+  for (int jc0 = jc_begin; jc0 < jc_end; jc0 += NCB) {
     cp_async_wait_all();
     __syncthreads();
     // stage 1: one line (i2) of one (valence, conduction) pair per thread
@@ -377,6 +381,8 @@ k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
         if (kk < nk3) xo[kk] = acc[kk];
     }
     __syncthreads();
+    // the conduction planes are free again: the next ones load while stage 2 runs
+    if (jc0 + NCB < jc_end) load_conduction(jc0 + NCB);
     // stage 2: one kept k3 column of one pair per thread
     for (int it = threadIdx.x; it < items2; it += blockDim.x) {
       const int kk3 = it % nk3, jj = it / nk3, j = jj % TV, cb = jj / TV;
@@ -391,7 +397,8 @@ k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
           if (kk < nk2) dst[(int64_t)kk * nk3] = acc[kk];
       }
     }
-    __syncthreads();
+    // no barrier here: the wait and barrier at the top of the next iteration order
+    // these reads of X before the next stage 1 writes it
   }
 }
 
