@@ -33,3 +33,26 @@ def test_pairs_fp32_all_grids(name, nv, nc):
     err = rel_fro(M, ref)
     print(f"\n{name}: n={prob.n} N_G={ref.shape[1]} pairs rel err {err:.2e}")
     assert err < 2e-6
+
+
+@pytest.mark.parametrize("name,n_g", [("c1", 300), ("c2", 900)])
+def test_pairs_fp32_scattered_g_list(name, n_g):
+    """A G list that is not a sphere: distinct vectors drawn at random from the
+    box |g_i| <= n/4 - 1, in random order, so that columns (k2, k3) have holes
+    and lone points and the caller's order is unrelated to column order."""
+    from paper_1601_06767_gb300 import Chi0Plan
+    prob = make_problem(name)
+    rng = np.random.default_rng(77)
+    r = prob.n // 4 - 1
+    box = np.stack(np.meshgrid(*(np.arange(-r, r + 1),) * 3, indexing="ij"), -1).reshape(-1, 3)
+    g = box[rng.choice(box.shape[0], n_g, replace=False)].astype(np.int32)
+    cv, cc = prob.coeff_v(0, np.arange(2)), prob.coeff_c(np.arange(3))
+    uv, uc = wfn_to_grid(cv, prob.gw, prob.n), wfn_to_grid(cc, prob.gw, prob.n)
+    ref = pair_elements(uv, uc, g, prob.n)
+    with Chi0Plan(prob.n, [g], prob.omega, prob.delta, precision="bf16", gw=prob.gw) as plan:
+        M = plan.pairs(0, plan.wfn_to_grid(_dev(cv)), plan.wfn_to_grid(_dev(cc)))
+        plan.sync_status()
+        M = M.cpu().numpy()
+    err = np.max(np.abs(M - ref)) / np.max(np.abs(ref))
+    print(f"\n{name}: scattered G list of {n_g}, max abs err / max |M| {err:.2e}")
+    assert err < 2e-6
