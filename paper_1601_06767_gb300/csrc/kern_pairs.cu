@@ -268,29 +268,27 @@ __device__ __forceinline__ void fft_reg(float2 (&x)[Q], const float2* __restrict
   }
 }
 
-// acc[kk] = sum over the P sub-sequences of one length-n line (outputs kk < nk <= NK)
+// acc[kk] = sum over the P sub-sequences of one length-n line, for every kk < NK
+// (the caller uses the first nk; computing all NK avoids a predicate per output)
 template <int P, int Q, int NK, typename Load>
-__device__ __forceinline__ void line_transform(Load load, int nk, const float2* __restrict__ ow,
+__device__ __forceinline__ void line_transform(Load load, const float2* __restrict__ ow,
                                                const float2* __restrict__ tw, float2 (&acc)[NK]) {
+  {
+    float2 x[Q];
 #pragma unroll
-  for (int kk = 0; kk < NK; ++kk) acc[kk] = make_float2(0.f, 0.f);
+    for (int b = 0; b < Q; ++b) x[b] = load(P * b);
+    fft_reg<Q>(x, tw);
+#pragma unroll
+    for (int kk = 0; kk < NK; ++kk) acc[kk] = x[kk % Q];
+  }
 #pragma unroll 1
-  for (int a = 0; a < P; ++a) {
+  for (int a = 1; a < P; ++a) {
     float2 x[Q];
 #pragma unroll
     for (int b = 0; b < Q; ++b) x[b] = load(a + P * b);
     fft_reg<Q>(x, tw);
 #pragma unroll
-    for (int kk = 0; kk < NK; ++kk) {
-      if (kk < nk) {
-        if (a == 0) {
-          acc[kk].x += x[kk % Q].x;
-          acc[kk].y += x[kk % Q].y;
-        } else {
-          cfma(acc[kk], x[kk % Q], ow[a * NKMAX + kk]);
-        }
-      }
-    }
+    for (int kk = 0; kk < NK; ++kk) cfma(acc[kk], x[kk % Q], ow[a * NKMAX + kk]);
   }
 }
 
@@ -374,7 +372,7 @@ k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
       const float2* uv = Uv + (j * n + i2) * ld;
       const float2* uc = Uc + (cb * n + i2) * ld;
       float2 acc[NK];
-      line_transform<P, Q, NK>([&](int i3) { return cconjmul(uv[i3], uc[i3]); }, nk3, ow, tw, acc);
+      line_transform<P, Q, NK>([&](int i3) { return cconjmul(uv[i3], uc[i3]); }, ow, tw, acc);
       float2* xo = X + ((cb * TV + j) * n + i2) * ldx;
 #pragma unroll
       for (int kk = 0; kk < NK; ++kk)
@@ -389,7 +387,7 @@ k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
       const int jv = jv0 + j, jc = jc0 + cb;
       const float2* xi = X + ((cb * TV + j) * n) * ldx + kk3;
       float2 acc[NK];
-      line_transform<P, Q, NK>([&](int i2) { return xi[i2 * ldx]; }, nk2, ow, tw, acc);
+      line_transform<P, Q, NK>([&](int i2) { return xi[i2 * ldx]; }, ow, tw, acc);
       if (jv < nv && jc < jc_end) {
         float2* dst = D + ((int64_t)(jv * nc + jc) * n + i1) * box + kk3;
 #pragma unroll
@@ -480,7 +478,7 @@ k_pair_gather_fft(const float2* __restrict__ D, int nc, int64_t row0, int64_t ld
   const int jv = pl / nc, jc = pl - jv * nc;
   const float2* Dp = D + (int64_t)pl * n * box + col_off[c];
   float2 acc[NK];
-  line_transform<P, Q, NK>([&](int i1) { return cmul(Dp[(int64_t)i1 * box], sh[i1]); }, nk1, ow, tw, acc);
+  line_transform<P, Q, NK>([&](int i1) { return cmul(Dp[(int64_t)i1 * box], sh[i1]); }, ow, tw, acc);
   float2* out = M + (row0 + (int64_t)jv * ldv + jc) * nG;
   int t = col_start[c];
   const int t_end = col_start[c + 1];
