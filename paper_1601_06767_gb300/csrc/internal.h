@@ -83,7 +83,6 @@ struct chi0_plan_s {
   int64_t graph_family[CHI0_K_COUNT] = {};   // kernel launches per family inside the captured graph
   double* d_bwd = nullptr;   // adjoint work: per-pair grad dE and per-tile partial sums
   void* d_inv = nullptr;     // dielectric-inverse workspace (grown on demand)
-  double2* Tnd = nullptr; float2* Tnf = nullptr;   // [n3] exp(+2 pi i e/n3), register-FFT twiddles
   size_t inv_bytes = 0;
   size_t ws_bytes = 0;
   std::string err;

@@ -208,8 +208,7 @@ k_pair_gather(const typename Cx<R>::T* __restrict__ D, int nc, int64_t row0, int
 // so each line transform only needs its first nk outputs:
 //   sum_i x(i) e^{2 pi i kk i/n} = sum_{a<P} e^{2 pi i a kk/n} F_a(kk mod Q),
 //   F_a(m) = sum_{b<Q} x(a + P b) e^{2 pi i b m/Q}   (Q-point FFT in registers).
-// Shared memory: Uv'[TV][n][ld], Uc[NCB][n][ld], X[NCB][TV][n][ldx], tables
-// (the twiddles copied from the plan's table of n-th roots of unity).
+// Shared memory: Uv'[TV][n][ld], Uc[NCB][n][ld], X[NCB][TV][n][ldx].
 // ---------------------------------------------------------------------------
 constexpr int NKMAX = 28;
 
@@ -230,9 +229,113 @@ __host__ __device__ constexpr int bitrev(int i) {
   return r;
 }
 
-// in-place Q-point transform with e^{+2 pi i/Q}; tw[j] = e^{2 pi i j/Q}, j < Q/2
-template <int Q>
-__device__ __forceinline__ void fft_reg(float2 (&x)[Q], const float2* __restrict__ tw) {
+// n-th roots of unity as compile-time constants in constant memory, so that the
+// register FFTs multiply by constant-bank operands (no shared-memory twiddle
+// loads, no registers held for them).  Values: cos and sin of 2 pi m / n from
+// their Taylor series in double, evaluated by the compiler on |x| <= pi/4 after
+// an exact reduction of m / n to the first octant, then rounded to float.
+constexpr double kTwoPi = 6.283185307179586476925;
+constexpr double cx_sin_series(double x) {
+  double term = x, sum = x;
+  for (int k = 1; k < 14; ++k) {
+    term *= -x * x / (double)((2 * k) * (2 * k + 1));
+    sum += term;
+  }
+  return sum;
+}
+constexpr double cx_cos_series(double x) {
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 14; ++k) {
+    term *= -x * x / (double)((2 * k - 1) * (2 * k));
+    sum += term;
+  }
+  return sum;
+}
+template <int N> struct Roots {
+  float re[N];
+  float im[N];
+};
+template <int N>
+constexpr Roots<N> make_roots() {
+  Roots<N> r{};
+  for (int m = 0; m < N; ++m) {
+    const int q = (4 * m) / N;                 // quadrant
+    const int num = 4 * m - q * N;             // angle within the quadrant = 2 pi num / (4 N), num in [0, N)
+    double c = 0.0, sn = 0.0;
+    if (2 * num <= N) {                        // <= pi/4
+      const double x = kTwoPi * num / (4.0 * N);
+      c = cx_cos_series(x);
+      sn = cx_sin_series(x);
+    } else {                                   // complement, pi/2 - angle < pi/4
+      const double x = kTwoPi * (N - num) / (4.0 * N);
+      c = cx_sin_series(x);
+      sn = cx_cos_series(x);
+    }
+    double re = c, im = sn;
+    if (q == 1) { re = -sn; im = c; }
+    if (q == 2) { re = -c; im = -sn; }
+    if (q == 3) { re = sn; im = -c; }
+    r.re[m] = (float)re;
+    r.im[m] = (float)im;
+  }
+  return r;
+}
+constexpr Roots<24> k_roots24 = make_roots<24>();
+constexpr Roots<36> k_roots36 = make_roots<36>();
+constexpr Roots<48> k_roots48 = make_roots<48>();
+constexpr Roots<96> k_roots96 = make_roots<96>();
+__constant__ Roots<24> c_roots24 = k_roots24;
+__constant__ Roots<36> c_roots36 = k_roots36;
+__constant__ Roots<48> c_roots48 = k_roots48;
+__constant__ Roots<96> c_roots96 = k_roots96;
+
+// combination factors e^{2 pi i a kk / N} of the P sub-transforms, [a][kk] for kk < NKMAX,
+// so that a runtime sub-transform index a costs one address computation
+template <int P, int N> struct CombTable {
+  float re[P][NKMAX];
+  float im[P][NKMAX];
+};
+template <int P, int N>
+constexpr CombTable<P, N> make_comb(const Roots<N>& r) {
+  CombTable<P, N> t{};
+  for (int a = 0; a < P; ++a)
+    for (int kk = 0; kk < NKMAX; ++kk) {
+      t.re[a][kk] = r.re[(a * kk) % N];
+      t.im[a][kk] = r.im[(a * kk) % N];
+    }
+  return t;
+}
+constexpr CombTable<3, 24> k_comb24 = make_comb<3, 24>(k_roots24);
+constexpr CombTable<9, 36> k_comb36 = make_comb<9, 36>(k_roots36);
+constexpr CombTable<3, 48> k_comb48 = make_comb<3, 48>(k_roots48);
+constexpr CombTable<3, 96> k_comb96 = make_comb<3, 96>(k_roots96);
+__constant__ CombTable<3, 24> c_comb24 = k_comb24;
+__constant__ CombTable<9, 36> c_comb36 = k_comb36;
+__constant__ CombTable<3, 48> c_comb48 = k_comb48;
+__constant__ CombTable<3, 96> c_comb96 = k_comb96;
+
+template <int N>
+__device__ __forceinline__ float2 comb(int a, int kk) {
+  static_assert(N == 24 || N == 36 || N == 48 || N == 96, "no combination table for this length");
+  if constexpr (N == 24) return make_float2(c_comb24.re[a][kk], c_comb24.im[a][kk]);
+  if constexpr (N == 36) return make_float2(c_comb36.re[a][kk], c_comb36.im[a][kk]);
+  if constexpr (N == 48) return make_float2(c_comb48.re[a][kk], c_comb48.im[a][kk]);
+  if constexpr (N == 96) return make_float2(c_comb96.re[a][kk], c_comb96.im[a][kk]);
+}
+
+// e^{2 pi i m / N}, 0 <= m < N
+template <int N>
+__device__ __forceinline__ float2 root(int m) {
+  static_assert(N == 24 || N == 36 || N == 48 || N == 96, "no root table for this length");
+  if constexpr (N == 24) return make_float2(c_roots24.re[m], c_roots24.im[m]);
+  if constexpr (N == 36) return make_float2(c_roots36.re[m], c_roots36.im[m]);
+  if constexpr (N == 48) return make_float2(c_roots48.re[m], c_roots48.im[m]);
+  if constexpr (N == 96) return make_float2(c_roots96.re[m], c_roots96.im[m]);
+}
+
+// in-place Q-point transform with e^{+2 pi i/Q}, twiddles from the N-th roots (Q | N)
+template <int Q, int N>
+__device__ __forceinline__ void fft_reg(float2 (&x)[Q]) {
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int j = bitrev<Q>(i);
@@ -244,6 +347,7 @@ __device__ __forceinline__ void fft_reg(float2 (&x)[Q], const float2* __restrict
   }
   constexpr int LOG2Q = (Q >= 32) ? 5 : (Q >= 16) ? 4 : (Q >= 8) ? 3 : (Q >= 4) ? 2 : 1;
   static_assert((1 << LOG2Q) == Q, "Q must be a power of two <= 32");
+  static_assert(N % Q == 0, "Q must divide N");
   // stage loop with an additive counter so that it unrolls completely and x stays in registers
 #pragma unroll
   for (int stage = 0; stage < LOG2Q; ++stage) {
@@ -259,7 +363,7 @@ __device__ __forceinline__ void fft_reg(float2 (&x)[Q], const float2* __restrict
         } else if (4 * e == Q) {           // multiply by i
           v = make_float2(-v.y, v.x);
         } else {
-          v = cmul(v, tw[e]);
+          v = cmul(v, root<N>(e * (N / Q)));
         }
         x[i + k] = make_float2(u.x + v.x, u.y + v.y);
         x[i + k + len / 2] = make_float2(u.x - v.x, u.y - v.y);
@@ -271,24 +375,38 @@ __device__ __forceinline__ void fft_reg(float2 (&x)[Q], const float2* __restrict
 // acc[kk] = sum over the P sub-sequences of one length-n line, for every kk < NK
 // (the caller uses the first nk; computing all NK avoids a predicate per output)
 template <int P, int Q, int NK, typename Load>
-__device__ __forceinline__ void line_transform(Load load, const float2* __restrict__ ow,
-                                               const float2* __restrict__ tw, float2 (&acc)[NK]) {
+__device__ __forceinline__ void line_transform(Load load, float2 (&acc)[NK]) {
+  constexpr int n = P * Q;
   {
     float2 x[Q];
 #pragma unroll
     for (int b = 0; b < Q; ++b) x[b] = load(P * b);
-    fft_reg<Q>(x, tw);
+    fft_reg<Q, n>(x);
 #pragma unroll
     for (int kk = 0; kk < NK; ++kk) acc[kk] = x[kk % Q];
   }
+  if constexpr (P <= 3 && Q <= 16) {
+    // unrolled: every twiddle index is a compile-time constant
+#pragma unroll
+    for (int a = 1; a < P; ++a) {
+      float2 x[Q];
+#pragma unroll
+      for (int b = 0; b < Q; ++b) x[b] = load(a + P * b);
+      fft_reg<Q, n>(x);
+#pragma unroll
+      for (int kk = 0; kk < NK; ++kk) cfma(acc[kk], x[kk % Q], root<n>((a * kk) % n));
+    }
+  } else {
+    // long or many sub-transforms: one at a time (registers), factors by row a of the table
 #pragma unroll 1
-  for (int a = 1; a < P; ++a) {
-    float2 x[Q];
+    for (int a = 1; a < P; ++a) {
+      float2 x[Q];
 #pragma unroll
-    for (int b = 0; b < Q; ++b) x[b] = load(a + P * b);
-    fft_reg<Q>(x, tw);
+      for (int b = 0; b < Q; ++b) x[b] = load(a + P * b);
+      fft_reg<Q, n>(x);
 #pragma unroll
-    for (int kk = 0; kk < NK; ++kk) cfma(acc[kk], x[kk % Q], ow[a * NKMAX + kk]);
+      for (int kk = 0; kk < NK; ++kk) cfma(acc[kk], x[kk % Q], comb<n>(a, kk));
+    }
   }
 }
 
@@ -297,7 +415,7 @@ __global__ void __launch_bounds__(192, (TV * NCB >= 4) ? 2 : 1)
 k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ v_idx, int v0, int nv,
                   const float2* __restrict__ psi_c, const int32_t* __restrict__ c_idx, int c0, int nc, int c_per_cta,
                   int nk2, int nk3, int nk2p, int nk3p, const float2* __restrict__ T2, const float2* __restrict__ T3,
-                  const float2* __restrict__ Tn, float2* __restrict__ D) {
+                  float2* __restrict__ D) {
   constexpr int n = P * Q;
   constexpr int ld = n | 1;
   constexpr int NP = NCB * TV;                               // pairs per iteration
@@ -306,8 +424,6 @@ k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
   float2* Uv = reinterpret_cast<float2*>(smem_raw);          // [TV][n][ld]
   float2* Uc = Uv + TV * n * ld;                             // [NCB][n][ld]
   float2* X = Uc + NCB * n * ld;                             // [NP][n][ldx]
-  float2* ow = X + NP * n * ldx;                             // [P][NKMAX] e^{2 pi i a kk/n}
-  float2* tw = ow + P * NKMAX;                               // [Q/2]      e^{2 pi i j/Q}
   const int i1 = blockIdx.x;
   const int jv0 = blockIdx.y * TV;
   const int jc_begin = blockIdx.z * c_per_cta;
@@ -317,11 +433,6 @@ k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
   constexpr int plane = n * n;
   const int64_t box = (int64_t)nk2 * nk3;
 
-  for (int e = threadIdx.x; e < P * NKMAX; e += blockDim.x) {
-    const int a = e / NKMAX, kk = e - a * NKMAX;
-    ow[e] = Tn[(a * kk) % n];
-  }
-  for (int e = threadIdx.x; e < Q / 2; e += blockDim.x) tw[e] = Tn[e * P];
   for (int j = 0; j < TV; ++j) {
     const int jv = jv0 + j;
     const bool ok = jv < nv;
@@ -372,7 +483,7 @@ k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
       const float2* uv = Uv + (j * n + i2) * ld;
       const float2* uc = Uc + (cb * n + i2) * ld;
       float2 acc[NK];
-      line_transform<P, Q, NK>([&](int i3) { return cconjmul(uv[i3], uc[i3]); }, ow, tw, acc);
+      line_transform<P, Q, NK>([&](int i3) { return cconjmul(uv[i3], uc[i3]); }, acc);
       float2* xo = X + ((cb * TV + j) * n + i2) * ldx;
 #pragma unroll
       for (int kk = 0; kk < NK; ++kk)
@@ -387,7 +498,7 @@ k_pair_planes_fft(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
       const int jv = jv0 + j, jc = jc0 + cb;
       const float2* xi = X + ((cb * TV + j) * n) * ldx + kk3;
       float2 acc[NK];
-      line_transform<P, Q, NK>([&](int i2) { return xi[i2 * ldx]; }, ow, tw, acc);
+      line_transform<P, Q, NK>([&](int i2) { return xi[i2 * ldx]; }, acc);
       if (jv < nv && jc < jc_end) {
         float2* dst = D + ((int64_t)(jv * nc + jc) * n + i1) * box + kk3;
 #pragma unroll
@@ -404,8 +515,7 @@ template <int P, int Q, int NK, int TV, int NCB>
 size_t fft_planes_smem(int nk3) {
   constexpr int n = P * Q, ld = n | 1;
   const size_t ldx = nk3 | 1;
-  return ((size_t)TV * n * ld + (size_t)NCB * n * ld + (size_t)NCB * TV * n * ldx + P * NKMAX + Q / 2) *
-         sizeof(float2);
+  return ((size_t)TV * n * ld + (size_t)NCB * n * ld + (size_t)NCB * TV * n * ldx) * sizeof(float2);
 }
 
 template <int P, int Q, int NK, int TV, int NCB>
@@ -421,7 +531,7 @@ cudaError_t launch_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void
   while (cpc > NCB && (int64_t)p->n1 * vt * ((nc + cpc - 1) / cpc) < 4 * 152) cpc >>= 1;
   dim3 grid(p->n1, vt, (nc + cpc - 1) / cpc);
   kern<<<grid, 192, sm, st>>>((const float2*)psi_v, v_idx, v0, nv, (const float2*)psi_c, c_idx, c0, nc, cpc, s.nk2,
-                              s.nk3, s.nk2p, s.nk3p, s.T2f, s.T3f, p->Tnf, (float2*)D);
+                              s.nk3, s.nk2p, s.nk3p, s.T2f, s.T3f, (float2*)D);
   return cudaGetLastError();
 }
 
@@ -460,16 +570,9 @@ __global__ void __launch_bounds__(kThreads)
 k_pair_gather_fft(const float2* __restrict__ D, int nc, int64_t row0, int64_t ldv, int64_t box, int nG,
                   int ncol, int64_t n_items, const int* __restrict__ col_off, const int* __restrict__ col_start,
                   const int* __restrict__ ent_k1, const int* __restrict__ ent_j, const float2* __restrict__ T1,
-                  int nk1, const float2* __restrict__ Tn, float scale, float2* __restrict__ M) {
+                  int nk1, float scale, float2* __restrict__ M) {
   constexpr int n = P * Q;
-  __shared__ float2 ow[P * NKMAX];   // e^{2 pi i a kk/n}
-  __shared__ float2 tw[Q / 2];       // e^{2 pi i j/Q}
   __shared__ float2 sh[n];           // e^{2 pi i k1min i1/n}
-  for (int e = threadIdx.x; e < P * NKMAX; e += blockDim.x) {
-    const int a = e / NKMAX, kk = e - a * NKMAX;
-    ow[e] = Tn[(a * kk) % n];
-  }
-  for (int e = threadIdx.x; e < Q / 2; e += blockDim.x) tw[e] = Tn[e * P];
   for (int e = threadIdx.x; e < n; e += blockDim.x) sh[e] = T1[(size_t)e * nk1];
   __syncthreads();
   const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -478,7 +581,7 @@ k_pair_gather_fft(const float2* __restrict__ D, int nc, int64_t row0, int64_t ld
   const int jv = pl / nc, jc = pl - jv * nc;
   const float2* Dp = D + (int64_t)pl * n * box + col_off[c];
   float2 acc[NK];
-  line_transform<P, Q, NK>([&](int i1) { return cmul(Dp[(int64_t)i1 * box], sh[i1]); }, ow, tw, acc);
+  line_transform<P, Q, NK>([&](int i1) { return cmul(Dp[(int64_t)i1 * box], sh[i1]); }, acc);
   float2* out = M + (row0 + (int64_t)jv * ldv + jc) * nG;
   int t = col_start[c];
   const int t_end = col_start[c + 1];
@@ -502,7 +605,7 @@ cudaError_t launch_gather_fft(const chi0_plan_s* p, const SphereQ& s, const void
   if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
   k_pair_gather_fft<P, Q, NK><<<(unsigned)blocks, kThreads, 0, st>>>(
       (const float2*)D, nc, row0, ldv, (int64_t)s.nk2 * s.nk3, s.nG, s.ncol, items, s.col_off, s.col_start,
-      s.ent_k1, s.ent_j, s.T1f, s.nk1, p->Tnf, (float)(1.0 / (double)p->nr), (float2*)M);
+      s.ent_k1, s.ent_j, s.T1f, s.nk1, (float)(1.0 / (double)p->nr), (float2*)M);
   return cudaGetLastError();
 }
 

@@ -103,7 +103,6 @@ void free_plan(chi0_plan_s* p) {
   cudaFree(w.T3d); cudaFree(w.T3f);
   cudaFree(p->d_omega); cudaFree(p->d_D); cudaFree(p->d_M); cudaFree(p->d_f);
   cudaFree(p->d_pack); cudaFree(p->d_status); cudaFree(p->d_bwd); cudaFree(p->d_inv);
-  cudaFree(p->Tnd); cudaFree(p->Tnf);
   for (size_t i = 1; i < p->bq_M.size(); ++i) {
     cudaFree(p->bq_M[i]);
     cudaFree(p->bq_f[i]);
@@ -348,11 +347,6 @@ chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* d) {
   }
   st = analyse_wfn(p, d->gw, d->npw);
   if (st != CHI0_OK) return bail(st);
-  {
-    // Tn[e] = exp(2 pi i e / n3): twiddles of the register FFTs along the grid axes
-    cudaError_t e = make_table(p->n3, 1, 1, 1, &p->Tnd, &p->Tnf);
-    if (e != cudaSuccess) { p->err = cudaGetErrorString(e); return bail(CHI0_ERR_CUDA); }
-  }
 
   // workspace
   const size_t cb = chi0::cbytes(p);
