@@ -56,3 +56,19 @@ def test_pairs_fp32_scattered_g_list(name, n_g):
     err = np.max(np.abs(M - ref)) / np.max(np.abs(ref))
     print(f"\n{name}: scattered G list of {n_g}, max abs err / max |M| {err:.2e}")
     assert err < 2e-6
+
+
+@pytest.mark.parametrize("name,nb", [("c1", 7), ("c2", 5), ("c4", 4), ("c5", 2)])
+def test_wfn_to_grid_fp32_all_grids(name, nb):
+    """Split plans put the wavefunctions on the grid in FP32; element by element
+    against the FP64 oracle on every workload grid, bar 1e-6 of the largest value."""
+    from paper_1601_06767_gb300 import Chi0Plan
+    prob = make_problem(name)
+    cc = prob.coeff_c(np.arange(nb))
+    ref = wfn_to_grid(cc, prob.gw, prob.n)
+    with Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision="bf16", gw=prob.gw) as plan:
+        psi = plan.wfn_to_grid(_dev(cc)).cpu().numpy()
+    err = np.max(np.abs(psi.reshape(ref.shape) - ref)) / np.max(np.abs(ref))
+    print(f"\n{name}: n={prob.n} wavefunctions max abs err / max |psi| {err:.2e}")
+    assert err < 1e-6
+
