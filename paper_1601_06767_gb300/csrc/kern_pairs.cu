@@ -3,8 +3,10 @@
 // pruned forward transforms along i3 and i2 inside the plane (stages 1-2),
 // then the transform along i1 evaluated only on the G sphere (stage 3).
 //
-// All transforms are direct sums with exact twiddle tables, restricted to the
-// frequencies the sphere needs; the three stages together equal
+// FP32 plans on cubic grids of 24, 36, 48 or 96 points transform with
+// register FFTs (length-Q FFTs of P interleaved sub-sequences); FP64 plans and
+// other grids use direct sums with exact twiddle tables.  Both are restricted
+// to the frequencies the sphere needs, and the three stages together equal
 // M(G) = (1/N_r) sum_r conj(psi_v(r)) psi_c(r) exp(2 pi i G.r).
 #include <algorithm>
 #include <type_traits>
