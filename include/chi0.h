@@ -139,7 +139,14 @@ chi0_status chi0_accumulate(chi0_plan plan, int iq, const void* M, int n_v, int 
 /* The whole hot path for one q-point: for blocks of conduction columns,
  * chi0_pairs into plan workspace followed by chi0_accumulate, so M is never
  * held for all pairs at once.  Arguments as for chi0_pairs/chi0_accumulate
- * (valence rows 0..n_v-1 of psi_v; conduction rows c_idx[ic] of psi_c). */
+ * (valence rows 0..n_v-1 of psi_v; conduction rows c_idx[ic] of psi_c).
+ * Split plans with more than one block pipeline the blocks: the pair stage and
+ * packing of block k+1 run on a low-priority plan-owned stream beside the
+ * contraction of block k on a high-priority one, with a second workspace set
+ * allocated on the first such call (chi0_workspace_bytes grows by it; if it
+ * cannot be had the build stays serial).  Both streams are joined back into
+ * `stream` before the call returns, so ordering on `stream` is as for a
+ * serial build. */
 chi0_status chi0_build(chi0_plan plan, int iq, const void* psi_v, int n_v, const double* E_v,
                        const void* psi_c, const int32_t* c_idx, int n_c,
                        const double* E_col, const double* w_col, void* chi0, void* stream);

@@ -83,6 +83,15 @@ struct chi0_plan_s {
   int64_t graph_family[CHI0_K_COUNT] = {};   // kernel launches per family inside the captured graph
   double* d_bwd = nullptr;   // adjoint work: per-pair grad dE and per-tile partial sums
   void* d_inv = nullptr;     // dielectric-inverse workspace (grown on demand)
+  // pipelined chi0_build (split plans): the pair stage and packing of block k+1 run on a
+  // low-priority stream beside the contraction of block k on a high-priority one, with a
+  // second M / factor / split-plane set (allocated on first use)
+  cudaStream_t pipe_lo = nullptr, pipe_hi = nullptr;
+  cudaEvent_t pipe_ev[7] = {};  // fork, packed[2], contracted[2], join lo, join hi
+  void* pipe_M = nullptr;
+  double2* pipe_f = nullptr;
+  void* pipe_pack = nullptr;
+  int pipe_state = 0;           // 0 not set up, 1 ready, -1 unavailable (serial build)
   size_t inv_bytes = 0;
   size_t ws_bytes = 0;
   std::string err;
@@ -140,8 +149,10 @@ struct TcJob {
   double2* chi;           // [n_freq][nG][nG]
   void* pack;             // split-plane workspace (tc_pack_bytes)
 };
+// mode 0: pack and contract; 1: pack only (absmax, scales, split planes into jobs[].pack);
+// 2: contract only, from planes an earlier mode-1 call packed with the same K and shapes
 cudaError_t launch_contract_tc_batch(chi0_plan_s* p, const TcJob* jobs, int n_jobs, int64_t K, cudaStream_t s,
-                                     std::string* why);
+                                     std::string* why, int mode = 0);
 // split-precision tensor-core path for K pairs of M (float2) with factors f
 cudaError_t launch_contract_tc(chi0_plan_s* p, int nG, const float2* M, int64_t K,
                                const double2* f, double2* chi, cudaStream_t s, std::string* why);

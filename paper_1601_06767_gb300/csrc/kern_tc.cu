@@ -898,7 +898,7 @@ static cudaError_t pack_one(chi0_plan_s* p, int nG, const float2* M, int64_t K, 
 
 template <bool BF16, int NT>
 static cudaError_t run_tc(chi0_plan_s* p, const TcJob* jobs, int n_jobs, int64_t K, cudaStream_t s,
-                          std::string* why) {
+                          std::string* why, int mode) {
   const int Kp = (int)((K + 63) / 64 * 64);
   TcBatch* P = new TcBatch();
   memset(P, 0, sizeof(TcBatch));
@@ -908,8 +908,11 @@ static cudaError_t run_tc(chi0_plan_s* p, const TcJob* jobs, int n_jobs, int64_t
     const TcJob& jb = jobs[j];
     const int nGp = round_up_i(jb.nG, pair ? 2 * BM : BM);
     PackWs w = pack_ws(p, jb.pack, nGp, Kp);
-    cudaError_t e = pack_one<BF16, NT>(p, jb.nG, jb.M, K, jb.f, w, nGp, Kp, s);
-    if (e != cudaSuccess) { delete P; return e; }
+    if (mode != 2) {
+      cudaError_t e = pack_one<BF16, NT>(p, jb.nG, jb.M, K, jb.f, w, nGp, Kp, s);
+      if (e != cudaSuccess) { delete P; return e; }
+      if (mode == 1) continue;
+    }
     if (!encode_planes(&P->tmB[j], w.Bp, BF16, Kp, nGp, 2 * NT, why, pair ? BN / 2 : BN) ||
         !encode_planes(&P->tmA[j], w.Ap, BF16, Kp, nGp, 2 * NT * n_parts(p) * p->n_freq, why, BM)) {
       delete P;
@@ -926,6 +929,10 @@ static cudaError_t run_tc(chi0_plan_s* p, const TcJob* jobs, int n_jobs, int64_t
     P->tpf[j] = p->tc_herm ? (int64_t)(TN / TM) * TM * (TM + 1) / 2 : (int64_t)TM * TN;
     P->item0[j] = items;
     items += P->tpf[j] * p->n_freq;
+  }
+  if (mode == 1) {
+    delete P;
+    return cudaSuccess;
   }
   P->n_parts = n_parts(p);
   P->rr = pair ? 2 : 1;
@@ -961,7 +968,7 @@ static cudaError_t run_tc(chi0_plan_s* p, const TcJob* jobs, int n_jobs, int64_t
 }
 
 cudaError_t launch_contract_tc_batch(chi0_plan_s* p, const TcJob* jobs, int n_jobs, int64_t K, cudaStream_t s,
-                                     std::string* why) {
+                                     std::string* why, int mode) {
   if (K <= 0 || n_jobs <= 0) return cudaSuccess;
   if (n_jobs > MAXQ) {
     if (why) *why = "at most 16 q-points per batch";
@@ -970,11 +977,11 @@ cudaError_t launch_contract_tc_batch(chi0_plan_s* p, const TcJob* jobs, int n_jo
   if (!resolve_encoder(why)) return cudaErrorNotSupported;
   const bool bf16 = p->prec == CHI0_SPLIT_BF16;
   if (n_terms(p) == 3) {
-    if (bf16) return run_tc<true, 3>(p, jobs, n_jobs, K, s, why);
-    return run_tc<false, 3>(p, jobs, n_jobs, K, s, why);
+    if (bf16) return run_tc<true, 3>(p, jobs, n_jobs, K, s, why, mode);
+    return run_tc<false, 3>(p, jobs, n_jobs, K, s, why, mode);
   }
-  if (bf16) return run_tc<true, 2>(p, jobs, n_jobs, K, s, why);
-  return run_tc<false, 2>(p, jobs, n_jobs, K, s, why);
+  if (bf16) return run_tc<true, 2>(p, jobs, n_jobs, K, s, why, mode);
+  return run_tc<false, 2>(p, jobs, n_jobs, K, s, why, mode);
 }
 
 cudaError_t launch_contract_tc(chi0_plan_s* p, int nG, const float2* M, int64_t K, const double2* f, double2* chi,

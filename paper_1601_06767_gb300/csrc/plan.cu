@@ -110,6 +110,11 @@ void free_plan(chi0_plan_s* p) {
   }
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  cudaFree(p->pipe_M); cudaFree(p->pipe_f); cudaFree(p->pipe_pack);
+  for (cudaEvent_t e : p->pipe_ev)
+    if (e) cudaEventDestroy(e);
+  if (p->pipe_lo) cudaStreamDestroy(p->pipe_lo);
+  if (p->pipe_hi) cudaStreamDestroy(p->pipe_hi);
 }
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -740,6 +745,93 @@ chi0_status chi0_accumulate(chi0_plan p, int iq, const void* M, int n_v, int n_c
   return accumulate_impl(p, iq, M, n_v, n_c, E_v, E_col, w_col, chi0, (cudaStream_t)stream);
 }
 
+// Streams, events and the second workspace set of the pipelined build; on any
+// failure the plan falls back to the serial build for good (pipe_state -1).
+static bool pipe_setup(chi0_plan p) {
+  if (p->pipe_state != 0) return p->pipe_state > 0;
+  p->pipe_state = -1;
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&p->pipe_lo, cudaStreamNonBlocking, least) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&p->pipe_hi, cudaStreamNonBlocking, greatest) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  for (cudaEvent_t& e : p->pipe_ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+  const size_t bytes_M = (size_t)p->max_pairs * p->max_nG * chi0::cbytes(p);
+  const size_t bytes_f = (size_t)p->n_freq * p->max_pairs * sizeof(double2);
+  if (cudaMalloc(&p->pipe_M, bytes_M) != cudaSuccess || cudaMalloc((void**)&p->pipe_f, bytes_f) != cudaSuccess ||
+      cudaMalloc(&p->pipe_pack, p->pack_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(p->pipe_M); cudaFree(p->pipe_f); cudaFree(p->pipe_pack);
+    p->pipe_M = nullptr; p->pipe_f = nullptr; p->pipe_pack = nullptr;
+    return false;
+  }
+  p->ws_bytes += bytes_M + bytes_f + p->pack_bytes;
+  p->pipe_state = 1;
+  return true;
+}
+
+// Split-plan build with two workspace sets: block k's pair stage, factors and
+// split planes go on the low-priority stream, its contraction on the
+// high-priority one, so the next block's pair stage takes the SMs the
+// contraction's last wave leaves idle and never delays a contraction.  Events
+// order: packing into set b after the contraction that read set b (two blocks
+// earlier), and each contraction after its own packing.  Both streams join the
+// caller's stream at the end, also after an error.
+static chi0_status build_pipelined(chi0_plan p, int iq, const void* psi_v, int n_v, const double* E_v,
+                                   const void* psi_c, const int32_t* c_idx, int n_c, const double* E_col,
+                                   const double* w_col, void* chi0, cudaStream_t s, int cb) {
+  cudaStream_t lo = p->pipe_lo, hi = p->pipe_hi;
+  cudaEvent_t* ev = p->pipe_ev;
+  const int nG = p->q[iq].nG;
+  chi0_status st = CHI0_OK;
+  cudaError_t e = cudaEventRecord(ev[0], s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(lo, ev[0], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(hi, ev[0], 0);
+  std::string why;
+  int k = 0;
+  for (int c0 = 0; c0 < n_c && e == cudaSuccess && st == CHI0_OK; c0 += cb, ++k) {
+    const int nc = std::min(cb, n_c - c0);
+    const int b = k & 1;
+    void* M = b ? p->pipe_M : p->d_M;
+    double2* f = b ? p->pipe_f : p->d_f;
+    void* pk = b ? p->pipe_pack : p->d_pack;
+    const int64_t K = (int64_t)n_v * nc;
+    st = pairs_impl(p, iq, psi_v, nullptr, n_v, psi_c, c_idx, c0, nc, M, nc, lo);
+    if (st != CHI0_OK) break;
+    {
+      chi0::ProfScope ps(p, CHI0_K_WEIGHTS, lo, 1);
+      e = chi0::launch_weights(p, 0, K, nc, E_v, E_col + c0, w_col ? w_col + c0 : nullptr, f, lo);
+    }
+    if (e == cudaSuccess && k >= 2) e = cudaStreamWaitEvent(lo, ev[3 + b], 0);
+    if (e == cudaSuccess) {
+      chi0::TcJob jb{nG, (const float2*)M, f, nullptr, pk};
+      e = chi0::launch_contract_tc_batch(p, &jb, 1, K, lo, &why, 1);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1 + b], lo);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hi, ev[1 + b], 0);
+    if (e == cudaSuccess) {
+      chi0::TcJob jb{nG, nullptr, nullptr, (double2*)chi0, pk};
+      e = chi0::launch_contract_tc_batch(p, &jb, 1, K, hi, &why, 2);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3 + b], hi);
+  }
+  // join, whatever happened above
+  cudaEventRecord(ev[5], lo);
+  cudaStreamWaitEvent(s, ev[5], 0);
+  cudaEventRecord(ev[6], hi);
+  cudaStreamWaitEvent(s, ev[6], 0);
+  if (st != CHI0_OK) return st;
+  if (e != cudaSuccess)
+    return fail(p, CHI0_ERR_CUDA, "pipelined build: " + why + " " + cudaGetErrorString(e));
+  return CHI0_OK;
+}
+
 chi0_status chi0_build(chi0_plan p, int iq, const void* psi_v, int n_v, const double* E_v,
                        const void* psi_c, const int32_t* c_idx, int n_c, const double* E_col,
                        const double* w_col, void* chi0, void* stream) {
@@ -754,6 +846,8 @@ chi0_status chi0_build(chi0_plan p, int iq, const void* psi_v, int n_v, const do
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t blk = p->block_pairs > 0 ? std::min(p->block_pairs, p->max_pairs) : p->max_pairs;
   const int cb = (int)std::max<int64_t>(1, blk / n_v);
+  if (chi0::is_split(p) && n_c > cb && pipe_setup(p))
+    return build_pipelined(p, iq, psi_v, n_v, E_v, psi_c, c_idx, n_c, E_col, w_col, chi0, s, cb);
   for (int c0 = 0; c0 < n_c; c0 += cb) {
     int nc = std::min(cb, n_c - c0);
     st = pairs_impl(p, iq, psi_v, nullptr, n_v, psi_c, c_idx, c0, nc, p->d_M, nc, s);
