@@ -846,7 +846,14 @@ chi0_status chi0_build(chi0_plan p, int iq, const void* psi_v, int n_v, const do
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t blk = p->block_pairs > 0 ? std::min(p->block_pairs, p->max_pairs) : p->max_pairs;
   const int cb = (int)std::max<int64_t>(1, blk / n_v);
-  if (chi0::is_split(p) && n_c > cb && pipe_setup(p))
+  // the pipelined build sets up streams and buffers on first use, which a stream
+  // capture does not allow: a captured build stays serial
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    cap = cudaStreamCaptureStatusActive;
+  }
+  if (chi0::is_split(p) && n_c > cb && cap == cudaStreamCaptureStatusNone && pipe_setup(p))
     return build_pipelined(p, iq, psi_v, n_v, E_v, psi_c, c_idx, n_c, E_col, w_col, chi0, s, cb);
   for (int c0 = 0; c0 < n_c; c0 += cb) {
     int nc = std::min(cb, n_c - c0);
