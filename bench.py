@@ -708,6 +708,7 @@ def run_case(args):
     """Small fixed cases for ncu captures (no JSON line): 'contract' = two
     accumulate calls of 8192 pairs on the 2500-vector sphere with 9
     frequencies; 'pairs' = two pair-element calls of 128 x 64 pairs on 48^3;
+    'wfn' = two grid transforms of 512 conduction bands on 48^3;
     'eps' = two dielectric inverses of 9 matrices of the 2500-vector sphere;
     'coh' = plasmon-pole parameters and COH sums (4 targets x 663 bands)."""
     import torch
@@ -723,6 +724,13 @@ def run_case(args):
                       gw=prob.gw, n_products=args.n_products, hermitian=herm) as plan:
         if args.case == "contract" and not args.no_tune:
             plan.autotune(0)          # the variant the benchmark runs
+        if args.case == "wfn":
+            cc = torch.from_numpy(prob.coeff_c(np.arange(512))).cuda()
+            psi = torch.empty((512,) + plan.n, dtype=plan.cdtype, device="cuda")
+            for _ in range(2):
+                plan.wfn_to_grid(cc, out=psi)
+            plan.sync_status()
+            return 0
         if args.case == "coh":
             # plasmon-pole parameters and the COH sums for 4 targets x 663 bands on the 2500-vector sphere
             nb = 663
@@ -1053,7 +1061,7 @@ def main(argv=None):
     ap.add_argument("--no-eps", action="store_true", help="skip the dielectric-matrix measurement")
     ap.add_argument("--no-quad", action="store_true", help="skip the quadrature variants of Eq. 3")
     ap.add_argument("--no-coh", action="store_true", help="skip the COH self-energy measurement")
-    ap.add_argument("--case", choices=["contract", "pairs", "eps", "coh", "c3", "c4", "c5"], default=None,
+    ap.add_argument("--case", choices=["contract", "pairs", "wfn", "eps", "coh", "c3", "c4", "c5"], default=None,
                     help="run a small fixed case for profiling (contract, pairs) or the 256-atom-sized "
                          "measurement (c5) instead of the benchmark")
     ap.add_argument("--c5-frac", type=float, default=1.0, help="fraction of conduction bands timed in --case c5")

@@ -65,6 +65,110 @@ k_wfn_to_grid(const double2* __restrict__ coeff, int npw, int n1, int n2, int n3
 }
 
 // ---------------------------------------------------------------------------
+// The same three stages in FP32 for WPL planes per CTA, with the tables in
+// shared memory and every load reused: stage A applies each coefficient to the
+// WPL planes, stages B and C give each thread 4 consecutive outputs (i2 or i3)
+// that share the input value and read their 4 twiddles as two 16-byte loads;
+// stage C writes 4 consecutive i3 (32 bytes) per thread.
+// Shared memory: A[WPL][nw2][nw3], B[WPL][n2][nw3], T2s[nw2][n2] (transposed),
+// T3s[nw3][n3], T1s[WPL][nw1].
+// ---------------------------------------------------------------------------
+constexpr int WPL = 4;
+
+size_t wfn_blk_smem(const chi0_plan_s* p) {
+  const WfnSphere& w = p->w;
+  return ((size_t)WPL * w.nw2 * w.nw3 + (size_t)WPL * p->n2 * w.nw3 + (size_t)w.nw2 * p->n2 +
+          (size_t)w.nw3 * p->n3 + (size_t)WPL * w.nw1) * sizeof(float2);
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+k_wfn_to_grid_blk(const double2* __restrict__ coeff, int npw, int n1, int n2, int n3, int nw1, int nw2, int nw3,
+                  const int* __restrict__ col_start, const int* __restrict__ col_pw, const int* __restrict__ col_g1,
+                  const float2* __restrict__ T1, const float2* __restrict__ T2, const float2* __restrict__ T3t,
+                  float2* __restrict__ psi) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int cw = nw2 * nw3;
+  float2* A = reinterpret_cast<float2*>(smem_raw);   // [WPL][cw]
+  float2* B = A + WPL * cw;                          // [WPL][n2][nw3]
+  float2* T2s = B + WPL * n2 * nw3;                  // [nw2][n2]
+  float2* T3s = T2s + nw2 * n2;                      // [nw3][n3]
+  float2* T1s = T3s + nw3 * n3;                      // [WPL][nw1]
+  const int i1_0 = blockIdx.x * WPL;
+  const int npl = min(WPL, n1 - i1_0);
+  const int64_t b = blockIdx.y;
+  const double2* cb = coeff + b * npw;
+  for (int e = threadIdx.x; e < nw2 * n2; e += blockDim.x) {
+    const int g2 = e / n2, i2 = e - g2 * n2;
+    T2s[e] = T2[(size_t)i2 * nw2 + g2];
+  }
+  for (int e = threadIdx.x; e < nw3 * n3; e += blockDim.x) T3s[e] = T3t[e];
+  for (int e = threadIdx.x; e < WPL * nw1; e += blockDim.x) {
+    const int pl = e / nw1, g1 = e - pl * nw1;
+    T1s[e] = pl < npl ? T1[(size_t)(i1_0 + pl) * nw1 + g1] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  // stage A: along g1 for every (g2, g3) column of the sphere, all planes at once
+  for (int c = threadIdx.x; c < cw; c += blockDim.x) {
+    float2 acc[WPL];
+#pragma unroll
+    for (int pl = 0; pl < WPL; ++pl) acc[pl] = make_float2(0.f, 0.f);
+    const int k1 = col_start[c + 1];
+    for (int k = col_start[c]; k < k1; ++k) {
+      const double2 d = cb[col_pw[k]];
+      const float2 v = make_float2((float)d.x, (float)d.y);
+      const int g1 = col_g1[k];
+#pragma unroll
+      for (int pl = 0; pl < WPL; ++pl) cfma(acc[pl], v, T1s[pl * nw1 + g1]);
+    }
+#pragma unroll
+    for (int pl = 0; pl < WPL; ++pl) A[pl * cw + c] = acc[pl];
+  }
+  __syncthreads();
+  // stage B: B[pl][i2][g3] = sum_g2 A[pl][g2][g3] T2(i2, g2), four i2 per thread
+  const int n2q = n2 >> 2;
+  for (int it = threadIdx.x; it < npl * n2q * nw3; it += blockDim.x) {
+    const int g3 = it % nw3, r = it / nw3, q = r % n2q, pl = r / n2q;
+    float2 acc[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] = make_float2(0.f, 0.f);
+    const float2* a = A + pl * cw + g3;
+    for (int g2 = 0; g2 < nw2; ++g2) {
+      const float2 x = a[g2 * nw3];
+      const float4 t01 = *reinterpret_cast<const float4*>(T2s + g2 * n2 + 4 * q);
+      const float4 t23 = *reinterpret_cast<const float4*>(T2s + g2 * n2 + 4 * q + 2);
+      cfma(acc[0], x, make_float2(t01.x, t01.y));
+      cfma(acc[1], x, make_float2(t01.z, t01.w));
+      cfma(acc[2], x, make_float2(t23.x, t23.y));
+      cfma(acc[3], x, make_float2(t23.z, t23.w));
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) B[(pl * n2 + 4 * q + j) * nw3 + g3] = acc[j];
+  }
+  __syncthreads();
+  // stage C: psi[i1][i2][i3] = sum_g3 B[pl][i2][g3] T3(g3, i3), four i3 per thread
+  const int n3q = n3 >> 2;
+  for (int it = threadIdx.x; it < npl * n2 * n3q; it += blockDim.x) {
+    const int q = it % n3q, r = it / n3q, i2 = r % n2, pl = r / n2;
+    float2 acc[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] = make_float2(0.f, 0.f);
+    const float2* brow = B + (pl * n2 + i2) * nw3;
+    for (int g3 = 0; g3 < nw3; ++g3) {
+      const float2 x = brow[g3];
+      const float4 t01 = *reinterpret_cast<const float4*>(T3s + g3 * n3 + 4 * q);
+      const float4 t23 = *reinterpret_cast<const float4*>(T3s + g3 * n3 + 4 * q + 2);
+      cfma(acc[0], x, make_float2(t01.x, t01.y));
+      cfma(acc[1], x, make_float2(t01.z, t01.w));
+      cfma(acc[2], x, make_float2(t23.x, t23.y));
+      cfma(acc[3], x, make_float2(t23.z, t23.w));
+    }
+    float4* out = reinterpret_cast<float4*>(psi + (((size_t)b * n1 + i1_0 + pl) * n2 + i2) * n3 + 4 * q);
+    out[0] = make_float4(acc[0].x, acc[0].y, acc[1].x, acc[1].y);
+    out[1] = make_float4(acc[2].x, acc[2].y, acc[3].x, acc[3].y);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Stages 1+2 for one plane i1, a tile of TV valence bands and a run of
 // conduction bands.  Shared memory: Uv[TV][n2][ld3], Uc[n2][ld3], X[TV][n2][nk3p].
 //   stage 1: X_j(i2,k3) = sum_i3 conj(u_vj(i1,i2,i3)) u_c(i1,i2,i3) e^{2 pi i k3 i3/n3}
@@ -799,6 +903,17 @@ cudaError_t launch_wfn_to_grid(const chi0_plan_s* p, const double2* coeff, int n
   const WfnSphere& w = p->w;
   dim3 grid(p->n1, nb);
   if (is_split(p)) {
+    const size_t smb = wfn_blk_smem(p);
+    // 16-byte stores: psi must be 16-byte aligned (every band plane then is, n3 % 4 == 0)
+    if (p->n2 % 4 == 0 && p->n3 % 4 == 0 && smb <= (size_t)110 * 1024 && (reinterpret_cast<uintptr_t>(psi) & 15) == 0) {
+      cudaError_t e = cudaFuncSetAttribute(k_wfn_to_grid_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+      if (e != cudaSuccess) return e;
+      dim3 gridb((p->n1 + WPL - 1) / WPL, nb);
+      k_wfn_to_grid_blk<<<gridb, kThreads, smb, s>>>(coeff, w.npw, p->n1, p->n2, p->n3, w.nw1, w.nw2, w.nw3,
+                                                     w.col_start, w.col_pw, w.col_g1, w.T1f, w.T2f, w.T3f,
+                                                     (float2*)psi);
+      return cudaGetLastError();
+    }
     size_t sm = ((size_t)w.nw2 * w.nw3 + (size_t)p->n2 * w.nw3) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_wfn_to_grid<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
