@@ -186,7 +186,7 @@ def h2_products(Ev, Ec, omega, delta, n_prod):
 
 def coh_study(pkg, prob, plan, chi, psi_v, psi_c, dev, n_t=4):
     """Diagonal COH self-energy of the n_t lowest conduction bands with the
-    plasmon-pole model fitted to this build's static eps^-1 (plain form, FP32
+    plasmon-pole model fitted to the static eps^-1 of the benchmark's chi0 (plain form, FP32
     inverse of the split plan): pair elements <t|e^{iG.r}|b> for the valence
     bands and every conduction band (full) or the Eq. 3/4 columns
     (accelerated), then chi0_sigma_coh.  Times are CUDA events around the pair
