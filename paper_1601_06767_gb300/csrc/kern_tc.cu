@@ -250,9 +250,8 @@ struct Barriers {
 // to one stage and ordered smallest-first: every term product t_i t_j with
 // i + j > 0 goes in while the accumulator is still small, and the t0 t0
 // products (the only large ones) come last.
-template <bool BF16, int NT, bool PAIR = false>
-__device__ __forceinline__ void issue_stage(const unsigned char* st, uint32_t d_re, uint32_t d_im, bool first,
-                                            int n_products) {
+template <bool BF16, int NT, bool PAIR, int NPROD>
+__device__ __forceinline__ void issue_stage_np(const unsigned char* st, uint32_t d_re, uint32_t d_im, bool first) {
   constexpr int P = 2 * NT;
   // in a CTA pair each CTA holds 128 rows of A and 64 rows of B; the MMA spans 256 rows
   constexpr int B_BYTES = PAIR ? TILE_BYTES / 2 : TILE_BYTES;
@@ -271,7 +270,7 @@ __device__ __forceinline__ void issue_stage(const unsigned char* st, uint32_t d_
         const int j = order - i;
         if (j < 0 || j >= NT) continue;
         // 3: t0t0, t0t1, t1t0; 4: adds t1t1; 6: all t_i t_j with i + j <= 2
-        const bool keep = (i + j < 2) || (i + j == 2 && (n_products == 6 || (n_products == 4 && i == 1)));
+        const bool keep = (i + j < 2) || (i + j == 2 && (NPROD == 6 || (NPROD == 4 && i == 1)));
         if (!keep) continue;
         // planes: Re terms 0..NT-1, Im terms NT..2NT-1; K step ks is +32 bytes
         const uint64_t ar = d0 + (uint64_t)i * kTile + (uint64_t)(ks * 2);
@@ -298,6 +297,15 @@ __device__ __forceinline__ void issue_stage(const unsigned char* st, uint32_t d_
       }
     }
   }
+}
+
+// the product count as a compile-time constant: no per-MMA test in the issue loop
+template <bool BF16, int NT, bool PAIR = false>
+__device__ __forceinline__ void issue_stage(const unsigned char* st, uint32_t d_re, uint32_t d_im, bool first,
+                                            int n_products) {
+  if (n_products == 6) issue_stage_np<BF16, NT, PAIR, 6>(st, d_re, d_im, first);
+  else if (n_products == 4) issue_stage_np<BF16, NT, PAIR, 4>(st, d_re, d_im, first);
+  else issue_stage_np<BF16, NT, PAIR, 3>(st, d_re, d_im, first);
 }
 
 // One persistent launch over a list of work items (q-point, frequency, 128x128
@@ -475,15 +483,19 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
       int64_t gs = 0, gc = 0;
+      int slot = 0;
+      uint32_t ph = 0;
       bool ok = true;
       for (int64_t item = blockIdx.x; item < P.total_items && ok; item += gridDim.x) {
         int q, iw, tm, tn;
         decode_item(P, item, q, iw, tm, tn);
         for (int part = 0; part < P.n_parts && ok; ++part) {
           const int np = part_products(P, q, iw, part), ck = part_chain(P, q, iw, part);
-          for (int kc = 0; kc < nK; ++kc, ++gs) {
+          // pos: stage within the accumulation chain; s, ph: ring slot and its phase (counters,
+          // not divisions, on this single issuing thread)
+          for (int kc = 0, pos = 0; kc < nK; ++kc, ++gs) {
             const int buf = (int)(gc & 1);
-            const bool first = (kc % ck) == 0;
+            const bool first = pos == 0;
             if (first) {
               if (!tc::mbar_wait(&bar->tempty[buf], (uint32_t)(((gc >> 1) & 1) ^ 1), status, 1, WAIT_BUDGET_NS)) {
                 ok = false;
@@ -491,19 +503,24 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
               }
               tc::fence_after();
             }
-            const int s = (int)(gs % STAGES);
-            if (!tc::mbar_wait(&bar->full[s], (uint32_t)((gs / STAGES) & 1), status, 1, WAIT_BUDGET_NS)) {
+            const int s = slot;
+            if (!tc::mbar_wait(&bar->full[s], ph, status, 1, WAIT_BUDGET_NS)) {
               ok = false;
               break;
+            }
+            if (++slot == STAGES) {
+              slot = 0;
+              ph ^= 1u;
             }
             tc::fence_after();
             const unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
             const uint32_t d_re = tbase + buf * 256, d_im = d_re + 128;
             issue_stage<BF16, NT>(st, d_re, d_im, first, np);
             tc::mma_commit(&bar->empty[s]);
-            if ((kc % ck) == ck - 1 || kc == nK - 1) {
+            if (++pos == ck || kc == nK - 1) {
               tc::mma_commit(&bar->tfull[buf]);
               ++gc;
+              pos = 0;
             }
           }
         }
@@ -674,15 +691,19 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
     if (lane == 0 && leader) {
       // ---------------- MMA issuer (first CTA of the pair) ----------------
       int64_t gs = 0, gc = 0;
+      int slot = 0;
+      uint32_t ph = 0;
       bool ok = true;
       for (int64_t item = pair; item < P.total_items && ok; item += npairs) {
         int q, iw, tm, tn;
         decode_item(P, item, q, iw, tm, tn);
         for (int part = 0; part < P.n_parts && ok; ++part) {
           const int np = part_products(P, q, iw, part), ck = part_chain(P, q, iw, part);
-          for (int kc = 0; kc < nK; ++kc, ++gs) {
+          // pos: stage within the accumulation chain; s, ph: ring slot and its phase (counters,
+          // not divisions, on this single issuing thread)
+          for (int kc = 0, pos = 0; kc < nK; ++kc, ++gs) {
             const int buf = (int)(gc & 1);
-            const bool first = (kc % ck) == 0;
+            const bool first = pos == 0;
             if (first) {
               if (!tc::mbar_wait(&bar->tempty[buf], (uint32_t)(((gc >> 1) & 1) ^ 1), status, 1, WAIT_BUDGET_NS)) {
                 ok = false;
@@ -690,19 +711,24 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
               }
               tc::fence_after();
             }
-            const int s = (int)(gs % STAGES);
-            if (!tc::mbar_wait(&bar->full[s], (uint32_t)((gs / STAGES) & 1), status, 1, WAIT_BUDGET_NS)) {
+            const int s = slot;
+            if (!tc::mbar_wait(&bar->full[s], ph, status, 1, WAIT_BUDGET_NS)) {
               ok = false;
               break;
+            }
+            if (++slot == STAGES) {
+              slot = 0;
+              ph ^= 1u;
             }
             tc::fence_after();
             const unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
             const uint32_t d_re = tbase + buf * 256, d_im = d_re + 128;
             issue_stage<BF16, NT, true>(st, d_re, d_im, first, np);
             tc::mma_commit_pair(&bar->empty[s], 0x3);
-            if ((kc % ck) == ck - 1 || kc == nK - 1) {
+            if (++pos == ck || kc == nK - 1) {
               tc::mma_commit_pair(&bar->tfull[buf], 0x3);
               ++gc;
+              pos = 0;
             }
           }
         }
