@@ -452,6 +452,8 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
       int64_t gs = 0;
+      int slot = 0;        // ring slot of stage gs and its phase parity (counters, not divisions)
+      uint32_t ph = 0;
       bool ok = true;
       for (int64_t item = blockIdx.x; item < P.total_items && ok; item += gridDim.x) {
         int q, iw, tm, tn;
@@ -460,17 +462,21 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
           // planes of the terms the part's products read (t2 only with six products)
           const int nt = (NT == 3 && part_products(P, q, iw, part) != 6) ? 2 : NT;
           const int plane0 = (part * P.n_freq + iw) * PL;
+          const int row_a = tm * BM, row_b = tn * BN;
           for (int kc = 0; kc < nK; ++kc, ++gs) {
-            const int s = (int)(gs % STAGES);
-            const uint32_t u = (uint32_t)(gs / STAGES);
-            if (!tc::mbar_wait(&bar->empty[s], (u & 1) ^ 1, status, 1, WAIT_BUDGET_NS)) { ok = false; break; }
+            const int s = slot;
+            if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, status, 1, WAIT_BUDGET_NS)) { ok = false; break; }
+            if (++slot == STAGES) {
+              slot = 0;
+              ph ^= 1u;
+            }
             tc::mbar_arrive_expect_tx(&bar->full[s], 4 * nt * TILE_BYTES);
             unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
 #pragma unroll
             for (int j = 0; j < PL; ++j) {
               if (j % NT >= nt) continue;
-              tc::tma_load_3d(st + j * TILE_BYTES, &P.tmA[q], &bar->full[s], kc * BK, tm * BM, plane0 + j);
-              tc::tma_load_3d(st + (PL + j) * TILE_BYTES, &P.tmB[q], &bar->full[s], kc * BK, tn * BN, j);
+              tc::tma_load_3d(st + j * TILE_BYTES, &P.tmA[q], &bar->full[s], kc * BK, row_a, plane0 + j);
+              tc::tma_load_3d(st + (PL + j) * TILE_BYTES, &P.tmB[q], &bar->full[s], kc * BK, row_b, j);
             }
           }
         }
