@@ -662,6 +662,8 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
     if (lane == 0) {
       // ---------------- TMA producer (both CTAs) ----------------
       int64_t gs = 0;
+      int slot = 0;        // ring slot of stage gs and its phase parity
+      uint32_t ph = 0;
       bool ok = true;
       for (int64_t item = pair; item < P.total_items && ok; item += npairs) {
         int q, iw, tm, tn;
@@ -672,9 +674,12 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
           const int nt = (NT == 3 && part_products(P, q, iw, part) != 6) ? 2 : NT;
           const int plane0 = (part * P.n_freq + iw) * PL;
           for (int kc = 0; kc < nK; ++kc, ++gs) {
-            const int s = (int)(gs % STAGES);
-            const uint32_t u = (uint32_t)(gs / STAGES);
-            if (!tc::mbar_wait(&bar->empty[s], (u & 1) ^ 1, status, 1, WAIT_BUDGET_NS)) { ok = false; break; }
+            const int s = slot;
+            if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, status, 1, WAIT_BUDGET_NS)) { ok = false; break; }
+            if (++slot == STAGES) {
+              slot = 0;
+              ph ^= 1u;
+            }
             // the first CTA's barrier counts the loads of both CTAs
             if (leader) tc::mbar_arrive_expect_tx(&bar->full[s], 4 * nt * (RG::A_BYTES + RG::B_BYTES));
             const uint32_t fb = tc::mapa(&bar->full[s], 0);
