@@ -172,6 +172,38 @@ def accelerated_pairs(E_v: np.ndarray, E_c: np.ndarray, sel: dict):
     return c_idx, Ecol, wcol, dE, w
 
 
+def grid_energy_of_bands(E_c: np.ndarray, N0: int, dE: float, E_max: float) -> np.ndarray:
+    """The energy each conduction band carries in Eq. 3 with the grid of Eq. 4.
+
+    Bands 1..N0 (0-based 0..N0-1) keep their own energy.  A band above N0
+    takes the midpoint E_i of the Eq. 4 step [e_k, e_{k+1}) that holds its
+    energy, with the steps of select_accelerated (uniform from E_0, the last
+    one clipped at E_max); the last step is closed and also collects energies
+    above E_max, the first collects any below E_0.
+    """
+    E_c = np.asarray(E_c, dtype=np.float64)
+    out = E_c.copy()
+    sel = select_accelerated(E_c, N0, dE, 1.0, 0.0, E_max)   # A, V0 only enter the weights
+    edges = sel["edges"]
+    if edges.size < 2:
+        return out
+    N0 = int(N0)
+    k = np.searchsorted(edges, E_c[N0:], side="right") - 1  # last edge <= E_c
+    k = np.clip(k, 0, edges.size - 2)
+    out[N0:] = sel["E_i"][k]
+    return out
+
+
+def energy_substitution_estimate(E_c: np.ndarray, grad_E_c: np.ndarray, N0: int, dE: float,
+                                 E_max: float) -> float:
+    """First-order change of a loss L when every band above N0 is given its
+    Eq. 4 grid energy in the denominators of Eq. 1 (the energy-substitution
+    part of the accelerated sum's error):  sum_c dL/dE_c (E_i(c) - E_c),
+    with dL/dE_c from the adjoint (chi0_grad)."""
+    E_c = np.asarray(E_c, dtype=np.float64)
+    return float(np.sum(np.asarray(grad_E_c, dtype=np.float64) * (grid_energy_of_bands(E_c, N0, dE, E_max) - E_c)))
+
+
 def chi0_full(prob, iq: int = 0, coeff_v=None, coeff_c=None, v_bands=None, c_bands=None):
     """chi0 of Eq. 1 for q-point iq over the given bands (default: all)."""
     v_bands = np.arange(prob.n_v) if v_bands is None else np.asarray(v_bands)

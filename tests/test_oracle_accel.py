@@ -128,3 +128,83 @@ def test_explicit_part_is_eq1_restricted_at_static_limit():
     expl = chi0_from_pairs(M[keep], f)[0]
     direct = sum(M[p][:, None] * M[p].conj()[None, :] / dE[p] for p in np.flatnonzero(keep))
     assert rel_fro(expl, direct) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# the dE -> 0 limit of Eq. 3/4 with the wavefunctions' own pair elements
+# (the text after Eq. 4 and Table I: the accelerated sum approaches the full
+# one as the energy grid is refined).  The synthetic conduction energies are
+# the DOS-quantile midpoints E_c(j) = F^-1(j - 1/2), F(E) = int_V0^E g, so the
+# bins [F^-1(j - 1), F^-1(j)] hold exactly one band each.
+# ---------------------------------------------------------------------------
+def _one_state_bins(prob, N0):
+    from oracle.quadrature import bin_edges, dos_count
+    A, V0, Emax = prob.dos_A, prob.dos_V0, prob.E_max
+    E_lo = V0 + (N0 / (A * 2.0 * math.sqrt(2.0) / 3.0)) ** (2.0 / 3.0)    # F(E_lo) = N0
+    n_bins = prob.n_c - N0
+    step = (Emax - E_lo) / n_bins
+    edges = bin_edges(E_lo, Emax, step, A, V0, "quantile")
+    assert edges.size == n_bins + 1
+    assert np.allclose(dos_count(edges, A, V0) - N0, np.arange(n_bins + 1), rtol=0, atol=1e-9)
+    return edges, step
+
+
+def _pairs_of(prob):
+    from oracle import pair_elements, wfn_to_grid
+    uv = wfn_to_grid(prob.coeff_v(0), prob.gw, prob.n)
+    uc = wfn_to_grid(prob.coeff_c(), prob.gw, prob.n)
+    return pair_elements(uv, uc, prob.gvec[0], prob.n)
+
+
+def test_one_state_per_dos_quantile_bin_is_the_full_sum():
+    """Nodes at the DOS midpoints F^-1((F(a) + F(b))/2) with weights int_a^b g = 1:
+    every bin's state is its own band with its own energy, and Eq. 3/4 gives
+    Eq. 1 to rounding."""
+    from oracle.quadrature import bin_edges, dos_count, nearest_bands
+    prob = make_problem("c1", n_v=4, n_c=96, n_imag=2)
+    N0 = 8
+    A, V0 = prob.dos_A, prob.dos_V0
+    edges, step = _one_state_bins(prob, N0)
+    nodes = bin_edges(edges[0], prob.E_max, step / 2, A, V0, "quantile")[1::2]
+    w = dos_count(edges[1:], A, V0) - dos_count(edges[:-1], A, V0)
+    assert np.allclose(w, 1.0, rtol=0, atol=1e-12)
+    assert np.allclose(nodes, prob.E_c[N0:], rtol=0, atol=1e-14)
+    rep = np.array([nearest_bands(prob.E_c, N0, e, 1)[0] for e in nodes])
+    assert np.array_equal(rep, np.arange(N0, prob.n_c))
+    sel = dict(explicit=np.arange(N0), rep=rep, E_i=nodes, w_i=w)
+    c_idx, Ecol, wcol, dEp, wp = accelerated_pairs(prob.E_v, prob.E_c, sel)
+    assert np.array_equal(c_idx, np.arange(prob.n_c))
+    M = _pairs_of(prob)
+    _, _, _, dEf, wf = full_pairs(prob.E_v, prob.E_c)
+    acc = chi0_from_pairs(M, freq_factor(dEp, wp, prob.omega, prob.delta))
+    full = chi0_from_pairs(M, freq_factor(dEf, wf, prob.omega, prob.delta))
+    for iw in range(prob.omega.size):
+        assert rel_fro(acc[iw], full[iw]) < 1e-14
+
+
+def test_midpoint_rule_on_one_state_bins_converges_quadratically():
+    """Eq. 4's midpoint node and weight g(E_i) dE_i on the same one-state bins:
+    the node moves off the band energy and the weight off 1 by O(dE^2) per
+    bin, so the distance from the full sum falls as dE^2 (fitted slope) while
+    the bands are refined (N0 / N_c fixed, so E_0 stays put)."""
+    from oracle.quadrature import nearest_bands, quadrature_nodes
+    hs, errs = [], []
+    for n_c in (60, 120, 240, 480):
+        prob = make_problem("c1", n_v=3, n_c=n_c, n_imag=1)
+        N0 = n_c // 10
+        edges, step = _one_state_bins(prob, N0)
+        nodes, raw = quadrature_nodes(edges, "midpoint")
+        rep = np.array([nearest_bands(prob.E_c, N0, e, 1)[0] for e in nodes])
+        assert np.array_equal(rep, np.arange(N0, n_c))
+        sel = dict(explicit=np.arange(N0), rep=rep, E_i=nodes, w_i=dos(nodes, prob.dos_A, prob.dos_V0) * raw)
+        _, _, _, dEp, wp = accelerated_pairs(prob.E_v, prob.E_c, sel)
+        _, _, _, dEf, wf = full_pairs(prob.E_v, prob.E_c)
+        M = _pairs_of(prob)
+        acc = chi0_from_pairs(M, freq_factor(dEp, wp, prob.omega, prob.delta))
+        full = chi0_from_pairs(M, freq_factor(dEf, wf, prob.omega, prob.delta))
+        errs.append(max(rel_fro(acc[iw], full[iw]) for iw in range(prob.omega.size)))
+        hs.append(step)
+    slope = np.polyfit(np.log(hs), np.log(errs), 1)[0]
+    print(f"\nmidpoint on one-state bins: errors {['%.2e' % e for e in errs]}, fitted order {slope:.3f}")
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    assert 1.8 < slope < 2.2

@@ -63,7 +63,7 @@ def test_first_order_energy_substitution_estimate():
     loss by sum_c dL/dE_c (E_i(c) - E_c) to first order: the residual of the
     linear estimate falls quadratically with the step while the change itself
     falls linearly."""
-    from oracle import select_accelerated
+    from oracle import energy_substitution_estimate, grid_energy_of_bands, select_accelerated
     rng = np.random.default_rng(11)
     nv, nc, ng = 3, 60, 6
     M = (rng.standard_normal((nv * nc, ng)) + 1j * rng.standard_normal((nv * nc, ng))) / 4
@@ -84,11 +84,18 @@ def test_first_order_energy_substitution_estimate():
     out = []
     for step in (0.08, 0.04, 0.02):
         sel = select_accelerated(Ec, N0, step, 1.0, 0.17, 2.2)
-        k = np.clip(np.searchsorted(sel["edges"], Ec[N0:], side="right") - 1, 0, sel["E_i"].size - 1)
+        # brute force: the midpoint of the step whose half-open interval holds E_c
         Esub = Ec.copy()
-        Esub[N0:] = sel["E_i"][k]
+        for c in range(N0, nc):
+            for k in range(sel["E_i"].size):
+                last = k == sel["E_i"].size - 1
+                if sel["edges"][k] <= Ec[c] and (last or Ec[c] < sel["edges"][k + 1]):
+                    Esub[c] = sel["E_i"][k]
+                    break
+        assert np.array_equal(Esub, grid_energy_of_bands(Ec, N0, step, 2.2))
         actual = loss(Esub) - loss(Ec)
-        est = float(np.sum(gEc * (Esub - Ec)))
+        est = energy_substitution_estimate(Ec, gEc, N0, step, 2.2)
+        assert est == pytest.approx(float(np.sum(gEc * (Esub - Ec))), rel=1e-14)
         out.append((abs(actual), abs(actual - est)))
     for (a1, r1), (a2, r2) in zip(out, out[1:]):
         assert r2 < 0.5 * r1            # residual: second order
