@@ -184,6 +184,27 @@ chi0_status chi0_backward(chi0_plan plan, int iq, const void* M, int n_v, int n_
                           const double* diag_g, void* grad_M, double* grad_Ev, double* grad_Ecol,
                           void* stream);
 
+/* First-order error estimate of Eq. 3/4's energy substitution (derived from Eq. 1 and
+ * Eq. 4): when every conduction band above N0 is given the energy E_i of its Eq. 4
+ * grid point in the denominators, a loss L changes by
+ *   dL ~ sum_{c >= N0} dL/dE_c (E_i(c) - E_c),
+ * with dL/dE_c the grad_Ecol of chi0_backward over the full band sum.  E_i(c) is the
+ * midpoint of the step [e_k, e_k+1) holding E_c, e_k = min(E_0 + k dE, E_max),
+ * E_0 = E_c[N0-1], k = 0..N_E-1, N_E = ceil((E_max - E_0)/dE) (the steps of
+ * chi0_select_accelerated; the last step is closed and energies outside [E_0, E_max]
+ * go to the end steps); bands below N0 keep E_c.  Computed on the device, reduced in
+ * a fixed order (deterministic).
+ * E_c, grad_Ecol: (device) [n_c] FP64, E_c sorted ascending; E_sub: (device) [n_c]
+ * receives E_i(c) (E_c for c < N0), or NULL; *estimate (host) receives the sum.
+ * Uses one double of the plan's workspace and synchronises `stream`. */
+chi0_status chi0_energy_substitution_estimate(chi0_plan plan, const double* E_c, const double* grad_Ecol, int n_c,
+                                              int N0, double dE, double E_max, double* E_sub, double* estimate,
+                                              void* stream);
+
+/* Host version of the band-to-grid-energy map above (host arrays, host computation):
+ * E_out[c] = E_i(c) for c >= N0, E_c[c] otherwise.  Returns 0, or -1 for bad arguments. */
+int chi0_grid_energies(const double* E_c, int n_c, int N0, double dE, double E_max, double* E_out);
+
 /* Diagnostic (not part of the method): enqueue a one-thread wait on a barrier
  * that nothing releases, bounded by budget_ms (0 < budget_ms <= 1000), through
  * the same bounded-wait code the tensor-core kernels use.  The wait runs out,

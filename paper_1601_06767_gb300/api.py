@@ -389,20 +389,13 @@ class Chi0DiagLoss(torch.autograd.Function):
         return gM, gEv, gEc, None, None, None, None
 
 
-def grid_energies_of_bands(E_c, N0: int, dE: float, E_max: float):
-    """For every conduction band above N0, the midpoint E_i of the Eq. 4 energy
-    step that contains its energy (steps of width dE from E_0 = E_c[N0-1], the
-    last one clipped at E_max); bands up to N0 keep their own energy."""
-    E_c = np.asarray(E_c, dtype=np.float64)
-    out = E_c.copy()
-    if N0 <= 0 or N0 >= E_c.size:
-        return out
-    E0 = E_c[N0 - 1]
-    k = np.floor((E_c[N0:] - E0) / dE)
-    k = np.clip(k, 0, max(np.ceil((E_max - E0) / dE - 1e-12) - 1, 0))
-    lo = E0 + k * dE
-    hi = np.minimum(lo + dE, E_max)
-    out[N0:] = 0.5 * (lo + hi)
+def grid_energies_of_bands(E_c, N0: int, dE: float, E_max: float) -> np.ndarray:
+    """chi0_grid_energies: for every conduction band above N0 the energy E_i of
+    its Eq. 4 grid point; bands up to N0 keep their own energy (host arrays)."""
+    E_c = _f64(E_c)
+    out = np.empty_like(E_c)
+    if L.lib().chi0_grid_energies(E_c.ctypes.data, E_c.size, int(N0), float(dE), float(E_max), out.ctypes.data) != 0:
+        raise L.Chi0Error(L.CHI0_ERR_INVALID, "chi0_grid_energies rejected its input")
     return out
 
 
@@ -410,9 +403,13 @@ def energy_substitution_estimate(plan, iq: int, M, E_v, E_c, w_col, N0: int, dE:
                                  diag_g=None, grad_chi=None):
     """First-order estimate of the change of a loss when every conduction band
     above N0 is given the energy of its Eq. 4 grid point instead of its own:
-    dL ~ sum_c dL/dE_c (E_i(c) - E_c), with dL/dE_c from chi0_backward on the
-    full band sum.  Returns (estimate, grad_E_c)."""
+    chi0_backward on the full band sum for dL/dE_c, then
+    chi0_energy_substitution_estimate for sum_c dL/dE_c (E_i(c) - E_c).
+    Returns (estimate, grad_E_c)."""
     n_v, n_c = int(E_v.numel()), int(E_c.numel())
     _, _, gEc = plan.backward(iq, M, n_v, n_c, E_v, E_c, w_col, grad_chi=grad_chi, diag_g=diag_g)
-    Ei = torch.from_numpy(grid_energies_of_bands(E_c.cpu().numpy(), N0, dE, E_max)).to(E_c.device)
-    return float((gEc * (Ei - E_c)).sum()), gEc
+    est = C.c_double(0.0)
+    plan._check(L.lib().chi0_energy_substitution_estimate(plan._h, _ptr(plan._c(E_c, "E_c", torch.float64)),
+                                                          _ptr(gEc), n_c, int(N0), float(dE), float(E_max), None,
+                                                          C.byref(est), _stream()))
+    return est.value, gEc

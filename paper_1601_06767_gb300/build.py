@@ -15,7 +15,10 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libchi0.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+# host code: no contraction of a*b + c into fused multiply-adds, so host results (band selections,
+# grid energies) round the same way on x86-64 and aarch64
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+         "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]
 
 
@@ -43,6 +46,11 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "chi0.h"))
     extra = list(extra or [])
+    # a change of compiler or flags rebuilds everything
+    stamp = os.path.join(BUILD, "flags.txt")
+    flags_now = " ".join([nvcc, *ARCH, *FLAGS, *extra])
+    if not os.path.exists(stamp) or open(stamp).read() != flags_now:
+        force = True
     jobs = []
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
@@ -55,6 +63,8 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
             sys.stderr.write(r.stdout + r.stderr)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed: {' '.join(cmd)}")
+    with open(stamp, "w") as fh:
+        fh.write(flags_now)
     objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in sources()]
     if force or jobs or not os.path.exists(LIB) or _stale(LIB, objs):
         tmp = LIB + ".tmp"

@@ -162,6 +162,10 @@ cudaError_t launch_backward(chi0_plan_s* p, int nG, const void* M, int64_t p0, i
                             const double* E_v, const double* E_col, const double* w_col, const double2* gamma,
                             const double* diag, void* gM, double* gEv, double* gEc, double* work, cudaStream_t s);
 int bwd_max_freq();
+// first-order energy-substitution estimate of Eq. 3/4 (one block; writes the grid energy of every
+// band to E_sub when it is not NULL and the sum to *out, both device pointers)
+cudaError_t launch_energy_substitution(const double* E_c, const double* sens, int n_c, int N0, double dE, double E_max,
+                                       double* E_sub, double* out, cudaStream_t s);
 // autotuner: apply a cached entry for sphere iq if one exists (returns true if applied)
 bool tune_apply_cached(chi0_plan_s* p, int iq);
 cudaError_t launch_wait_selftest(chi0_plan_s* p, double budget_ms, cudaStream_t s);

@@ -219,7 +219,56 @@ __global__ void k_reduce_cols(const double* __restrict__ gdE, int64_t p0, int64_
   gEc[ic] -= s;
 }
 
+// Eq. 4 step edge e_k = min(E_0 + k dE, E_max), rounded as written (no fused multiply-add, so the
+// value is the same as the host selection's)
+__device__ __forceinline__ double step_edge(double E0, double dE, int k, double E_max) {
+  return fmin(__dadd_rn(E0, __dmul_rn(dE, (double)k)), E_max);
+}
+
+// First-order estimate of the energy substitution of Eq. 3/4: every band c >= N0 takes the
+// midpoint E_i of the Eq. 4 step [e_k, e_k+1) holding E_c (the last step closed, energies outside
+// [E_0, E_max] to the end steps), and the estimate is sum_c sens_c (E_i(c) - E_c).  One block:
+// each thread sums a fixed stride of bands, then a fixed tree in shared memory (deterministic).
+constexpr int kEstThreads = 1024;
+__global__ void __launch_bounds__(kEstThreads)
+k_energy_substitution(const double* __restrict__ E_c, const double* __restrict__ sens, int n_c, int N0, double dE,
+                      double E_max, double* __restrict__ E_sub, double* __restrict__ out) {
+  __shared__ double red[kEstThreads];
+  // E_0 = E_c of band N0 and N_E = ceil((E_max - E_0) / dE) steps, as the host selection has them
+  const bool grid = N0 > 0 && N0 < n_c;
+  const double E0 = grid ? E_c[N0 - 1] : 0.0;
+  const int NE = grid ? (int)fmax(ceil((E_max - E0) / dE - 1e-12), 0.0) : 0;
+  double acc = 0.0;
+  for (int c = threadIdx.x; c < n_c; c += kEstThreads) {
+    const double E = E_c[c];
+    double Ei = E;
+    if (c >= N0 && NE > 0) {
+      // last k in [0, NE-1] with e_k <= E: start from the quotient, then step to the exact edge
+      int k = (int)fmin(fmax(floor((E - E0) / dE), 0.0), (double)(NE - 1));
+      while (k + 1 <= NE - 1 && step_edge(E0, dE, k + 1, E_max) <= E) ++k;
+      while (k > 0 && step_edge(E0, dE, k, E_max) > E) --k;
+      const double lo = step_edge(E0, dE, k, E_max), hi = step_edge(E0, dE, k + 1, E_max);
+      Ei = __dmul_rn(0.5, __dadd_rn(lo, hi));
+      acc = __dadd_rn(acc, __dmul_rn(sens[c], __dadd_rn(Ei, -E)));
+    }
+    if (E_sub) E_sub[c] = Ei;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = kEstThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
 }  // namespace
+
+cudaError_t launch_energy_substitution(const double* E_c, const double* sens, int n_c, int N0, double dE, double E_max,
+                                       double* E_sub, double* out, cudaStream_t s) {
+  k_energy_substitution<<<1, kEstThreads, 0, s>>>(E_c, sens, n_c, N0, dE, E_max, E_sub, out);
+  return cudaGetLastError();
+}
 
 int bwd_max_freq() { return kMaxFreqBwd; }
 

@@ -891,6 +891,23 @@ chi0_status chi0_backward(chi0_plan p, int iq, const void* M, int n_v, int n_c, 
   return CHI0_OK;
 }
 
+chi0_status chi0_energy_substitution_estimate(chi0_plan p, const double* E_c, const double* grad_Ecol, int n_c,
+                                              int N0, double dE, double E_max, double* E_sub, double* estimate,
+                                              void* stream) {
+  chi0_status st = check_plan(p);
+  if (st != CHI0_OK) return st;
+  if (n_c < 0 || N0 < 0 || !(dE > 0.0)) return fail(p, CHI0_ERR_INVALID, "need n_c >= 0, N0 >= 0 and dE > 0");
+  if (!estimate) return fail(p, CHI0_ERR_INVALID, "estimate is NULL");
+  *estimate = 0.0;
+  if (n_c == 0) return CHI0_OK;
+  if (!E_c || !grad_Ecol) return fail(p, CHI0_ERR_INVALID, "NULL buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(p, chi0::launch_energy_substitution(E_c, grad_Ecol, n_c, std::min(N0, n_c), dE, E_max, E_sub, p->d_bwd, s));
+  CK(p, cudaMemcpyAsync(estimate, p->d_bwd, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(p, cudaStreamSynchronize(s));
+  return CHI0_OK;
+}
+
 chi0_status chi0_selftest_wait(chi0_plan p, double budget_ms, void* stream) {
   chi0_status st = check_plan(p);
   if (st != CHI0_OK) return st;
@@ -1053,6 +1070,27 @@ int chi0_select_accelerated(const double* E_c, int n_c, int N0, double dE, doubl
     c_sel[n] = best; E_sel[n] = Ei; w_sel[n] = g * dEi; ++n;
   }
   return n;
+}
+
+int chi0_grid_energies(const double* E_c, int n_c, int N0, double dE, double E_max, double* E_out) {
+  if (!E_c || !E_out || n_c < 0 || N0 < 0 || !(dE > 0.0)) return -1;
+  for (int c = 0; c < n_c; ++c) E_out[c] = E_c[c];
+  N0 = std::min(N0, n_c);
+  if (N0 == 0 || N0 >= n_c) return 0;
+  const double E0 = E_c[N0 - 1];
+  const int NE = (int)ceil((E_max - E0) / dE - 1e-12);
+  if (NE <= 0) return 0;
+  auto edge = [&](int k) { return std::min(E0 + dE * k, E_max); };   // Eq. 4 step edges
+  for (int c = N0; c < n_c; ++c) {
+    // the step [e_k, e_k+1) holding E_c: last k in [0, NE-1] with e_k <= E_c
+    int a = 0, b = NE - 1;
+    while (a < b) {
+      const int m = (a + b + 1) / 2;
+      if (edge(m) <= E_c[c]) a = m; else b = m - 1;
+    }
+    E_out[c] = 0.5 * (edge(a) + edge(a + 1));
+  }
+  return 0;
 }
 
 int chi0_select_quadrature(const double* E_c, int n_c, int N0, double dE, double dos_A, double dos_V0,

@@ -130,3 +130,31 @@ def test_host_selection_entry_points_reject_bad_arguments():
                                     c.ctypes.data, e.ctypes.data, w.ctypes.data, 64) == -1
     assert lib.chi0_select_adaptive(E.ctypes.data, 4, 2, s.ctypes.data, 0.1, 1.0, 0.17, 2.2, -1, 1,
                                     c.ctypes.data, e.ctypes.data, w.ctypes.data, 64) == -1
+
+
+@pytest.mark.parametrize("name,dE_eV", [("c2", 2.0), ("c5", 2.0), ("c5", 0.37), ("c1", 1.5)])
+def test_grid_energies_match_oracle(name, dE_eV):
+    """chi0_grid_energies (host C) gives every band the same Eq. 4 grid energy
+    as the oracle, bit for bit."""
+    from oracle import grid_energy_of_bands
+    pr = make_problem(name)
+    N0 = pr.N0 if pr.N0 else 40
+    dE = dE_eV / HARTREE_EV
+    got = P.grid_energies_of_bands(pr.E_c, N0, dE, pr.E_max)
+    assert np.array_equal(got, grid_energy_of_bands(pr.E_c, N0, dE, pr.E_max))
+
+
+def test_grid_energies_edge_cases():
+    from oracle import grid_energy_of_bands
+    rng = np.random.default_rng(9)
+    E = np.sort(rng.uniform(0.2, 2.0, 200))
+    E0, dE = E[19], 0.05
+    E[60] = E0 + 3 * dE                 # exactly on an interior edge: the upper step holds it
+    E[-3:] = [2.3, 2.4, 2.5]            # above E_max: the last step
+    E.sort()
+    for N0, Emax in ((20, 2.2), (0, 2.2), (200, 2.2), (250, 2.2), (20, E0), (20, E0 - 0.1), (1, 2.2)):
+        got = P.grid_energies_of_bands(E, N0, dE, Emax)
+        assert np.array_equal(got, grid_energy_of_bands(E, N0, dE, Emax)), (N0, Emax)
+    assert np.array_equal(P.grid_energies_of_bands(E[:0], 5, dE, 2.2), E[:0])
+    with pytest.raises(L.Chi0Error):
+        P.grid_energies_of_bands(E, 5, 0.0, 2.2)

@@ -136,3 +136,36 @@ def test_energy_substitution_estimate_gpu(precision):
     for (a1, r1), (a2, r2) in zip(rows, rows[1:]):
         assert r2 < 0.5 * r1
     assert rows[-1][1] < 0.05 * rows[-1][0]
+
+
+def test_energy_substitution_estimate_matches_oracle():
+    """chi0_energy_substitution_estimate against the oracle on the same
+    sensitivities: the grid energy of every band bit for bit, the sum to
+    rounding (the device sums in a fixed tree order)."""
+    import ctypes as C
+    import torch
+    import paper_1601_06767_gb300 as pkg
+    from paper_1601_06767_gb300 import _lib as L
+    from oracle import energy_substitution_estimate, grid_energy_of_bands
+    from synth import HARTREE_EV
+    prob = make_problem("c5")
+    rng = np.random.default_rng(21)
+    sens = rng.standard_normal(prob.n_c) * np.exp(-prob.E_c)
+    small = make_problem("c1")                      # the plan only lends its workspace
+    with pkg.Chi0Plan(small.n, small.gvec, [0.0], small.delta, precision="fp64") as plan:
+        Ecd, sd = _dev(prob.E_c), _dev(sens)
+        for N0, dE_eV in ((prob.N0, 2.0), (prob.N0, 0.31), (1, 4.0), (0, 2.0), (prob.n_c, 2.0)):
+            dE = dE_eV / HARTREE_EV
+            Esub = torch.empty_like(Ecd)
+            est = C.c_double(0.0)
+            plan._check(pkg.lib().chi0_energy_substitution_estimate(
+                plan._h, C.c_void_p(Ecd.data_ptr()), C.c_void_p(sd.data_ptr()), prob.n_c, N0, dE, prob.E_max,
+                C.c_void_p(Esub.data_ptr()), C.byref(est), None))
+            ref_E = grid_energy_of_bands(prob.E_c, N0, dE, prob.E_max)
+            assert np.array_equal(Esub.cpu().numpy(), ref_E), (N0, dE_eV)
+            ref = energy_substitution_estimate(prob.E_c, sens, N0, dE, prob.E_max)
+            scale = float(np.sum(np.abs(sens * (ref_E - prob.E_c)))) or 1.0
+            assert abs(est.value - ref) <= 1e-13 * scale, (N0, dE_eV, est.value, ref)
+        st = pkg.lib().chi0_energy_substitution_estimate(plan._h, None, None, 10, 1, 0.0, 2.2, None,
+                                                         C.byref(est), None)
+        assert st == L.CHI0_ERR_INVALID
