@@ -272,7 +272,10 @@ chi0_status chi0_profile_read(chi0_plan plan, double* total_ms, int64_t* launche
  * Scratch: a fixed 4 MiB array of FP64 frequency factors in the library's
  * device image, held by every device that loads the library until the process
  * exits.  The first call on a device looks up that array's device address
- * (with the device current) and should come before any stream capture.  All
+ * (with the device current) and should come before any stream capture; so does
+ * the first call in a new context on that device (after cudaDeviceReset, or a
+ * context made current through the driver API), which has its own copy of the
+ * array at its own address and is recognised by its context id.  All
  * calls share the array and it keeps the last call's contents; every entry a
  * call reads is written earlier in the same call, so nothing needs clearing,
  * but calls whose work can overlap on the GPU (other streams, other host

@@ -1,6 +1,9 @@
 // Frequency factors of Eq. 1 (FP64) and the plain FP64 contraction
 //   chi0[w][G][G'] += sum_p f_p(w) M_p(G) conj(M_p(G'))
 // on the CUDA cores (DFMA), used by CHI0_FP64 plans.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <mutex>
 #include <string>
 
@@ -165,7 +168,32 @@ __global__ void k_weights_noalloc(int64_t p0, int64_t K, int n_c, const double* 
 
 std::mutex g_noalloc_mu;
 constexpr int kNoAllocMaxDevices = 64;
-double2* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+// device address of the array per device, and the id of the CUDA context it was looked up in:
+// a new context on the device (after cudaDeviceReset, or a context the caller made current
+// through the driver API) holds its own copy of the array at its own address
+struct NoAllocSlot {
+  unsigned long long ctx_id;
+  double2* ptr;
+};
+NoAllocSlot g_noalloc_slot[kNoAllocMaxDevices] = {};
+PFN_cuCtxGetId_v12000 g_ctx_get_id = nullptr;
+bool g_ctx_get_id_tried = false;
+
+// unique id of the current context (ids are never reused within a process), 0 if unavailable
+unsigned long long current_context_id() {
+  if (!g_ctx_get_id_tried) {
+    g_ctx_get_id_tried = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(fn);
+    cudaGetLastError();
+  }
+  unsigned long long id = 0;
+  if (!g_ctx_get_id || g_ctx_get_id(nullptr, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 }  // namespace
 }  // namespace chi0
@@ -195,20 +223,26 @@ extern "C" chi0_status chi0_accumulate_fp64_noalloc(int n_G, const void* M, int 
   }
   double2* scratch = nullptr;
   {
-    // set-up, once per device, with that device current: the host-side name of
-    // the array is only a stand-in, so look up its device address
+    // set-up, once per device and context, with that device current: the host-side name of
+    // the array is only a stand-in, so look up its device address.  Without context ids
+    // (an old driver) the address is looked up on every call.
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-      e = cudaGetSymbolAddress((void**)&g_noalloc_ptr[dev], g_noalloc_factors);
+    const unsigned long long ctx = current_context_id();   // 0 before the runtime's first use of the device
+    NoAllocSlot& slot = g_noalloc_slot[dev];
+    if (!slot.ptr || ctx == 0 || slot.ctx_id != ctx) {
+      double2* ptr = nullptr;
+      e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_factors);
       if (e != cudaSuccess) {
-        g_noalloc_ptr[dev] = nullptr;
+        slot.ptr = nullptr;
         set_global_error(std::string("chi0_accumulate_fp64_noalloc: cudaGetSymbolAddress: ") +
                          cudaGetErrorString(e));
         cudaGetLastError();
         return CHI0_ERR_CUDA;
       }
+      slot.ptr = ptr;
+      slot.ctx_id = current_context_id();                   // the lookup made the context current
     }
-    scratch = g_noalloc_ptr[dev];
+    scratch = slot.ptr;
   }
   FreqList fl;
   for (int i = 0; i < kNoAllocMaxFreq; ++i) fl.om[i] = make_double2(i < n_freq ? freq_re[i] : 0.0, i < n_freq ? freq_im[i] : 0.0);

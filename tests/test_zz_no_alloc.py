@@ -1,5 +1,6 @@
 """The allocation-free FP64 accumulate (chi0_accumulate_fp64_noalloc) against
-the plan-based chi0_accumulate of a CHI0_FP64 plan.
+the plan-based chi0_accumulate of a CHI0_FP64 plan and against the FP64
+oracle of Eq. 1.
 
 That entry point is for callers that cannot allocate device memory when they
 need chi0 (a framework that owns all device memory, a loop that must not call
@@ -11,6 +12,7 @@ import ctypes as C
 import numpy as np
 import pytest
 
+from oracle import chi0_from_pairs, freq_factor
 from synth import make_problem
 
 pytestmark = pytest.mark.gpu
@@ -52,8 +54,15 @@ def test_noalloc_matches_plan_accumulate_twice():
                                               C.c_void_p(got.data_ptr()), stream)
         assert st == L.CHI0_OK, lib.chi0_last_error(None)
         torch.cuda.synchronize()
-        err = max(_rel(got[i].cpu().numpy(), ref[i].cpu().numpy()) for i in range(nf))
+        got_h = got.cpu().numpy()
+        err = max(_rel(got_h[i], ref[i].cpu().numpy()) for i in range(nf))
         assert err < TOL64, (call, err)
+        # and against the FP64 oracle of Eq. 1 directly
+        dE = (Ev[:, None] - Ec[None, :]).reshape(-1)
+        wp = np.tile(w, nv) if weighted else np.ones_like(dE)
+        oracle = chi0_from_pairs(M, freq_factor(dE, wp, prob.omega, prob.delta))
+        err_o = max(_rel(got_h[i], oracle[i]) for i in range(nf))
+        assert err_o < TOL64, (call, err_o)
 
 
 def test_noalloc_rejects_sizes_beyond_its_limit():
