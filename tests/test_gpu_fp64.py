@@ -5,6 +5,7 @@ Bar: relative Frobenius error <= 1e-12."""
 import numpy as np
 import pytest
 
+from _parity import check_chi
 from oracle import (accelerated_pairs, chi0_from_pairs, freq_factor, pair_elements, rel_fro,
                     select_accelerated, wfn_to_grid)
 from synth import make_problem
@@ -86,8 +87,7 @@ def test_accumulate_fp64_matches_eq1():
     ref = chi0_from_pairs(M, freq_factor(dE, np.tile(w, nv), prob.omega, prob.delta))
     with _plan(prob, max_pairs=64) as plan:       # several internal pair blocks
         chi = plan.accumulate(0, _dev(M), nv, nc, _dev(Ev), _dev(Ec), _dev(w)).cpu().numpy()
-    for iw in range(prob.omega.size):
-        assert rel_fro(chi[iw], ref[iw]) < TOL64
+    check_chi(chi, ref, TOL64, label="fp64 accumulate")
 
 
 def test_build_c1_full_fp64():
@@ -104,7 +104,7 @@ def test_build_c1_full_fp64():
         chi = plan.build(0, psi_v, _dev(prob.E_v), psi_c, _dev(prob.E_c))
         plan.sync_status()
         chi = chi.cpu().numpy()
-    assert rel_fro(chi[0], ref[0]) < TOL64
+    check_chi(chi, ref, TOL64, label="fp64 build c1")
 
 
 def test_build_accelerated_fp64():
@@ -120,7 +120,7 @@ def test_build_accelerated_fp64():
         psi_c = plan.wfn_to_grid(_dev(cc))
         chi = plan.build(0, psi_v, _dev(prob.E_v), psi_c, _dev(Ecol), w_col=_dev(wcol),
                          c_idx=_dev(c_idx.astype(np.int32))).cpu().numpy()
-    assert rel_fro(chi, ref) < TOL64
+    check_chi(chi, ref, TOL64, label="fp64 accelerated build")
 
 
 def test_empty_inputs_are_no_ops():

@@ -1,0 +1,123 @@
+"""GPU parity at the sizes the benchmark runs, against the FP64 oracle.
+
+* The 64-atom-sized build as the benchmark runs it: N_G = 2500 on the 48^3
+  grid, pair blocks of 8192 pairs (3 valence x 6000 conduction bands: three
+  conduction blocks, the last ragged), pipelined on two streams, Hermitian
+  mode with its long H2 chains for BF16 x6.
+* The contraction at the 256-atom-sized sphere (N_G = 8000): one launch of
+  1024 pairs, split and FP64 paths.
+* The whole 256-atom-sized path (96^3 grid, N_G = 8000) through the pipelined
+  build on a band subset.
+
+Bars per frequency: relative Frobenius error <= 1e-6 (split) / 1e-12 (FP64)
+and the same bound on max|chi - ref| / max|ref|."""
+import numpy as np
+import pytest
+
+from _parity import check_chi
+from oracle import chi0_from_pairs, freq_factor, pair_elements, wfn_to_grid
+from synth import make_problem
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-6
+TOL64 = 1e-12
+_CACHE = {}
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _plan(prob, precision, **kw):
+    from paper_1601_06767_gb300 import Chi0Plan
+    return Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision=precision, gw=prob.gw, **kw)
+
+
+def _oracle_pairs(prob, vb, cb, chunk=256):
+    """M[p][G], p = iv * len(cb) + ic, from the oracle, conduction bands in chunks."""
+    nG = prob.gvec[0].shape[0]
+    uv = wfn_to_grid(prob.coeff_v(0, vb), prob.gw, prob.n)
+    M = np.empty((vb.size, cb.size, nG), dtype=np.complex128)
+    for c0 in range(0, cb.size, chunk):
+        uc = wfn_to_grid(prob.coeff_c(cb[c0:c0 + chunk]), prob.gw, prob.n)
+        M[:, c0:c0 + chunk] = pair_elements(uv, uc, prob.gvec[0], prob.n).reshape(vb.size, -1, nG)
+    return M.reshape(-1, nG)
+
+
+def _c2_case():
+    if "c2" not in _CACHE:
+        prob = make_problem("c2", n_imag=2)                 # omega = 0, 0.01i, 2i Ha
+        vb = np.array([0, 61, 127])                         # spread over the valence band
+        cb = np.arange(prob.n_c)
+        M = _oracle_pairs(prob, vb, cb)
+        dE = (prob.E_v[vb][:, None] - prob.E_c[None, :]).reshape(-1)
+        ref = chi0_from_pairs(M, freq_factor(dE, np.ones_like(dE), prob.omega, prob.delta))
+        _CACHE["c2"] = (prob, vb, ref)
+    return _CACHE["c2"]
+
+
+@pytest.mark.parametrize("precision,n_products,herm", [("bf16", 6, None), ("fp16", 3, None), ("fp16", 3, True)])
+def test_build_64atom_pipelined_blocks(precision, n_products, herm):
+    """3 x 6000 pairs through chi0_build with the default 8192-pair blocks
+    (2730 + 2730 + 540 conduction columns), as in the benchmark step."""
+    prob, vb, ref = _c2_case()
+    with _plan(prob, precision, n_products=n_products, hermitian=herm) as plan:
+        psi_v = plan.wfn_to_grid(_dev(prob.coeff_v(0, vb)))
+        psi_c = plan.wfn_to_grid(_dev(prob.coeff_c()))
+        chi = plan.build(0, psi_v, _dev(prob.E_v[vb]), psi_c, _dev(prob.E_c))
+        plan.sync_status()
+        chi = chi.cpu().numpy()
+    check_chi(chi, ref, TOL, label=f"64-atom build {precision} x{n_products} herm={herm}")
+
+
+def _c5_contraction_case():
+    if "c5c" not in _CACHE:
+        prob = make_problem("c5", n_imag=2)
+        nG = prob.gvec[0].shape[0]
+        vb = np.arange(0, prob.n_v, prob.n_v // 8)          # 8 valence bands
+        cb = np.linspace(0, prob.n_c - 1, 128).round().astype(np.int64)
+        rng = np.random.default_rng(8000)
+        M = (rng.standard_normal((vb.size * cb.size, nG)) + 1j * rng.standard_normal((vb.size * cb.size, nG)))
+        M *= 1.0 / np.sqrt(2.0 * nG)
+        Ev, Ec = prob.E_v[vb], prob.E_c[cb]
+        dE = (Ev[:, None] - Ec[None, :]).reshape(-1)
+        ref = chi0_from_pairs(M, freq_factor(dE, np.ones_like(dE), prob.omega, prob.delta))
+        _CACHE["c5c"] = (prob, M, Ev, Ec, ref)
+    return _CACHE["c5c"]
+
+
+@pytest.mark.parametrize("precision,herm", [("fp16", None), ("fp16", True), ("bf16", None), ("fp64", None)])
+def test_contraction_256atom_sphere(precision, herm):
+    """chi0_accumulate of 8 x 128 pairs on the 8000-vector sphere (63 x 63
+    tiles of 128, the last ragged), seeded pair elements."""
+    prob, M, Ev, Ec, ref = _c5_contraction_case()
+    cdt = np.complex128 if precision == "fp64" else np.complex64
+    with _plan(prob, precision, hermitian=herm) as plan:
+        chi = plan.accumulate(0, _dev(M.astype(cdt)), Ev.size, Ec.size, _dev(Ev), _dev(Ec))
+        plan.sync_status()
+        chi = chi.cpu().numpy()
+    tol = TOL64 if precision == "fp64" else TOL
+    check_chi(chi, ref, tol, label=f"N_G 8000 contraction {precision} herm={herm}")
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_build_256atom_path_pipelined(precision):
+    """The 256-atom-sized path on 8 valence x 96 conduction bands spread over
+    the band energies: wavefunctions and pair elements on the 96^3 grid, the
+    N_G = 8000 contraction, blocks of 256 pairs (3 conduction blocks, pipelined)."""
+    if "c5b" not in _CACHE:
+        prob = make_problem("c5", n_imag=2)
+        vb = np.arange(3, prob.n_v, prob.n_v // 8)
+        cb = np.linspace(0, prob.n_c - 1, 96).round().astype(np.int64)
+        M = _oracle_pairs(prob, vb, cb, chunk=32)
+        dE = (prob.E_v[vb][:, None] - prob.E_c[cb][None, :]).reshape(-1)
+        _CACHE["c5b"] = (prob, vb, cb, chi0_from_pairs(M, freq_factor(dE, np.ones_like(dE), prob.omega, prob.delta)))
+    prob, vb, cb, ref = _CACHE["c5b"]
+    with _plan(prob, precision, max_pairs=256) as plan:
+        psi_v = plan.wfn_to_grid(_dev(prob.coeff_v(0, vb)))
+        psi_c = plan.wfn_to_grid(_dev(prob.coeff_c(cb)))
+        chi = plan.build(0, psi_v, _dev(prob.E_v[vb]), psi_c, _dev(prob.E_c[cb]))
+        plan.sync_status()
+        chi = chi.cpu().numpy()
+    check_chi(chi, ref, TOL, label=f"256-atom path {precision}")
