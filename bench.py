@@ -1,24 +1,35 @@
 #!/usr/bin/env python
-"""Benchmark of the chi0 hot path on the 64-atom-MgO-sized workload.
+"""Benchmark of the chi0 hot path on the 256-atom-MgO-sized workload.
 
-One step = one complete build of chi0_{G,G'}(q, omega) by the full band sum of
-Eq. 1 from plane-wave coefficients resident in HBM: wavefunctions on the 48^3
-grid for 128 valence + 6000 conduction bands, 768,000 pair matrix elements on
-the 2500-vector sphere, FP64 frequency factors for omega = 0 and 8 imaginary
-frequencies, split-precision tcgen05 contraction and FP64 merge into chi0.
+Workload (the largest single-GPU configuration): N_v = 512 valence bands,
+N_c = 20000 conduction bands, 96^3 grid, N_G = 8000 sphere vectors, one q,
+omega = 0 plus 8 imaginary frequencies, delta = 1e-3 Ha.  The full build
+streams 1250 conduction blocks of 16 bands (8192 pairs each) through the same
+kernels, one after another; one benchmark step builds chi0 over a fixed,
+seeded sample of those blocks (--c5-blocks, default 12: 192 conduction bands,
+98,304 pairs) from plane-wave coefficients resident in HBM: wavefunctions of
+the 512 valence and the sampled conduction bands on the 96^3 grid, pair
+matrix elements on the 8000-vector sphere, FP64 frequency factors, split
+precision tcgen05 contraction and FP64 merge into chi0 (9.2 GB).  The cost of
+a build is linear in the conduction blocks, so the full build time is the
+step time x 1250 / blocks (reported as extrapolated).
 
 Metric: effective TFLOP/s = 8 N_G^2 N_pairs n_omega / build time (the
-algorithmic work of the contraction only).  Inputs (6.6 GB of coefficients and
-grids) exceed L2, so no explicit flush is done between steps.
+algorithmic work of the contraction only).  Inputs and chi0 (about 15 GB)
+exceed L2, so no explicit flush is done between steps.
 
 Legs:
   --impl ours (default): the CUDA path through the C ABI, plus
-      e2e (host buffers, every copy inside the timed region, pipelined over
-      two buffers and a copy stream), the accelerated
-      sum of Eq. 3/4 on the same workload, the plain FP64 GPU path timed on a
-      sample of pairs and extrapolated, per-kernel device times (roofline)
-      and the FP64 oracle on host cores (cpu_baseline, rank 0 only).
-  --impl reference: the FP64 oracle on host cores, one bounded sample per step.
+      e2e (host buffers, every step's coefficient upload and chi0 download
+      inside the timed region, pipelined over two buffer sets and a copy
+      stream), the plain FP64 GPU path on a sub-sample of the same blocks
+      (per-pair cost, so the ratio holds for the whole build), the
+      accelerated sum of Eq. 3/4 on the whole 256-atom-sized workload,
+      per-kernel device times (roofline) and the FP64 oracle on host cores
+      (cpu_baseline, rank 0 only); the 64-atom-sized build (N_G = 2500) with
+      its dielectric, quadrature and COH studies under "c2_64atom".
+  --impl reference: the FP64 oracle on host cores, one bounded sample of the
+      same workload per step.
 Multi-GPU: N independent replicas (the build of one q-point is one unit of
 work; there is no data-path collective), max time over ranks.
 """
@@ -40,8 +51,22 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "chi0 build time + effective TFLOP/s, mixed vs FP64 GPU path at ≤1e-6 rel error"
-WORKLOAD = ("64-atom-MgO-sized chi0, full band sum (Eq. 1): N_v=128, N_c=6000, grid 48^3, "
-            "N_G=2500, one q=(0.001,0,0) bohr^-1, omega = 0 + 8 imaginary (0.01-2 Ha), delta=1e-3 Ha")
+C5_BLOCK_BANDS = 16          # conduction bands per 8192-pair block at 512 valence bands
+
+
+def c5_workload(n_blocks: int) -> str:
+    return ("256-atom-MgO-sized chi0, full band sum (Eq. 1): N_v=512, N_c=20000, grid 96^3, N_G=8000, one "
+            "q=(0.001,0,0) bohr^-1, omega = 0 + 8 imaginary (0.01-2 Ha), delta=1e-3 Ha; one step = "
+            f"{n_blocks} of the 1250 conduction blocks of 16 bands (seeded sample, "
+            f"{n_blocks * C5_BLOCK_BANDS} bands, {512 * n_blocks * C5_BLOCK_BANDS} pairs)")
+
+
+def c5_sample_bands(n_c: int, n_blocks: int, seed: int) -> np.ndarray:
+    """Conduction bands of a fixed, seeded sample of n_blocks blocks of 16
+    consecutive bands (the build's own block structure), in ascending order."""
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(n_c // C5_BLOCK_BANDS, size=n_blocks, replace=False))
+    return (pick[:, None] * C5_BLOCK_BANDS + np.arange(C5_BLOCK_BANDS)[None, :]).reshape(-1)
 
 
 # ---------------------------------------------------------------------------
@@ -172,16 +197,48 @@ def algorithmic_flops(nG: int, n_pairs: int, n_freq: int) -> float:
 # ---------------------------------------------------------------------------
 # the oracle on host cores (cpu_baseline / reference arm)
 # ---------------------------------------------------------------------------
-def h2_products(Ev, Ec, omega, delta, n_prod):
-    """Products of the H2 part per frequency in Hermitian mode: three where
-    |Im f_p| <= 2^-6 |Re f_p| for every pair (then the block maxima the library
-    compares satisfy the same bound), otherwise n_prod (an upper bound)."""
+def h2_products(Ev, Ec, omega, delta, n_prod, precision):
+    """Products of the H2 part per frequency in Hermitian mode, as the library
+    decides them per block: three where |Im f_p| <= 2^-6 |Re f_p| for every
+    pair (then the block maxima the library compares satisfy the same bound),
+    otherwise n_prod (an upper bound)."""
     dE = (np.asarray(Ev)[:, None] - np.asarray(Ec)[None, :]).reshape(-1)
     out = []
     for om in np.atleast_1d(omega):
         f = 1.0 / (dE - om + 1j * delta) + 1.0 / (dE + om + 1j * delta)
-        out.append(3 if np.all(np.abs(f.imag) <= np.abs(f.real) * 2.0 ** -6) else n_prod)
+        small = bool(np.all(np.abs(f.imag) <= np.abs(f.real) * 2.0 ** -6))
+        out.append(3 if small else n_prod)
     return np.array(out)
+
+
+def alu_peaks():
+    """Measured FP32 and FP64 FMA throughput of this GPU (chi0_peak_fma, best of
+    three launches) with the SM clock sampled meanwhile."""
+    import ctypes as C
+    import torch
+    import paper_1601_06767_gb300 as pkg
+    lib = pkg.lib()
+    out = {}
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for kind, name, iters in ((0, "fp32_tflops", 16384), (1, "fp64_tflops", 512)):
+            best = 0.0
+            for _ in range(4):                  # the first launch is a warm-up
+                ms, fl = C.c_double(0.0), C.c_double(0.0)
+                st = lib.chi0_peak_fma(kind, iters, C.byref(ms), C.byref(fl), None)
+                if st != 0:
+                    raise RuntimeError(lib.chi0_last_error(None))
+                best = max(best, fl.value / (ms.value / 1e3) / 1e12)
+            out[name] = best
+    out["clocks"] = clk.summary()
+    out["how"] = "chi0_peak_fma: 8 CTAs x 256 threads per SM, 8 independent FMA chains per thread, best of 3"
+    return out
+
+
+def run_peaks(args):
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps({"case": "peaks", **alu_peaks()}))
+    return 0
 
 
 def coh_study(pkg, prob, plan, chi, psi_v, psi_c, dev, n_t=4):
@@ -364,13 +421,50 @@ def dielectric(args, pkg, prob, plan, chi, chi_a, dev):
     return out
 
 
-def oracle_sample(prob, nv: int, nc: int, seed_offset: int = 0):
-    """Time the FP64 oracle on nv x nc pairs of the workload (wavefunctions,
-    pair elements, factors, contraction).  Returns (seconds, flops, chi, bands)."""
-    import numpy as np
+
+
+def tc_tiles(nG: int, herm: bool, cta_pair: bool) -> int:
+    """Output tiles (of 128 x 128 elements, 256 x 128 for CTA pairs) one
+    frequency of the tensor-core contraction computes: all tiles of the padded
+    sphere, or the ones on or above the diagonal in Hermitian mode."""
+    rows = 256 if cta_pair else 128
+    nGp = (nG + rows - 1) // rows * rows
+    TM, TN = nGp // rows, nGp // 128
+    return (TN // TM) * TM * (TM + 1) // 2 if herm else TM * TN
+
+
+def contraction_roofline(prof, alg_flops, pairs, n_prod, n2, nG, nf, herm, cta_pair, traffic, note):
+    """Roofline line of k_contract_tc from the launches timed over the region:
+    frac = algorithmic flops (8 N_G^2 per pair and frequency) per launch over
+    the average launch time, against the measured sustained bf16 peak (fp16
+    runs at the same dense rate); the tensor-pipe figures count every MMA the
+    kernel issues (split products, padded and mirrored tiles)."""
+    pk, pk_kind = peaks()
+    peak = pk.get("bf16_tflops_sustained", 1700.0)
+    tc_ms, tc_n = prof["contract_tc"]
+    tc_n = max(tc_n, 1)
+    avg_s = tc_ms / 1e3 / tc_n
+    elems = tc_tiles(nG, herm, cta_pair) * (256 if cta_pair else 128) * 128
+    # per pair and frequency: products x 4 real products x 2 flops x computed elements
+    prods = (np.asarray(n_prod) + (np.asarray(n2) if herm else 0)).astype(np.float64)
+    tensor_total = float(np.sum(prods * 8.0 * elems * pairs))
+    alg_launch = alg_flops / tc_n
+    ach = alg_launch / avg_s / 1e12
+    t_ach = tensor_total / tc_n / avg_s / 1e12
+    return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": traffic, "kernel": "k_contract_tc", "peak_source": f"{pk_kind} bf16_tflops_sustained",
+            "flops_per_launch": alg_launch, "flops_kind": "algorithmic, 8 N_G^2 per pair and frequency",
+            "launches": tc_n, "avg_launch_ms": avg_s * 1e3,
+            "tensor_pipe": {"flops_per_launch": tensor_total / tc_n, "achieved": t_ach, "frac": t_ach / peak,
+                            "products_per_frequency": [int(x) for x in np.atleast_1d(prods)] if herm else int(n_prod),
+                            "hermitian": herm, "cta_pair": bool(cta_pair)},
+            "note": note}
+
+
+def oracle_sample(prob, vb, cb):
+    """Time the FP64 oracle on the pairs vb x cb of the workload (wavefunctions,
+    pair elements, factors, contraction).  Returns (seconds, flops, chi, coefficients)."""
     from oracle import chi0_from_pairs, freq_factor, pair_elements, wfn_to_grid
-    vb = (np.arange(nv) + seed_offset * nv) % prob.n_v
-    cb = (np.arange(nc) * 37 + seed_offset * 11) % prob.n_c
     cv, cc = prob.coeff_v(0, vb), prob.coeff_c(cb)
     t0 = time.perf_counter()
     uv, uc = wfn_to_grid(cv, prob.gw, prob.n), wfn_to_grid(cc, prob.gw, prob.n)
@@ -379,7 +473,10 @@ def oracle_sample(prob, nv: int, nc: int, seed_offset: int = 0):
     chi = chi0_from_pairs(M, freq_factor(dE, np.ones_like(dE), prob.omega, prob.delta))
     dt = time.perf_counter() - t0
     nG = prob.gvec[0].shape[0]
-    return dt, algorithmic_flops(nG, nv * nc, prob.omega.size), chi, (vb, cb, cv, cc)
+    return dt, algorithmic_flops(nG, vb.size * cb.size, prob.omega.size), chi, (cv, cc)
+
+
+REF_NV, REF_NC = 2, 8          # pairs per step of the reference arm (256-atom-sized workload)
 
 
 def run_reference(args):
@@ -387,23 +484,31 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    prob = make_problem("c2")
-    nv, nc = 8, 64          # the cpu_baseline sample of the GPU arm
+    prob = make_problem("c5")
+    bands = c5_sample_bands(prob.n_c, args.c5_blocks, prob.seed + 5)
+
+    def sample(k):
+        vb = (np.arange(REF_NV) * 97 + 13 * k) % prob.n_v
+        cb = bands[(np.arange(REF_NC) * 23 + 7 * k) % bands.size]
+        return vb, np.sort(cb)
+
     for w in range(args.warmup):
-        oracle_sample(prob, nv, nc, w)
+        oracle_sample(prob, *sample(w))
     secs, flops = 0.0, 0.0
     for k in range(args.steps):
-        dt, fl, _, _ = oracle_sample(prob, nv, nc, args.warmup + k)
+        dt, fl, chi, _ = oracle_sample(prob, *sample(args.warmup + k))
+        del chi
         secs += dt
         flops += fl
     value = flops / secs / 1e12
     cores = os.cpu_count()
+    desc = f"{REF_NV} valence x {REF_NC} conduction bands of the benchmark's sampled blocks per step"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_per_step": f"{nv}x{nc} pairs"},
-            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{nv} valence x {nc} conduction bands per step (of 128 x 6000)"},
+            "data": "synthetic", "config": {"workload": c5_workload(args.c5_blocks),
+                                            "sample_per_step": f"{REF_NV}x{REF_NC} pairs"},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -411,7 +516,6 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------
 def run_ours(args):
-    import numpy as np
     import torch
 
     import paper_1601_06767_gb300 as pkg
@@ -422,17 +526,18 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     if world > 1:
         dist_init("nccl")
-    prob = make_problem("c2")
+    prob = make_problem("c5")
     nG, nf = prob.gvec[0].shape[0], prob.omega.size
-    n_pairs = prob.n_v * prob.n_c
+    bands = c5_sample_bands(prob.n_c, args.c5_blocks, prob.seed + 5)
+    n_pairs = prob.n_v * bands.size
     F = algorithmic_flops(nG, n_pairs, nf)
 
     t0 = time.time()
-    cv_h = torch.from_numpy(prob.coeff_v(0)).pin_memory()
-    cc_h = torch.from_numpy(prob.coeff_c()).pin_memory()
+    cv_h = _threaded_coeff(prob, 1, np.arange(prob.n_v))
+    cc_h = _threaded_coeff(prob, 0, bands)
     gen_s = time.time() - t0
     Ev_h = torch.from_numpy(prob.E_v).pin_memory()
-    Ec_h = torch.from_numpy(prob.E_c).pin_memory()
+    Ec_h = torch.from_numpy(prob.E_c[bands].copy()).pin_memory()
     cv, cc = cv_h.to(dev), cc_h.to(dev)
     Ev, Ec = Ev_h.to(dev), Ec_h.to(dev)
 
@@ -441,7 +546,7 @@ def run_ours(args):
                         n_products=args.n_products, hermitian=herm)
     tuning = plan.autotune(0)
     psi_v = torch.empty((prob.n_v,) + plan.n, dtype=plan.cdtype, device=dev)
-    psi_c = torch.empty((prob.n_c,) + plan.n, dtype=plan.cdtype, device=dev)
+    psi_c = torch.empty((bands.size,) + plan.n, dtype=plan.cdtype, device=dev)
     chi = plan.new_chi(0)
 
     def step():
@@ -475,11 +580,10 @@ def run_ours(args):
     launches = sum(c for _, c in prof.values())
 
     # ---- e2e: host buffers, every step's copies inside the timed region ----
-    # Pipelined through the public API: inputs and chi0 are double-buffered and
-    # the copies run on a second stream, so step i+1's upload and step i's
-    # download overlap neighbouring builds; the region runs from the first
-    # upload to the last download.
-    n_e2e = max(1, min(args.steps, 3))
+    # Through the public API with inputs and chi0 double-buffered and the copies
+    # on a second stream: step i+1's upload and step i's chi0 download overlap
+    # the neighbouring builds; the region runs from the first upload to the
+    # last download, over as many steps as the timed region.
     chi_h = [torch.empty(chi.shape, dtype=chi.dtype).pin_memory() for _ in range(2)]
     ins = [(cv, cc, Ev, Ec), tuple(torch.empty_like(t) for t in (cv, cc, Ev, Ec))]
     chis = [chi, torch.empty_like(chi)]
@@ -517,19 +621,202 @@ def run_ours(args):
     barrier(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    run_e2e(n_e2e)
+    run_e2e(args.steps)
     e1.record()
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks(e0.elapsed_time(e1) / n_e2e / 1e3, dev)
+    plan.sync_status()
+    e2e_s = max_over_ranks(e0.elapsed_time(e1) / args.steps / 1e3, dev)
     h2d = cv_h.nbytes + cc_h.nbytes + Ev_h.nbytes + Ec_h.nbytes
     d2h = chi_h[0].nbytes
-    # the downloaded result is the build's chi0
-    assert torch.equal(chi_h[(n_e2e - 1) % 2], chis[(n_e2e - 1) % 2].cpu())
-    del chis[1], ins[1]
+    last = (args.steps - 1) % 2
+    assert torch.equal(chi_h[last], chis[last].cpu())     # the downloaded result is the build's chi0
+    del chis[1], ins[1], chi_h
 
-    # ---- accelerated sum (Eq. 3/4) on the same workload ----
-    # Eq. 3/4 needs the wavefunctions of the selected bands only: those (each
-    # once) are the step's conduction input, c_idx maps columns onto them
+    # ---- plain FP64 GPU path on a sub-sample of the same blocks ----
+    fp64 = None
+    if not args.no_fp64:
+        plan64 = pkg.Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision="fp64", gw=prob.gw,
+                              max_pairs=1024)
+        nc_s = args.fp64_sample
+        psi_v64 = plan64.wfn_to_grid(cv)
+        cc64 = cc[:nc_s].contiguous()
+        psi_c64 = plan64.wfn_to_grid(cc64)
+        chi64 = plan64.new_chi(0)
+        plan64.build(0, psi_v64, Ev, psi_c64, Ec[:nc_s].contiguous(), chi=chi64)     # warm-up
+        torch.cuda.synchronize()
+        e0.record()
+        plan64.wfn_to_grid(cc64, out=psi_c64)
+        chi64.zero_()
+        plan64.build(0, psi_v64, Ev, psi_c64, Ec[:nc_s].contiguous(), chi=chi64)
+        e1.record()
+        torch.cuda.synchronize()
+        plan64.sync_status()
+        s_ms = e0.elapsed_time(e1)
+        e0.record()
+        plan64.wfn_to_grid(cv, out=psi_v64)
+        e1.record()
+        torch.cuda.synchronize()
+        step64_s = (s_ms * bands.size / nc_s + e0.elapsed_time(e1)) / 1e3
+        fp64 = {"step_s_extrapolated": step64_s, "value_tflops": F / step64_s / 1e12,
+                "build_s_extrapolated": step64_s * prob.n_c / bands.size,
+                "sample": f"all 512 valence x {nc_s} conduction bands of the first sampled block timed, "
+                          f"scaled linearly to the step's {bands.size} bands (cost is linear in the pairs)",
+                "mixed_speedup": step64_s / (ms_step / 1e3)}
+        del plan64, psi_v64, psi_c64, chi64, cc64
+
+    # ---- accelerated sum of Eq. 3/4 on the whole 256-atom-sized workload ----
+    accel = None
+    if not args.no_accel:
+        c_sel, E_sel, w_sel = pkg.select_accelerated(prob.E_c, prob.N0, prob.dE, prob.dos_A, prob.dos_V0,
+                                                     prob.E_max)
+        c_uniq, c_inv = np.unique(c_sel, return_inverse=True)
+        cc_sel = _threaded_coeff(prob, 0, c_uniq).to(dev)
+        psi_sel = plan.wfn_to_grid(cc_sel)
+        c_idx = torch.from_numpy(c_inv.astype(np.int32)).to(dev)
+        Ecol, wcol = torch.from_numpy(E_sel).to(dev), torch.from_numpy(w_sel).to(dev)
+        chi.zero_()
+        torch.cuda.synchronize()
+        e0.record()
+        plan.wfn_to_grid(cv, out=psi_v)
+        plan.wfn_to_grid(cc_sel, out=psi_sel)
+        plan.build(0, psi_v, Ev, psi_sel, Ecol, w_col=wcol, c_idx=c_idx, chi=chi)
+        e1.record()
+        torch.cuda.synchronize()
+        plan.sync_status()
+        acc_s = e0.elapsed_time(e1) / 1e3
+        full_s = ms_step / 1e3 * prob.n_c / bands.size
+        accel = {"build_s": acc_s, "columns": int(c_sel.size), "bands_transformed": int(c_uniq.size),
+                 "pairs": prob.n_v * int(c_sel.size), "N0": prob.N0, "dE_eV": 2.0,
+                 "pair_ratio": prob.n_c / c_sel.size, "speedup_vs_full_build": full_s / acc_s}
+        del cc_sel, psi_sel
+
+    # ---- roofline of the dominant kernel (tensor-core contraction) ----
+    n_prod = {"fp16": 3, "bf16": 6}[args.precision] if args.n_products == 0 else args.n_products
+    n2 = h2_products(prob.E_v, prob.E_c[bands], prob.omega, prob.delta, n_prod, args.precision)
+    traffic = profiled_traffic("paper_1601_06767_gb300/csrc/kern_tc.cu", f"contract_tc_c5_{args.precision}.md")
+    roof = contraction_roofline(prof, F * args.steps, n_pairs * args.steps, n_prod, n2, nG, nf, plan.hermitian,
+                                tuning["cta_pair"], traffic,
+                                "launch durations inside the pipelined build: the last wave of each launch "
+                                "shares the GPU with the next block's pair stage")
+    kernel_ms = {k: round(v[0] / args.steps, 3) for k, v in prof.items()}
+    full_build_s = ms_step / 1e3 * prob.n_c / bands.size
+
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": c5_workload(args.c5_blocks), "pairs_per_step": n_pairs, "n_freq": nf,
+                       "sampled_conduction_bands": int(bands.size), "sample_fraction": bands.size / prob.n_c,
+                       "full_build_s_extrapolated": full_build_s,
+                       "precision": f"{args.precision} split x{n_prod} products, FP32 TMEM chains of "
+                                    f"32 pairs, FP64 factors and merge"
+                                    + ("; Hermitian parts H1 + i H2 on the upper triangle" if plan.hermitian else ""),
+                       "l2": "no flush: resident inputs and chi0 (about 15 GB) exceed the 129 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "kernel_ms_per_step": kernel_ms,
+            "kernel_ms_note": "CUDA-event time per kernel family; the build pipelines conduction blocks, "
+                              "the pair stage, factors and packing of block k+1 running on a second stream "
+                              "beside the contraction of block k, so those families' event times include "
+                              "waiting for SMs and the families overlap (their sum exceeds ms_per_step)",
+            "gpu_launches": launches,
+            "e2e": {"value": replica_value(F, world, e2e_s) / 1e12, "unit": "TFLOP/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
+                    "steps": args.steps},
+            "fp64_gpu": fp64, "accelerated": accel, "tuning": tuning, "clocks": clk.summary(),
+            "input_gen_s": gen_s}
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline_c5(prob, plan, psi_v, Ev, bands, dev)
+    line["alu_peaks"] = alu_peaks()
+    del plan, chi, psi_v, psi_c, cv, cc
+    torch.cuda.empty_cache()
+    if not args.no_c2:
+        line["c2_64atom"] = c2_study(args, pkg, dev, world)
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def cpu_baseline_c5(prob, plan, psi_v, Ev, bands, dev, nv=4, nc=16, rows=256):
+    """The oracle on host cores on a bounded sample of the workload (nv valence
+    x nc conduction bands of the sampled blocks, all 9 frequencies), plus the
+    GPU result on the same pairs for a parity figure (rows 0..rows-1 of chi0)."""
+    import torch
+    from oracle import rel_fro
+    vb = np.arange(nv) * (prob.n_v // nv)
+    cb = np.sort(bands[np.linspace(0, bands.size - 1, nc).round().astype(np.int64)])
+    dt, fl, chi_ref, (cv, cc) = oracle_sample(prob, vb, cb)
+    ref_rows = np.ascontiguousarray(chi_ref[:, :rows])
+    del chi_ref
+    psi_c = plan.wfn_to_grid(torch.from_numpy(cc).to(dev))
+    vi = torch.from_numpy(vb.astype(np.int32)).to(dev)
+    M = plan.pairs(0, psi_v, psi_c, v_idx=vi)
+    chi = plan.accumulate(0, M, nv, nc, Ev[vi.long()].contiguous(), torch.from_numpy(prob.E_c[cb]).to(dev))
+    got = chi[:, :rows].cpu().numpy()
+    del chi, M, psi_c
+    err = max(rel_fro(got[i], ref_rows[i]) for i in range(got.shape[0]))
+    emax = max(float(np.max(np.abs(got[i] - ref_rows[i])) / np.max(np.abs(ref_rows[i]))) for i in range(got.shape[0]))
+    return {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{nv} valence x {nc} conduction bands ({nv * nc} pairs) of the sampled blocks, all 9 "
+                      "frequencies, N_G = 8000 (wavefunctions, pair elements, factors, contraction)",
+            "seconds": dt, "parity_rows": rows, "parity_rel_fro_max_over_omega": err,
+            "parity_rel_max_elem_max_over_omega": emax}
+
+
+def c2_study(args, pkg, dev, world):
+    """The 64-atom-sized build (N_v 128, N_c 6000, 48^3, N_G 2500, 9 frequencies)
+    with the studies that use its chi0: accelerated sum, dielectric matrix,
+    quadrature variants, COH self-energy, the other split precision and the
+    FP64 path on a sample."""
+    import torch
+    from synth import make_problem
+    prob = make_problem("c2")
+    nG, nf = prob.gvec[0].shape[0], prob.omega.size
+    n_pairs = prob.n_v * prob.n_c
+    F = algorithmic_flops(nG, n_pairs, nf)
+    cv = _threaded_coeff(prob, 1, np.arange(prob.n_v)).to(dev)
+    cc = _threaded_coeff(prob, 0, np.arange(prob.n_c)).to(dev)
+    Ev, Ec = torch.from_numpy(prob.E_v).to(dev), torch.from_numpy(prob.E_c).to(dev)
+    prec = args.c2_precision
+    plan = pkg.Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision=prec, gw=prob.gw)
+    tuning = plan.autotune(0)
+    psi_v = torch.empty((prob.n_v,) + plan.n, dtype=plan.cdtype, device=dev)
+    psi_c = torch.empty((prob.n_c,) + plan.n, dtype=plan.cdtype, device=dev)
+    chi = plan.new_chi(0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(plan_, chi_, steps):
+        def step():
+            plan_.wfn_to_grid(cv, out=psi_v)
+            plan_.wfn_to_grid(cc, out=psi_c)
+            chi_.zero_()
+            plan_.build(0, psi_v, Ev, psi_c, Ec, chi=chi_)
+        step()
+        torch.cuda.synchronize()
+        plan_.profile(True)
+        plan_.profile_reset()
+        e0.record()
+        for _ in range(steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        plan_.sync_status()
+        pr = plan_.profile_read()
+        plan_.profile(False)
+        return e0.elapsed_time(e1) / steps, pr
+
+    ms, prof = timed(plan, chi, args.c2_steps)
+    n_prod = {"fp16": 3, "bf16": 6}[prec]
+    n2 = h2_products(prob.E_v, prob.E_c, prob.omega, prob.delta, n_prod, prec)
+    roof = contraction_roofline(prof, F * args.c2_steps, n_pairs * args.c2_steps, n_prod, n2, nG, nf,
+                                plan.hermitian, tuning["cta_pair"],
+                                profiled_traffic("paper_1601_06767_gb300/csrc/kern_tc.cu", f"contract_tc_c2_{prec}.md"),
+                                "inside the pipelined build")
+    out = {"workload": ("64-atom-MgO-sized chi0, full band sum (Eq. 1): N_v=128, N_c=6000, grid 48^3, N_G=2500, "
+                        "omega = 0 + 8 imaginary"),
+           "precision": prec, "ms_per_build": ms, "value_tflops": F / (ms / 1e3) / 1e12, "steps": args.c2_steps,
+           "roofline": roof, "tuning": tuning,
+           "kernel_ms_per_build": {k: round(v[0] / args.c2_steps, 3) for k, v in prof.items()}}
+
+    # accelerated sum (Eq. 3/4): transforms only the bands its columns select
     c_sel, E_sel, w_sel = pkg.select_accelerated(prob.E_c, prob.N0, prob.dE, prob.dos_A, prob.dos_V0, prob.E_max)
     c_uniq, c_inv = np.unique(c_sel, return_inverse=True)
     cc_sel = cc.index_select(0, torch.from_numpy(c_uniq.astype(np.int64)).to(dev)).contiguous()
@@ -551,52 +838,30 @@ def run_ours(args):
         step_acc()
     e1.record()
     torch.cuda.synchronize()
-    acc_ms = e0.elapsed_time(e1) / 3
     plan.sync_status()
-    acc_pairs = prob.n_v * len(c_sel)
-
-    # ---- dielectric matrix of both builds: eps = 1 - v chi0 (symmetrised), eps^-1, eps_inf ----
-    eps_info = None if args.no_eps else dielectric(args, pkg, prob, plan, chi, chi_a, dev)
+    acc_ms = e0.elapsed_time(e1) / 3
+    out["accelerated"] = {"ms": acc_ms, "pairs": prob.n_v * len(c_sel), "columns": len(c_sel),
+                          "bands_transformed": int(c_uniq.size), "pair_ratio": prob.n_c / len(c_sel),
+                          "speedup_vs_full": ms / acc_ms, "N0": prob.N0, "dE_eV": 2.0}
+    if not args.no_eps:
+        out["dielectric"] = dielectric(args, pkg, prob, plan, chi, chi_a, dev)
     del chi_a, psi_sel, cc_sel
-
-    # ---- quadrature variants of the accelerated sum: error against the full sum vs cost ----
-    quad_info = None if args.no_quad else quadrature_study(pkg, prob, plan, chi, psi_v, psi_c, Ev, cv, cc, dev)
-
-    # ---- COH self-energy (Eq. 2, plasmon-pole model): full and accelerated band sums ----
-    coh_info = None if args.no_coh else coh_study(pkg, prob, plan, chi, psi_v, psi_c, dev)
-
-    # ---- the other split precision on the same build (reported beside the headline) ----
-    variants = {}
+    if not args.no_quad:
+        out["quadrature"] = quadrature_study(pkg, prob, plan, chi, psi_v, psi_c, Ev, cv, cc, dev)
+    if not args.no_coh:
+        out["coh"] = coh_study(pkg, prob, plan, chi, psi_v, psi_c, dev)
+    del plan
     if not args.no_variants:
-        other = "fp16" if args.precision == "bf16" else "bf16"
+        other = "fp16" if prec == "bf16" else "bf16"
         plan2 = pkg.Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision=other, gw=prob.gw)
         plan2.autotune(0)
-        chi2 = plan2.new_chi(0)
-
-        def step2():
-            plan2.wfn_to_grid(cv, out=psi_v)
-            plan2.wfn_to_grid(cc, out=psi_c)
-            chi2.zero_()
-            plan2.build(0, psi_v, Ev, psi_c, Ec, chi=chi2)
-
-        step2()
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(args.steps):
-            step2()
-        e1.record()
-        torch.cuda.synchronize()
-        plan2.sync_status()
-        v_ms = e0.elapsed_time(e1) / args.steps
-        variants[other] = {"ms_per_step": v_ms, "value": F / (v_ms / 1e3) / 1e12, "unit": "TFLOP/s",
-                           "precision": {"fp16": "fp16 split x3 products", "bf16": "bf16 split x6 products"}[other]}
-        del plan2, chi2
-
-    # ---- plain FP64 GPU path on a sample of conduction bands, extrapolated ----
-    fp64 = None
+        v_ms, _ = timed(plan2, chi, args.c2_steps)
+        out["variants"] = {other: {"ms_per_build": v_ms, "value_tflops": F / (v_ms / 1e3) / 1e12,
+                                   "hermitian": plan2.hermitian}}
+        del plan2
     if not args.no_fp64:
         plan64 = pkg.Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision="fp64", gw=prob.gw)
-        nc_s = args.fp64_sample
+        nc_s = 32
         idx = torch.arange(nc_s, dtype=torch.int32, device=dev)
         psi_v64 = plan64.wfn_to_grid(cv)
         psi_c64 = plan64.wfn_to_grid(cc[:nc_s].contiguous())
@@ -610,98 +875,14 @@ def run_ours(args):
         e1.record()
         torch.cuda.synchronize()
         plan64.sync_status()
-        s_ms = e0.elapsed_time(e1)
-        wfn_v0, wfn_v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        wfn_v0.record()
-        plan64.wfn_to_grid(cv, out=psi_v64)
-        wfn_v1.record()
-        torch.cuda.synchronize()
-        full_s = (s_ms * prob.n_c / nc_s + wfn_v0.elapsed_time(wfn_v1)) / 1e3
-        fp64 = {"build_s_extrapolated": full_s, "value_tflops": F / full_s / 1e12,
-                "sample": f"all 128 valence x {nc_s} conduction bands timed, scaled linearly to 6000 "
-                          "(cost is linear in the pair count)",
-                "mixed_speedup": full_s / (ms_step / 1e3)}
+        full_s = e0.elapsed_time(e1) * prob.n_c / nc_s / 1e3
+        out["fp64_gpu"] = {"build_s_extrapolated": full_s, "value_tflops": F / full_s / 1e12,
+                           "sample": f"all 128 valence x {nc_s} conduction bands, scaled linearly to 6000",
+                           "mixed_speedup": full_s / (ms / 1e3)}
         del plan64, psi_v64, psi_c64, chi64
-
-    # ---- roofline of the dominant kernel (tensor-core contraction) ----
-    pk, pk_kind = peaks()
-    n_prod = {"fp16": 3, "bf16": 6}[args.precision] if args.n_products == 0 else args.n_products
-    hermitian = plan.hermitian
-    tc_ms, tc_n = prof["contract_tc"]
-    nG = prob.gvec[0].shape[0]
-    if hermitian:
-        # H1 (n_prod products) and H2 (3 products where max|Im f| <= 2^-6 max|Re f|,
-        # which holds pair by pair here, so in every block) on the G <= G' triangle
-        n2 = h2_products(prob.E_v, prob.E_c, prob.omega, prob.delta, n_prod)
-        tensor_flops_total = (4.0 * nG * (nG + 1) * n_pairs * (n_prod + n2)).sum() * args.steps
-    else:
-        n2 = None
-        tensor_flops_total = n_prod * F * args.steps
-    # every launch contracts one block of pairs; summed over the timed steps this is
-    # (tensor flops per launch x launches) / (average launch time x launches)
-    avg_launch_s = tc_ms / 1e3 / max(tc_n, 1)
-    tensor_flops_launch = tensor_flops_total / max(tc_n, 1)
-    ach = tensor_flops_launch / avg_launch_s / 1e12
-    peak = pk.get("bf16_tflops_sustained", 1700.0)
-    traffic = profiled_traffic("paper_1601_06767_gb300/csrc/kern_tc.cu", f"contract_tc_c2_{args.precision}.md")
-    roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": traffic, "kernel": "k_contract_tc", "peak_source": f"{pk_kind} bf16_tflops_sustained",
-            "flops_per_launch": tensor_flops_launch, "launches": tc_n,
-            "algorithmic_tflops": F * args.steps / max(tc_n, 1) / avg_launch_s / 1e12,
-            "hermitian": hermitian, "h2_products": None if n2 is None else [int(x) for x in n2],
-            "note": "launch durations inside the pipelined build: the last wave of each launch shares "
-                    "the GPU with the next block's pair stage"}
-    kernel_ms = {k: round(v[0] / args.steps, 3) for k, v in prof.items()}
-
-    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "pairs": n_pairs, "n_freq": nf,
-                       "precision": f"{args.precision} split x{n_prod} products, FP32 TMEM chains of "
-                                    f"32 pairs, FP64 factors and merge"
-                                    + ("; Hermitian parts H1 + i H2 on the upper triangle" if hermitian else ""),
-                       "l2": "no flush: resident inputs (6.6 GB) exceed the 129 MB L2",
-                       "parallelism": f"replicas x{world}"},
-            "roofline": roof, "kernel_ms_per_step": kernel_ms,
-            "kernel_ms_note": "CUDA-event time per kernel family; the build pipelines conduction blocks, "
-                              "the pair stage, factors and packing of block k+1 running on a second stream "
-                              "beside the contraction of block k, so those families' event times include "
-                              "waiting for SMs and the families overlap (their sum exceeds ms_per_step)",
-            "gpu_launches": launches,
-            "e2e": {"value": replica_value(F, world, e2e_s) / 1e12, "unit": "TFLOP/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
-            "accelerated": {"ms": acc_ms, "pairs": acc_pairs, "columns": len(c_sel), "bands_transformed": int(c_uniq.size),
-                            "pair_ratio": n_pairs / acc_pairs, "speedup_vs_full": ms_step / acc_ms,
-                            "N0": prob.N0, "dE_eV": 2.0},
-            "fp64_gpu": fp64, "variants": variants, "tuning": tuning, "clocks": clk.summary(), "input_gen_s": gen_s,
-            "dielectric": eps_info, "quadrature": quad_info, "coh": coh_info}
-
-    if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(prob, plan, psi_v, psi_c, Ev, Ec)
-    del plan
-    if rank == 0:
-        print(json.dumps(line))
-    return 0
-
-
-def cpu_baseline(prob, plan, psi_v, psi_c, Ev, Ec):
-    """The oracle on host cores on a bounded sample (8 x 64 pairs), plus the
-    GPU result on the same sample for a parity figure."""
-    import numpy as np
-    import torch
-    from oracle import rel_fro
-    nv, nc = 8, 64
-    dt, fl, chi_ref, (vb, cb, cv, cc) = oracle_sample(prob, nv, nc)
-    dev = psi_v.device
-    vi = torch.from_numpy(vb.astype(np.int32)).to(dev)
-    ci = torch.from_numpy(cb.astype(np.int32)).to(dev)
-    M = plan.pairs(0, psi_v, psi_c, v_idx=vi, c_idx=ci)
-    chi = plan.accumulate(0, M, nv, nc, Ev[vi.long()].contiguous(), Ec[ci.long()].contiguous())
-    torch.cuda.synchronize()
-    err = max(rel_fro(chi[i].cpu().numpy(), chi_ref[i]) for i in range(chi.shape[0]))
-    return {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{nv} valence x {nc} conduction bands ({nv * nc} of 768000 pairs), all 9 frequencies",
-            "seconds": dt, "parity_rel_fro_max_over_omega": err}
+    del chi, psi_v, psi_c, cv, cc
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_case(args):
@@ -710,13 +891,20 @@ def run_case(args):
     frequencies; 'pairs' = two pair-element calls of 128 x 64 pairs on 48^3;
     'wfn' = two grid transforms of 512 conduction bands on 48^3;
     'eps' = two dielectric inverses of 9 matrices of the 2500-vector sphere;
-    'coh' = plasmon-pole parameters and COH sums (4 targets x 663 bands)."""
+    'coh' = plasmon-pole parameters and COH sums (4 targets x 663 bands);
+    'contract5' / 'pairs5' = the same on the 256-atom-sized sphere (N_G 8000,
+    8192 = 512 x 16 pairs per call, 96^3 grid) with omega = 0 and one imaginary
+    frequency, so that a capture holds a few GB (per-launch counters scale to the
+    benchmark's 9 frequencies by 9/2)."""
     import torch
     import paper_1601_06767_gb300 as pkg
     from synth import make_problem
-    prob = make_problem("c2")
+    big = args.case in ("contract5", "pairs5")
+    prob = make_problem("c5", n_imag=1) if big else make_problem("c2")
     nG = prob.gvec[0].shape[0]
-    K, nv, nc = 8192, 128, 64
+    K, nv, nc = (8192, 512, 16) if big else (8192, 128, 64)
+    if big:
+        args.case = args.case[:-1]
     g = torch.Generator(device="cuda")
     g.manual_seed(0)
     herm = {"auto": None, "on": True, "off": False}[args.hermitian]
@@ -794,117 +982,6 @@ def _threaded_coeff(prob, stream: int, bands, workers: int = 16):
     return out
 
 
-def run_c5(args):
-    """256-atom-MgO-sized workload: the split path (full Eq. 1 sum and Eq. 3/4),
-    conduction bands streamed in blocks from host-generated coefficients; the
-    FP64 path on a sample, extrapolated; parity of a pair sample vs the oracle."""
-    import threading
-    import numpy as np
-    import torch
-    import paper_1601_06767_gb300 as pkg
-    from oracle import chi0_from_pairs, freq_factor, pair_elements, rel_fro, wfn_to_grid
-    from synth import make_problem
-
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    prob = make_problem("c5")
-    nG, nf = prob.gvec[0].shape[0], prob.omega.size
-    n_c_run = max(1, int(round(prob.n_c * args.c5_frac)))
-    CB = 512
-    t0 = time.time()
-    cv = _threaded_coeff(prob, 1, np.arange(prob.n_v)).to(dev)
-    Ev = torch.from_numpy(prob.E_v).to(dev)
-    Ec_all = torch.from_numpy(prob.E_c).to(dev)
-    plan = pkg.Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision=args.precision, gw=prob.gw,
-                        n_products=args.n_products, max_pairs=8192)
-    psi_v = plan.wfn_to_grid(cv)
-    chi = plan.new_chi(0)
-    psi_c = torch.empty((CB,) + plan.n, dtype=plan.cdtype, device=dev)
-
-    def stream_build(bands, E_cols, w_cols, chi_out):
-        """wavefunctions + build for conduction bands `bands` (host-generated, prefetched)."""
-        blocks = [bands[i:i + CB] for i in range(0, len(bands), CB)]
-        box = {}
-
-        def gen(k):
-            box[k] = _threaded_coeff(prob, 0, blocks[k])
-
-        th = threading.Thread(target=gen, args=(0,))
-        th.start()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        wall0 = time.time()
-        e0.record()
-        for k, blk in enumerate(blocks):
-            th.join()
-            host = box.pop(k)
-            if k + 1 < len(blocks):
-                th = threading.Thread(target=gen, args=(k + 1,))
-                th.start()
-            cc = host.to(dev, non_blocking=True)
-            out = psi_c[:len(blk)]
-            plan.wfn_to_grid(cc, out=out)
-            sl = slice(k * CB, k * CB + len(blk))
-            plan.build(0, psi_v, Ev, out, E_cols[sl].contiguous(),
-                       w_col=None if w_cols is None else w_cols[sl].contiguous(), chi=chi_out)
-        e1.record()
-        torch.cuda.synchronize()
-        plan.sync_status()
-        return e0.elapsed_time(e1) / 1e3, time.time() - wall0
-
-    # warm-up on one small block
-    stream_build(np.arange(64), Ec_all, None, chi)
-    chi.zero_()
-    full_s, full_wall = stream_build(np.arange(n_c_run), Ec_all, None, chi)
-    scale = prob.n_c / n_c_run
-    F = algorithmic_flops(nG, prob.n_v * prob.n_c, nf)
-    # accelerated sum of Eq. 3/4
-    c_sel, E_sel, w_sel = pkg.select_accelerated(prob.E_c, prob.N0, prob.dE, prob.dos_A, prob.dos_V0, prob.E_max)
-    chi_a = chi  # reuse the buffer
-    chi_a.zero_()
-    acc_s, _ = stream_build(c_sel.astype(np.int64), torch.from_numpy(E_sel).to(dev), torch.from_numpy(w_sel).to(dev),
-                            chi_a)
-    # parity on a pair sample (rows of chi0 limited to the first 400 sphere vectors)
-    vb, cb = np.arange(2), np.array([0, 7001, 13002, 19999])
-    cvs, ccs = prob.coeff_v(0, vb), prob.coeff_c(cb)
-    ref_M = pair_elements(wfn_to_grid(cvs, prob.gw, prob.n), wfn_to_grid(ccs, prob.gw, prob.n), prob.gvec[0], prob.n)
-    dE = (prob.E_v[vb][:, None] - prob.E_c[cb][None, :]).reshape(-1)
-    fq = freq_factor(dE, np.ones_like(dE), prob.omega, prob.delta)
-    rows = 400
-    ref = np.stack([(ref_M[:, :rows].T * fq[i][None, :]) @ ref_M.conj() for i in range(nf)])
-    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    psv = plan.wfn_to_grid(d(cvs))
-    psc = plan.wfn_to_grid(d(ccs))
-    Mg = plan.pairs(0, psv, psc)
-    chi_s = plan.accumulate(0, Mg, 2, 4, d(prob.E_v[vb]), d(prob.E_c[cb]))
-    torch.cuda.synchronize()
-    par = max(rel_fro(chi_s[i, :rows].cpu().numpy(), ref[i]) for i in range(nf))
-    del chi, chi_a, chi_s, psi_c
-    # FP64 path on a sample: all valence bands x 2 conduction bands
-    plan64 = pkg.Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision="fp64", gw=prob.gw, max_pairs=1024)
-    pv64 = plan64.wfn_to_grid(cv)
-    cc64 = d(prob.coeff_c(np.arange(2)))
-    pc64 = plan64.wfn_to_grid(cc64)
-    chi64 = plan64.new_chi(0)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    plan64.build(0, pv64, Ev, pc64, Ec_all[:2].contiguous(), chi=chi64)
-    e1.record()
-    torch.cuda.synchronize()
-    plan64.sync_status()
-    fp64_s = e0.elapsed_time(e1) / 1e3 * prob.n_c / 2
-    line = {"case": "c5", "workload": ("256-atom-MgO-sized chi0: N_v=512, N_c=20000, grid 96^3, N_G=8000, "
-                                         "omega = 0 + 8 imaginary; conduction bands streamed in blocks of 512"),
-            "precision": args.precision, "timed_conduction_bands": n_c_run,
-            "full": {"build_s": full_s * scale, "extrapolated": n_c_run < prob.n_c, "wall_s": full_wall * scale,
-                     "effective_tflops": F / (full_s * scale) / 1e12},
-            "accelerated": {"build_s": acc_s, "columns": len(c_sel), "pairs": prob.n_v * len(c_sel),
-                            "speedup_vs_full": full_s * scale / acc_s},
-            "fp64_gpu": {"build_s_extrapolated": fp64_s, "sample": "512 valence x 2 conduction bands",
-                         "effective_tflops": F / fp64_s / 1e12},
-            "mixed_vs_fp64": fp64_s / (full_s * scale),
-            "parity_sample_rel_fro": par, "input_gen_s": time.time() - t0}
-    print(json.dumps(line))
-    return 0
 
 
 def run_c3(args):
@@ -1043,35 +1120,44 @@ def run_c4(args):
     return 0
 
 
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["bf16", "fp16"], default="bf16")
+    ap.add_argument("--precision", choices=["bf16", "fp16"], default="fp16",
+                    help="split precision of the headline (256-atom-sized) build")
     ap.add_argument("--n-products", type=int, default=0)
     ap.add_argument("--hermitian", choices=["auto", "on", "off"], default="auto")
+    ap.add_argument("--c5-blocks", type=int, default=12,
+                    help="conduction blocks (16 bands, 8192 pairs) of the 256-atom-sized workload per step")
+    ap.add_argument("--c2-precision", choices=["bf16", "fp16"], default="bf16",
+                    help="split precision of the 64-atom-sized build")
+    ap.add_argument("--c2-steps", type=int, default=3)
     ap.add_argument("--no-tune", action="store_true",
                     help="--case contract: keep the plan's default tiles (CHI0_TC_PAIR picks the variant)")
-    ap.add_argument("--fp64-sample", type=int, default=32)
+    ap.add_argument("--fp64-sample", type=int, default=2,
+                    help="conduction bands of the FP64 GPU path's sample (with all 512 valence bands)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-accel", action="store_true", help="skip the accelerated 256-atom-sized build")
+    ap.add_argument("--no-c2", action="store_true", help="skip the 64-atom-sized build and its studies")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-eps", action="store_true", help="skip the dielectric-matrix measurement")
     ap.add_argument("--no-quad", action="store_true", help="skip the quadrature variants of Eq. 3")
     ap.add_argument("--no-coh", action="store_true", help="skip the COH self-energy measurement")
-    ap.add_argument("--case", choices=["contract", "pairs", "wfn", "eps", "coh", "c3", "c4", "c5"], default=None,
-                    help="run a small fixed case for profiling (contract, pairs) or the 256-atom-sized "
-                         "measurement (c5) instead of the benchmark")
-    ap.add_argument("--c5-frac", type=float, default=1.0, help="fraction of conduction bands timed in --case c5")
+    ap.add_argument("--case", choices=["contract", "contract5", "pairs", "wfn", "eps", "coh", "c3", "c4", "peaks"],
+                    default=None, help="run a small fixed case for profiling or a separate workload")
+    ap.add_argument("--c5-frac", type=float, default=1.0, help="fraction of conduction bands timed in --case c3")
     args = ap.parse_args(argv)
-    if args.case == "c5":
-        return run_c5(args)
     if args.case == "c3":
         return run_c3(args)
     if args.case == "c4":
         return run_c4(args)
+    if args.case == "peaks":
+        return run_peaks(args)
     if args.case:
         return run_case(args)
     if args.impl == "reference":

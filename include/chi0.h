@@ -212,6 +212,14 @@ int chi0_grid_energies(const double* E_c, int n_c, int N0, double dE, double E_m
  * next chi0_sync_status reports CHI0_ERR_TIMEOUT and the plan stays usable. */
 chi0_status chi0_selftest_wait(chi0_plan plan, double budget_ms, void* stream);
 
+/* Diagnostic (not part of the method): throughput of the CUDA-core fused
+ * multiply-add pipes, FP32 (kind 0) or FP64 (kind 1).  One launch of 8 CTAs of
+ * 256 threads per SM, each thread `iters` x 8 independent FMA chains, timed with
+ * CUDA events on `stream` (synchronised).  *ms (host) receives the device time,
+ * *flops (host) the flops executed (2 per FMA).  CHI0_ERR_INVALID unless
+ * kind is 0 or 1 and 1 <= iters <= 2^20.  Needs no plan. */
+chi0_status chi0_peak_fma(int kind, int iters, double* ms, double* flops, void* stream);
+
 /* Autotuner of the tensor-core contraction (split plans): times the kernel
  * variant (single CTAs with 128 x 128 tiles, or CTA pairs sharing one
  * tcgen05.mma.cta_group::2 over 256 x 128 tiles), the raster group of the
@@ -219,7 +227,7 @@ chi0_status chi0_selftest_wait(chi0_plan plan, double budget_ms, void* stream);
  * launch (2048, 4096, ... up to max_pairs) on synthetic operands
  * written into the plan's workspace for sphere iq (a scratch chi0 is
  * allocated and freed; every candidate over two launches, the three fastest
- * again over four), keeps the fastest in the plan and appends it to the
+ * again by their median over nine launches), keeps the fastest in the plan and appends it to the
  * text cache named by the environment variable CHI0_TUNE_CACHE (default
  * $HOME/.cache/chi0_tune.txt).  Unless flags & 1, a cached entry for the same
  * device, sphere size, frequency count, precision, products and Hermitian mode is applied

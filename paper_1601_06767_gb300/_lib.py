@@ -66,6 +66,7 @@ SIGNATURES = [
     ("chi0_profile_read", _I, [_VP, _VP, _VP]),
     ("chi0_energy_substitution_estimate", _I, [_VP, _VP, _VP, _I, _I, _D, _D, _VP, _VP, _VP]),
     ("chi0_grid_energies", _I, [_VP, _I, _I, _D, _D, _VP]),
+    ("chi0_peak_fma", _I, [_I, _I, _VP, _VP, _VP]),
     ("chi0_accumulate_fp64_noalloc", _I, [_I, _VP, _I, _I, _VP, _VP, _VP, _I, _VP, _VP, _D, _VP, _VP]),
 ]
 KERNELS = ["wfn", "pair_planes", "pair_gather", "weights", "pack", "contract_tc", "contract_f64",

@@ -116,9 +116,6 @@ extern "C" chi0_status chi0_autotune(chi0_plan p, int iq, int flags, double* bes
     p->err = "autotune: cannot allocate a scratch chi0";
     return CHI0_ERR_OOM;
   }
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
   const bool timing = p->prof_timing;
   p->prof_timing = false;
   std::vector<int> groups = {1, 2, 4, 8, 16};
@@ -133,28 +130,36 @@ extern "C" chi0_status chi0_autotune(chi0_plan p, int iq, int flags, double* bes
   int best_g = saved_group, best_pair = saved_pair;
   int64_t best_b = saved_block;
   std::string why;
-  // time one candidate: one untimed launch, then `reps` timed ones; microseconds per pair or < 0 on failure
+  // time one candidate: one untimed launch, then `reps` launches with an event pair each; the median
+  // launch in microseconds per pair, or < 0 on failure
+  constexpr int kMaxReps = 9;
+  cudaEvent_t ev[kMaxReps + 1];
+  for (cudaEvent_t& x : ev) cudaEventCreate(&x);
   auto time_candidate = [&](int pair, int64_t b, int g, int reps) -> double {
+    reps = std::min(reps, kMaxReps);
     p->tc_pair = pair;
     p->tc_group = g;
     p->block_pairs = b;
     const int nc = (int)(b / nv);
-    float ms = 0.f;
     cudaError_t le = cudaSuccess;
     for (int rep = 0; rep <= reps && le == cudaSuccess; ++rep) {
-      if (rep == 1) cudaEventRecord(e0, s);
+      if (rep >= 1) cudaEventRecord(ev[rep - 1], s);
       le = launch_weights(p, 0, b, nc, Ev, Ec, nullptr, p->d_f, s);
       if (le == cudaSuccess) le = launch_contract_tc(p, nG, (const float2*)p->d_M, b, p->d_f, chi, s, &why);
     }
-    cudaEventRecord(e1, s);
-    if (le != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+    cudaEventRecord(ev[reps], s);
+    if (le != cudaSuccess || cudaEventSynchronize(ev[reps]) != cudaSuccess) {
       cudaGetLastError();
       return -1.0;
     }
-    cudaEventElapsedTime(&ms, e0, e1);
-    return 1e3 * ms / (double)reps / (double)b;
+    std::vector<float> t(reps);
+    for (int r = 0; r < reps; ++r) cudaEventElapsedTime(&t[r], ev[r], ev[r + 1]);
+    std::sort(t.begin(), t.end());
+    const double med = reps % 2 ? t[reps / 2] : 0.5 * (t[reps / 2 - 1] + t[reps / 2]);
+    return 1e3 * med / (double)b;
   };
-  // pass 1: every candidate over two launches; pass 2: the three fastest again over four launches
+  // pass 1: every candidate over two launches; pass 2: the three fastest again, the median of
+  // nine launches each (so that repeated tuning runs pick the same candidate)
   struct Cand { double us; int pair; int64_t b; int g; };
   std::vector<Cand> cands;
   for (int pair = 0; pair < 2; ++pair)
@@ -165,7 +170,7 @@ extern "C" chi0_status chi0_autotune(chi0_plan p, int iq, int flags, double* bes
       }
   std::sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) { return x.us < y.us; });
   for (size_t k = 0; k < cands.size() && k < 3; ++k) {
-    const double us = time_candidate(cands[k].pair, cands[k].b, cands[k].g, 4);
+    const double us = time_candidate(cands[k].pair, cands[k].b, cands[k].g, kMaxReps);
     if (us > 0.0 && us < best) {
       best = us;
       best_g = cands[k].g;
@@ -174,8 +179,7 @@ extern "C" chi0_status chi0_autotune(chi0_plan p, int iq, int flags, double* bes
     }
   }
   p->prof_timing = timing;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (cudaEvent_t& x : ev) cudaEventDestroy(x);
   cudaFree(chi);
   p->tc_group = best_g;
   p->block_pairs = best_b;
