@@ -446,7 +446,7 @@ def contraction_roofline(prof, alg_flops, pairs, n_prod, n2, nG, nf, herm, cta_p
     avg_s = tc_ms / 1e3 / tc_n
     elems = tc_tiles(nG, herm, cta_pair) * (256 if cta_pair else 128) * 128
     # per pair and frequency: products x 4 real products x 2 flops x computed elements
-    prods = (np.asarray(n_prod) + (np.asarray(n2) if herm else 0)).astype(np.float64)
+    prods = (np.full(nf, float(n_prod)) + (np.asarray(n2, dtype=np.float64) if herm else 0.0))
     tensor_total = float(np.sum(prods * 8.0 * elems * pairs))
     alg_launch = alg_flops / tc_n
     ach = alg_launch / avg_s / 1e12
@@ -456,7 +456,7 @@ def contraction_roofline(prof, alg_flops, pairs, n_prod, n2, nG, nf, herm, cta_p
             "flops_per_launch": alg_launch, "flops_kind": "algorithmic, 8 N_G^2 per pair and frequency",
             "launches": tc_n, "avg_launch_ms": avg_s * 1e3,
             "tensor_pipe": {"flops_per_launch": tensor_total / tc_n, "achieved": t_ach, "frac": t_ach / peak,
-                            "products_per_frequency": [int(x) for x in np.atleast_1d(prods)] if herm else int(n_prod),
+                            "products_per_frequency": [int(x) for x in prods],
                             "hermitian": herm, "cta_pair": bool(cta_pair)},
             "note": note}
 
@@ -899,7 +899,7 @@ def run_case(args):
     import torch
     import paper_1601_06767_gb300 as pkg
     from synth import make_problem
-    big = args.case in ("contract5", "pairs5")
+    big = args.case in ("contract5", "pairs5", "wfn5")
     prob = make_problem("c5", n_imag=1) if big else make_problem("c2")
     nG = prob.gvec[0].shape[0]
     K, nv, nc = (8192, 512, 16) if big else (8192, 128, 64)
@@ -913,11 +913,18 @@ def run_case(args):
         if args.case == "contract" and not args.no_tune:
             plan.autotune(0)          # the variant the benchmark runs
         if args.case == "wfn":
-            cc = torch.from_numpy(prob.coeff_c(np.arange(512))).cuda()
-            psi = torch.empty((512,) + plan.n, dtype=plan.cdtype, device="cuda")
-            for _ in range(2):
-                plan.wfn_to_grid(cc, out=psi)
+            nb = 256 if big else 512
+            cc = torch.from_numpy(prob.coeff_c(np.arange(nb))).cuda()
+            psi = torch.empty((nb,) + plan.n, dtype=plan.cdtype, device="cuda")
+            plan.wfn_to_grid(cc, out=psi)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            plan.wfn_to_grid(cc, out=psi)
+            ev1.record()
+            torch.cuda.synchronize()
             plan.sync_status()
+            print(json.dumps({"case": "wfn" + ("5" if big else ""), "bands": nb, "ms": ev0.elapsed_time(ev1)}))
             return 0
         if args.case == "coh":
             # plasmon-pole parameters and the COH sums for 4 targets x 663 bands on the 2500-vector sphere
@@ -947,18 +954,33 @@ def run_case(args):
             plan.sync_status()
             return 0
         M = torch.randn(K, nG, dtype=torch.complex64, device="cuda", generator=g) * 4e-3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if args.case == "contract":
             Ev = torch.tensor(prob.E_v[:nv], device="cuda")
             Ec = torch.tensor(prob.E_c[:nc], device="cuda")
             chi = plan.new_chi(0)
-            for _ in range(2):
+
+            def call():
                 plan.accumulate(0, M, nv, nc, Ev, Ec, chi=chi)
         else:
             psi_v = torch.randn(nv, *plan.n, dtype=torch.complex64, device="cuda", generator=g)
             psi_c = torch.randn(nc, *plan.n, dtype=torch.complex64, device="cuda", generator=g)
-            for _ in range(2):
+
+            def call():
                 plan.pairs(0, psi_v, psi_c, out=M)
+        call()
+        torch.cuda.synchronize()
+        plan.profile(True)
+        plan.profile_reset()
+        e0.record()
+        call()
+        e1.record()
+        torch.cuda.synchronize()
         plan.sync_status()
+        prof = {k: v for k, v in plan.profile_read().items() if v[1]}
+        print(json.dumps({"case": args.case + ("5" if big else ""), "pairs": K, "ms": e0.elapsed_time(e1),
+                          "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()},
+                          "launches": {k: v[1] for k, v in prof.items()}}))
     return 0
 
 
@@ -1148,7 +1170,8 @@ def main(argv=None):
     ap.add_argument("--no-eps", action="store_true", help="skip the dielectric-matrix measurement")
     ap.add_argument("--no-quad", action="store_true", help="skip the quadrature variants of Eq. 3")
     ap.add_argument("--no-coh", action="store_true", help="skip the COH self-energy measurement")
-    ap.add_argument("--case", choices=["contract", "contract5", "pairs", "wfn", "eps", "coh", "c3", "c4", "peaks"],
+    ap.add_argument("--case", choices=["contract", "contract5", "pairs", "pairs5", "wfn", "wfn5", "eps", "coh", "c3", "c4",
+                                       "peaks"],
                     default=None, help="run a small fixed case for profiling or a separate workload")
     ap.add_argument("--c5-frac", type=float, default=1.0, help="fraction of conduction bands timed in --case c3")
     args = ap.parse_args(argv)

@@ -82,6 +82,8 @@ struct chi0_plan_s {
   std::vector<const void*> graph_key;
   int64_t graph_family[CHI0_K_COUNT] = {};   // kernel launches per family inside the captured graph
   double* d_bwd = nullptr;   // adjoint work: per-pair grad dE and per-tile partial sums
+  void* wfn_ws = nullptr;    // scratch of the three-pass wavefunction transform (FP32 plans on 96^3)
+  size_t wfn_ws_bytes = 0;
   void* d_inv = nullptr;     // dielectric-inverse workspace (grown on demand)
   // pipelined chi0_build (split plans): the pair stage and packing of block k+1 run on a
   // low-priority stream beside the contraction of block k on a high-priority one, with a

@@ -641,13 +641,272 @@ cudaError_t launch_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Stages 1+2 on the n^3 grids n = 3Q with group-cooperative transforms (used
+// for 96^3, Q = 32; on 48^3 the per-thread register FFTs above measured faster
+// than Q = 16): a group of Q lanes transforms one line (a warp holds 32/Q lines).  A line is split as i = a + 3b (a < 3, b < Q): lane
+// b of the group holds x(3b), x(3b+1), x(3b+2) (24 contiguous bytes, so the
+// group reads its row at once), the three Q-point transforms
+// F_a(m) = sum_b x(a+3b) e^{2 pi i m b/Q} run across the group's lanes by
+// radix-2 decimation in frequency (one shuffle per value and stage; lane b
+// ends with F_a(bitrev(b))), and lane b forms, for kk = bitrev(b) + Q t,
+//   y(kk) = F_0(kk mod Q) + e^{2 pi i kk/n} F_1(kk mod Q) + e^{4 pi i kk/n} F_2(kk mod Q)
+// (t = 0, 1: the kept extents are below 32).
+// One CTA per (plane i1, valence band) and a run of conduction bands:
+//   stage 1: rows i2 of conj(u_v') u_c, transformed along i3 into X[i2][k3];
+//   stage 2: the kept columns k3 of X, transformed along i2 into Y[k2][k3];
+//   Y is copied to D[pair][i1] (contiguous nk2 x nk3 values).
+// The shifted valence plane u_v' stays in shared memory for the whole run.
+// Shared memory: Uv[n][n+1], X[n][nk3|1], Y[nk2][nk3].
+// ---------------------------------------------------------------------------
+constexpr int WL_WARPS = 8;
+constexpr int WL_NKMAX = 32;
+
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
+// per-lane constants of the group transform: stage twiddles e^{2 pi i (b mod h)/(2h)} for
+// h = Q/2, ..., 1 and the combination factors e^{2 pi i kk/n}, e^{4 pi i kk/n} of both output sets
+// NS output sets: lane b forms y(bitrev(b) + Q t) for t < NS
+template <int Q, int NS = 2> struct WLConsts {
+  static constexpr int LOGQ = Q == 32 ? 5 : 4;
+  float2 tw[LOGQ];
+  float2 c1[NS], c2[NS];
+  int kk;
+};
+template <int Q, int NS = 2>
+__device__ __forceinline__ WLConsts<Q, NS> wl_consts(int b) {
+  constexpr int n = 3 * Q;
+  WLConsts<Q, NS> c;
+#pragma unroll
+  for (int s = 0; s < WLConsts<Q, NS>::LOGQ; ++s) {
+    const int h = (Q / 2) >> s;
+    c.tw[s] = root<n>((b % h) * (n / (2 * h)));      // (b mod h)/(2h) of a turn
+  }
+  c.kk = bitrev<Q>(b);
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    const int k = c.kk + Q * t;
+    c.c1[t] = root<n>(k % n);
+    c.c2[t] = root<n>((2 * k) % n);
+  }
+  return c;
+}
+
+// the Q-point transforms of the three sub-sequences across the group (in place, outputs in
+// bit-reversed lane order), then y[t] = y(bitrev(b) + Q t) of the length-3Q line whose values
+// x(a + 3b) lane b holds in x[a]
+template <int Q, int NS>
+__device__ __forceinline__ void wl_line(float2 (&x)[3], const WLConsts<Q, NS>& c, int b, float2 (&y)[NS]) {
+#pragma unroll
+  for (int s = 0; s < WLConsts<Q, NS>::LOGQ; ++s) {
+    const int h = (Q / 2) >> s;
+    const bool upper = (b & h) != 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float2 p = shfl_xor2(x[a], h);
+      const float2 sum = make_float2(x[a].x + p.x, x[a].y + p.y);
+      const float2 dif = cmul(make_float2(p.x - x[a].x, p.y - x[a].y), c.tw[s]);
+      x[a] = upper ? dif : sum;
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    y[t] = x[0];
+    cfma(y[t], x[1], c.c1[t]);
+    cfma(y[t], x[2], c.c2[t]);
+  }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(WL_WARPS * 32, 2)
+k_pair_planes_wl(const float2* __restrict__ psi_v, const int32_t* __restrict__ v_idx, int v0, int nv,
+                 const float2* __restrict__ psi_c, const int32_t* __restrict__ c_idx, int c0, int nc, int c_per_cta,
+                 int nk2, int nk3, int nk2p, int nk3p, const float2* __restrict__ T2, const float2* __restrict__ T3,
+                 float2* __restrict__ D) {
+  constexpr int n = 3 * Q, ld = n + 1;
+  constexpr int G = 32 / Q;                           // lines per warp
+  constexpr int LINES = WL_WARPS * G;                 // lines per CTA pass
+  constexpr int64_t nr = (int64_t)n * n * n;
+  constexpr int plane = n * n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ldx = nk3 | 1;
+  float2* Uv = reinterpret_cast<float2*>(smem_raw);   // [n][ld]
+  float2* X = Uv + n * ld;                            // [n][ldx]
+  float2* Y = X + n * ldx;                            // [nk2][nk3]
+  const int i1 = blockIdx.x;
+  const int jv = blockIdx.y;
+  const int jc_begin = blockIdx.z * c_per_cta;
+  const int jc_end = min(nc, jc_begin + c_per_cta);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = lane % Q, line0 = warp * G + lane / Q;
+  const int box = nk2 * nk3;
+  if (jv >= nv || jc_begin >= jc_end) return;
+  const WLConsts<Q, 2> cst = wl_consts<Q, 2>(b);
+  {
+    const int64_t band = v_idx ? v_idx[v0 + jv] : v0 + jv;
+    const float2* src = psi_v + band * nr + (int64_t)i1 * plane;
+    for (int e = threadIdx.x; e < plane; e += blockDim.x) {
+      const int i2 = e / n, i3 = e - i2 * n;
+      // shift to the lowest kept frequencies: u_v * conj(e^{2 pi i (k3min i3 + k2min i2)/n})
+      const float2 sh = cmul(T3[(size_t)i3 * nk3p], T2[(size_t)i2 * nk2p]);
+      Uv[i2 * ld + i3] = cmul(src[e], make_float2(sh.x, -sh.y));
+    }
+  }
+  __syncthreads();
+  for (int jc = jc_begin; jc < jc_end; ++jc) {
+    const int64_t band = c_idx ? c_idx[c0 + jc] : c0 + jc;
+    const float2* csrc = psi_c + band * nr + (int64_t)i1 * plane;
+    // stage 1: rows (n is a multiple of the lines per pass)
+    for (int i2 = line0; i2 < n; i2 += LINES) {
+      const float2* uc = csrc + i2 * n + 3 * b;
+      const float2* uv = Uv + i2 * ld + 3 * b;
+      float2 x[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) x[a] = cconjmul(uv[a], __ldg(uc + a));
+      float2 y[2];
+      wl_line<Q, 2>(x, cst, b, y);
+      if (cst.kk < nk3) X[i2 * ldx + cst.kk] = y[0];
+      if (cst.kk + Q < nk3) X[i2 * ldx + cst.kk + Q] = y[1];
+    }
+    __syncthreads();
+    // stage 2: kept columns; a pass runs warp-uniformly, groups past the last column idle
+    for (int k30 = 0; k30 < nk3; k30 += LINES) {
+      const int k3 = k30 + line0;
+      const bool ok = k3 < nk3;
+      float2 x[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) x[a] = ok ? X[(3 * b + a) * ldx + k3] : make_float2(0.f, 0.f);
+      float2 y[2];
+      wl_line<Q, 2>(x, cst, b, y);
+      if (ok && cst.kk < nk2) Y[cst.kk * nk3 + k3] = y[0];
+      if (ok && cst.kk + Q < nk2) Y[(cst.kk + Q) * nk3 + k3] = y[1];
+    }
+    __syncthreads();
+    float2* dst = D + ((int64_t)(jv * nc + jc) * n + i1) * box;
+    for (int e = threadIdx.x; e < box; e += blockDim.x) dst[e] = Y[e];
+    // the next run's stage 1 writes X only after the barrier above, and Y after its own first barrier
+  }
+}
+
+template <int Q>
+cudaError_t launch_planes_wl(const chi0_plan_s* p, const SphereQ& s, const void* psi_v, const int32_t* v_idx,
+                             int v0, int nv, const void* psi_c, const int32_t* c_idx, int c0, int nc, void* D,
+                             cudaStream_t st) {
+  constexpr int n = 3 * Q;
+  const size_t sm = ((size_t)n * (n + 1) + (size_t)n * (s.nk3 | 1) + (size_t)s.nk2 * s.nk3) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_pair_planes_wl<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  // long conduction runs per CTA (the valence plane is loaded once per run), but enough CTAs
+  int cpc = 16;
+  while (cpc > 1 && (int64_t)p->n1 * nv * ((nc + cpc - 1) / cpc) < 4 * 152) cpc >>= 1;
+  dim3 grid(p->n1, nv, (nc + cpc - 1) / cpc);
+  k_pair_planes_wl<Q><<<grid, WL_WARPS * 32, sm, st>>>((const float2*)psi_v, v_idx, v0, nv, (const float2*)psi_c,
+                                                       c_idx, c0, nc, cpc, s.nk2, s.nk3, s.nk2p, s.nk3p, s.T2f,
+                                                       s.T3f, (float2*)D);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Wavefunctions on the 96^3 grid (FP32 plans) by three passes of the same
+// warp transform, each over whole length-96 lines (all 96 outputs):
+//   pass 1 (k_wfn96_cols): for every (g2, g3) column of the sphere, the line
+//     along g1 (coefficients at g1 mod 96, zeros elsewhere) -> A[b][i1][col];
+//   pass 2 (k_wfn96_planes, one CTA per plane i1 and band): the lines along g2
+//     for every g3 (from A[b][i1] in shared memory) -> B[i2][g3], then the
+//     lines along g3 for every i2 -> psi[b][i1][i2][:].
+// psi_b(r) = sum_g c_b(g) e^{2 pi i g.r} as the direct kernels; the scratch
+// A holds 96 x nw2 x nw3 values per band of a chunk.
+// ---------------------------------------------------------------------------
+constexpr int WF_WARPS = 8;
+
+// the g in [gmin, gmin + 95] with g = i (mod 96); valid when g <= gmax
+__device__ __forceinline__ int wf_g(int i, int gmin) { return gmin + (((i - gmin) % 96) + 96) % 96; }
+
+__global__ void __launch_bounds__(WF_WARPS * 32)
+k_wfn96_cols(const double2* __restrict__ coeff, int npw, int ncols, const int* __restrict__ col_start,
+             const int* __restrict__ col_pw, const int* __restrict__ col_g1, int w1min, float2* __restrict__ A) {
+  __shared__ float2 line[WF_WARPS][96];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * WF_WARPS + warp;
+  if (c >= ncols) return;                             // whole warps only: no barrier below
+  const int64_t b = blockIdx.y;
+  float2* L = line[warp];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) L[lane + 32 * t] = make_float2(0.f, 0.f);
+  __syncwarp();
+  const double2* cb = coeff + b * npw;
+  for (int k = col_start[c] + lane; k < col_start[c + 1]; k += 32) {
+    const int g1 = col_g1[k] + w1min;
+    const double2 d = cb[col_pw[k]];
+    L[((g1 % 96) + 96) % 96] = make_float2((float)d.x, (float)d.y);
+  }
+  __syncwarp();
+  const WLConsts<32, 3> cst = wl_consts<32, 3>(lane);
+  float2 x[3], y[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) x[a] = L[3 * lane + a];
+  wl_line<32, 3>(x, cst, lane, y);
+  float2* out = A + b * 96 * (int64_t)ncols + c;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) out[(int64_t)(cst.kk + 32 * t) * ncols] = y[t];
+}
+
+__global__ void __launch_bounds__(WF_WARPS * 32, 3)
+k_wfn96_planes(const float2* __restrict__ A, int nw2, int nw3, int w2min, int w3min, float2* __restrict__ psi) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lda = nw3 | 1, ncols = nw2 * nw3;
+  float2* As = reinterpret_cast<float2*>(smem_raw);  // [nw2][lda]
+  float2* Bs = As + nw2 * lda;                       // [96][lda]
+  const int i1 = blockIdx.x;
+  const int64_t b = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float2* Ap = A + (b * 96 + i1) * (int64_t)ncols;
+  for (int e = threadIdx.x; e < ncols; e += blockDim.x) {
+    const int r = e / nw3;
+    As[r * lda + (e - r * nw3)] = Ap[e];
+  }
+  __syncthreads();
+  const WLConsts<32, 3> cst = wl_consts<32, 3>(lane);
+  int g2i[3], g3i[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    g2i[a] = wf_g(3 * lane + a, w2min) - w2min;       // row of As at line position 3 lane + a, if < nw2
+    g3i[a] = wf_g(3 * lane + a, w3min) - w3min;
+  }
+  // along g2 for every g3
+  for (int j3 = warp; j3 < nw3; j3 += WF_WARPS) {
+    float2 x[3], y[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = g2i[a] < nw2 ? As[g2i[a] * lda + j3] : make_float2(0.f, 0.f);
+    wl_line<32, 3>(x, cst, lane, y);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) Bs[(cst.kk + 32 * t) * lda + j3] = y[t];
+  }
+  __syncthreads();
+  // along g3 for every i2
+  float2* out = psi + (b * 96 + i1) * (int64_t)(96 * 96);
+  for (int i2 = warp; i2 < 96; i2 += WF_WARPS) {
+    float2 x[3], y[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = g3i[a] < nw3 ? Bs[i2 * lda + g3i[a]] : make_float2(0.f, 0.f);
+    wl_line<32, 3>(x, cst, lane, y);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) out[i2 * 96 + cst.kk + 32 * t] = y[t];
+  }
+}
+
 // FP32 planes with register FFTs when the grid is cubic, n = P*Q is supported and
 // the kept extents fit NKMAX; returns cudaErrorNotSupported otherwise.
 cudaError_t try_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void* psi_v, const int32_t* v_idx, int v0,
                            int nv, const void* psi_c, const int32_t* c_idx, int c0, int nc, void* D,
                            cudaStream_t st) {
   const int nk = std::max(s.nk2, s.nk3);
-  if (!(p->n1 == p->n2 && p->n2 == p->n3) || nk > NKMAX) return cudaErrorNotSupported;
+  if (!(p->n1 == p->n2 && p->n2 == p->n3)) return cudaErrorNotSupported;
+  if (p->n3 == 96 && nk <= WL_NKMAX && nv <= 65535)
+    return launch_planes_wl<32>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
+  if (nk > NKMAX) return cudaErrorNotSupported;
 #define CHI0_FFT_CASE(P, Q, TV, NCB)                                                                    \
   if (nk <= 12) return launch_fft_planes<P, Q, 12, TV, NCB>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st); \
   if (nk <= 16) return launch_fft_planes<P, Q, 16, TV, NCB>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st); \
@@ -902,6 +1161,26 @@ cudaError_t launch_wfn_to_grid(const chi0_plan_s* p, const double2* coeff, int n
   }
   const WfnSphere& w = p->w;
   dim3 grid(p->n1, nb);
+  if (is_split(p) && p->wfn_ws && p->n1 == 96 && p->n2 == 96 && p->n3 == 96) {
+    // three passes of warp transforms, bands in chunks that fit the plan's scratch
+    const int ncols = w.nw2 * w.nw3;
+    const int chunk = (int)std::max<int64_t>(1, p->wfn_ws_bytes / ((size_t)96 * ncols * sizeof(float2)));
+    const size_t sm = ((size_t)w.nw2 * (w.nw3 | 1) + (size_t)96 * (w.nw3 | 1)) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_wfn96_planes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    for (int b0 = 0; b0 < nb; b0 += chunk) {
+      const int nbc = std::min(chunk, nb - b0);
+      dim3 g1((ncols + WF_WARPS - 1) / WF_WARPS, nbc);
+      k_wfn96_cols<<<g1, WF_WARPS * 32, 0, s>>>(coeff + (size_t)b0 * w.npw, w.npw, ncols, w.col_start, w.col_pw,
+                                                w.col_g1, w.w1min, (float2*)p->wfn_ws);
+      dim3 g2(96, nbc);
+      k_wfn96_planes<<<g2, WF_WARPS * 32, sm, s>>>((const float2*)p->wfn_ws, w.nw2, w.nw3, w.w2min, w.w3min,
+                                                   (float2*)psi + (size_t)b0 * p->nr);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   if (is_split(p)) {
     const size_t smb = wfn_blk_smem(p);
     // 16-byte stores: psi must be 16-byte aligned (every band plane then is, n3 % 4 == 0)

@@ -102,7 +102,7 @@ void free_plan(chi0_plan_s* p) {
   cudaFree(w.T1d); cudaFree(w.T1f); cudaFree(w.T2d); cudaFree(w.T2f);
   cudaFree(w.T3d); cudaFree(w.T3f);
   cudaFree(p->d_omega); cudaFree(p->d_D); cudaFree(p->d_M); cudaFree(p->d_f);
-  cudaFree(p->d_pack); cudaFree(p->d_status); cudaFree(p->d_bwd); cudaFree(p->d_inv);
+  cudaFree(p->d_pack); cudaFree(p->d_status); cudaFree(p->d_bwd); cudaFree(p->d_inv); cudaFree(p->wfn_ws);
   for (size_t i = 1; i < p->bq_M.size(); ++i) {
     cudaFree(p->bq_M[i]);
     cudaFree(p->bq_f[i]);
@@ -361,8 +361,10 @@ chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* d) {
   mp = std::max<int64_t>(64, (mp + 63) / 64 * 64);
   p->max_pairs = mp;
   p->block_pairs = mp;
-  // D holds the per-plane transforms of up to D_pairs pairs (about 1 GiB)
-  p->D_pairs = std::max<int64_t>(64, std::min<int64_t>(mp, ((int64_t)1 << 30) / (box * (int64_t)cb)));
+  // D holds the per-plane transforms of up to D_pairs pairs (at most 4 GiB): a whole pair block
+  // on the 96^3 grid of the 256-atom-sized workload, so that its pair stage is one launch and each
+  // valence plane is read once per block
+  p->D_pairs = std::max<int64_t>(64, std::min<int64_t>(mp, ((int64_t)4 << 30) / (box * (int64_t)cb)));
   size_t bytes_D = (size_t)p->D_pairs * box * cb;
   size_t bytes_M = (size_t)mp * p->max_nG * cb;
   size_t bytes_f = (size_t)p->n_freq * mp * sizeof(double2);
@@ -382,6 +384,16 @@ chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* d) {
     return bail(e == cudaErrorMemoryAllocation ? CHI0_ERR_OOM : CHI0_ERR_CUDA);
   }
   p->ws_bytes = bytes_D + bytes_M + bytes_f + p->pack_bytes + bytes_bwd + sizeof(int);
+  if (chi0::is_split(p) && p->w.npw > 0 && p->n1 == 96 && p->n2 == 96 && p->n3 == 96) {
+    // the 96^3 wavefunction transform runs in passes over whole lines: scratch for 128 bands
+    p->wfn_ws_bytes = (size_t)128 * 96 * p->w.nw2 * p->w.nw3 * sizeof(float2);
+    if ((e = cudaMalloc(&p->wfn_ws, p->wfn_ws_bytes)) != cudaSuccess) {
+      p->err = std::string("workspace allocation: ") + cudaGetErrorString(e);
+      cudaGetLastError();
+      return bail(e == cudaErrorMemoryAllocation ? CHI0_ERR_OOM : CHI0_ERR_CUDA);
+    }
+    p->ws_bytes += p->wfn_ws_bytes;
+  }
   p->bq_M.assign(1, p->d_M);
   p->bq_f.assign(1, p->d_f);
   p->bq_pack.assign(1, p->d_pack);
