@@ -79,13 +79,15 @@ typedef struct {
   int chain_pairs;           /* pairs accumulated in tensor memory before they are added into FP32
                                 registers (multiple of 32).  The tensor cores round each MMA result
                                 toward zero, so the bias grows with this length; 0 = 32 (default) */
-  int hermitian;             /* split precisions: contract chi0 = H1 + i H2 with the Hermitian parts
-                                H1 = 1/2 sum Re(f) M M^H and H2 = 1/2 sum Im(f) M M^H of Eq. 1, only
-                                tiles on or above the diagonal, the lower triangle written as the
-                                conjugate transpose.  H2 takes three products at a frequency whose
-                                weights of the block satisfy max|Im f| <= 2^-6 max|Re f| (its share of
-                                chi0 is then that small), else n_products.  0 = automatic (on for
-                                n_products 6), 1 = on, -1 = off */
+  int hermitian;             /* split precisions: contract chi0 = (1 + i t) H1 + i H2 with the Hermitian
+                                parts H1 = sum Re(f_p) M_p M_p^H and H2 = sum g_p M_p M_p^H,
+                                g_p = Im f_p - t Re f_p (f_p the factor of Eq. 1), only tiles on or above
+                                the diagonal, the lower triangle written as the conjugate transpose.
+                                Per frequency and pair block, t is the midrange of Im f / Re f over the
+                                block (0 when that does not shrink the H2 weights) and rho bounds
+                                max|g| / max|Re f|: H2 takes one product where rho <= 2^-11 (FP16;
+                                2^-15 BF16), three where rho <= 2^-6, else n_products (its error scales
+                                with rho).  0 = automatic (on except for n_products 4), 1 = on, -1 = off */
 } chi0_plan_desc;
 
 /* Create a plan: validates the description, analyses each G sphere for the

@@ -65,9 +65,9 @@ class Chi0Plan:
         d.max_pairs = int(max_pairs)
         d.chain_pairs = int(chain_pairs)
         d.hermitian = 0 if hermitian is None else (1 if hermitian else -1)
-        # the library's rule: split precisions only; automatic means on for six products
+        # the library's rule: split precisions only; automatic means on except for four products
         eff_np = int(n_products) or (3 if precision == "fp16" else 6)
-        self.hermitian = precision != "fp64" and (bool(hermitian) if hermitian is not None else eff_np == 6)
+        self.hermitian = precision != "fp64" and (bool(hermitian) if hermitian is not None else eff_np != 4)
         h = C.c_void_p()
         L.check(lib.chi0_plan_create(C.byref(h), C.byref(d)), None)
         self._h = h

@@ -17,13 +17,19 @@
 //           finished accumulation chains into FP32 registers and finally add
 //           the tile into chi0 in FP64.
 //
-// Hermitian mode: chi0 = H1 + i H2 with H1 = sum Re(f) M M^H, H2 = sum Im(f) M M^H,
-// both Hermitian.  A item then contracts W1 = Re(f) M and W2 = Im(f) M (two
+// Hermitian mode: with a real ratio t per frequency and block of pairs,
+//   f_p = Re f_p (1 + i t) + i g_p,   g_p = Im f_p - t Re f_p,
+//   chi0 = (1 + i t) H1 + i H2,  H1 = sum Re(f) M M^H,  H2 = sum g M M^H,
+// H1 and H2 both Hermitian.  An item contracts W1 = Re(f) M and W2 = g M (two
 // parts, each with its own power-of-two scale) for one tile on or above the
 // diagonal, adds the elements with G <= G' and writes the conjugate transpose
-// of those with G < G' into the lower triangle.  H2 is the small part
-// (|Im f| / |Re f| <= delta / |E_v - E_c| on the imaginary axis), so it takes
-// three products (two terms) when its weights are below 2^-6 of H1's.
+// of those with G < G' into the lower triangle.  t is the midrange of
+// Im f_p / Re f_p over the block (0 where that does not shrink the weights),
+// so max|g| <= rho max|Re f| with rho = half the range of the ratio: about
+// delta / |E_v - E_c| spread over the block's energies, 1e-4 for a block of
+// neighbouring conduction bands.  H2 takes one product (t0 t0) when rho <=
+// 2^-11 for FP16 (2^-15 for BF16), three products (two terms) when rho <=
+// 2^-6, else the full count; the first two with long chains.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -87,10 +93,20 @@ __device__ __forceinline__ void splitn(float a, float b, uint32_t (&w)[NT]) {
   }
 }
 
+// order-preserving map of a float onto an unsigned int (for atomicMin / atomicMax)
+__device__ __forceinline__ unsigned int ord_of(float x) {
+  const unsigned int u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float float_of_ord(unsigned int o) {
+  return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
 // largest |component| of the M block -> amax[0]; largest |Re f(w)| -> amax[1 + 2w],
-// largest |Im f(w)| -> amax[2 + 2w]
+// largest |Im f(w)| -> amax[2 + 2w]; Hermitian mode: the smallest and largest
+// Im f / Re f over the block (order-mapped) -> tr[2w], tr[2w + 1]
 __global__ void k_absmax(const float2* __restrict__ M, int64_t n, const double2* __restrict__ f, int64_t K,
-                         int n_freq, unsigned int* __restrict__ amax) {
+                         int n_freq, unsigned int* __restrict__ amax, unsigned int* __restrict__ tr) {
   float m = 0.f;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float2 v = M[i];
@@ -113,7 +129,30 @@ __global__ void k_absmax(const float2* __restrict__ M, int64_t n, const double2*
       atomicMax(amax + 1 + 2 * iw, __float_as_uint(gr));
       atomicMax(amax + 2 + 2 * iw, __float_as_uint(gi));
     }
+    if (tr) {
+      float tlo = INFINITY, thi = -INFINITY;
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = f[(int64_t)iw * K + i];
+        const float t = (float)(v.y / v.x);   // +-inf or NaN where Re f vanishes: the range is then unusable
+        tlo = fminf(tlo, t);
+        thi = fmaxf(thi, t);
+        if (t != t) thi = INFINITY;
+      }
+      for (int o = 16; o; o >>= 1) {
+        tlo = fminf(tlo, __shfl_xor_sync(0xffffffffu, tlo, o));
+        thi = fmaxf(thi, __shfl_xor_sync(0xffffffffu, thi, o));
+      }
+      if ((threadIdx.x & 31) == 0) {
+        atomicMin(tr + 2 * iw, ord_of(tlo));
+        atomicMax(tr + 2 * iw + 1, ord_of(thi));
+      }
+    }
   }
+}
+
+// tr[2w] = the largest order value (the running minimum's start), tr[2w + 1] stays 0
+__global__ void k_ratio_init(unsigned int* __restrict__ tr, int n_freq) {
+  for (int iw = threadIdx.x; iw < n_freq; iw += blockDim.x) tr[2 * iw] = 0xffffffffu;
 }
 
 // power of two 2^(14 - e) with x < 2^e (1 when x is zero or not finite)
@@ -126,23 +165,36 @@ __device__ __forceinline__ float pow2_scale(float x) {
 
 // scale[0] = sM; scale[1 + w] = sW(w); inv[w] = 1 / (sM sW(w)).  Hermitian mode:
 // scale[1 + w], inv[w] belong to W1 = Re(f) M, scale[1 + n_freq + w],
-// inv[n_freq + w] to W2 = Im(f) M, and h2np[w] is the product count of the W2 part.
-__global__ void k_scales(const unsigned int* __restrict__ amax, int n_freq, int herm, int n_products,
-                         float* __restrict__ scale, double* __restrict__ inv, int* __restrict__ h2np) {
+// inv[n_freq + w] to W2 = g M with g = Im f - t Re f, tbar[w] is t and h2np[w]
+// the product count of the W2 part (+16: long chains).
+__global__ void k_scales(const unsigned int* __restrict__ amax, const unsigned int* __restrict__ tr, int n_freq,
+                         int herm, int n_products, int bf16, float* __restrict__ scale, double* __restrict__ inv,
+                         int* __restrict__ h2np, double* __restrict__ tbar) {
   const float mM = __uint_as_float(amax[0]);
   const float sM = pow2_scale(mM);
   if (threadIdx.x == 0) scale[0] = sM;
   for (int iw = threadIdx.x; iw < n_freq; iw += blockDim.x) {
     const float fr = __uint_as_float(amax[1 + 2 * iw]), fi = __uint_as_float(amax[2 + 2 * iw]);
     if (herm) {
-      // |components of W1| <= max|Re f| max|M|, of W2 <= max|Im f| max|M|
-      const float s1 = pow2_scale(fr * mM), s2 = pow2_scale(fi * mM);
+      // shift by the midrange t of Im f / Re f when that shrinks the W2 weights:
+      // |g_p| = |Re f_p| |t_p - t| <= max|Re f| (t_max - t_min) / 2
+      const float tlo = float_of_ord(tr[2 * iw]), thi = float_of_ord(tr[2 * iw + 1]);
+      const float half = 0.5f * (thi - tlo);
+      const bool shift = isfinite(tlo) && isfinite(thi) && isfinite(half) && half * fr < fi;
+      const double t = shift ? 0.5 * ((double)tlo + (double)thi) : 0.0;
+      // the bound on |g| (with a margin for the FP32 ratio range), else max|Im f|
+      const float gmax = shift ? half * fr * 1.0001f + fr * 1e-7f : fi;
+      const float rho = fr > 0.f ? gmax / fr : 0.f;
+      // |components of W1| <= max|Re f| max|M|, of W2 <= gmax max|M|
+      const float s1 = pow2_scale(fr * mM), s2 = pow2_scale(gmax * mM);
       scale[1 + iw] = s1;
       scale[1 + n_freq + iw] = s2;
       inv[iw] = 1.0 / ((double)sM * (double)s1);
       inv[n_freq + iw] = 1.0 / ((double)sM * (double)s2);
-      // small W2 part: three products and long chains (flag 16)
-      h2np[iw] = (fi <= ldexpf(fr, -6)) ? 3 + 16 : n_products;
+      tbar[iw] = t;
+      // a small W2 part needs fewer products (errors scale with rho) and takes long chains (flag 16)
+      const float one_term = bf16 ? ldexpf(1.f, -15) : ldexpf(1.f, -11);
+      h2np[iw] = rho <= one_term ? 1 + 16 : (rho <= ldexpf(1.f, -6) ? 3 + 16 : n_products);
     } else {
       // |Re W|, |Im W| <= 2 max|f| max|M|
       const float sW = pow2_scale(2.f * fmaxf(fr, fi) * mM);
@@ -157,7 +209,7 @@ template <bool BF16, int NT>
 __global__ void __launch_bounds__(256)
 k_pack(const float2* __restrict__ M, int nG, int64_t K, int nGp, int Kp, const double2* __restrict__ f,
        int n_freq, int herm, const float* __restrict__ scale, const int* __restrict__ h2np,
-       uint32_t* __restrict__ Bp, uint32_t* __restrict__ Ap) {
+       const double* __restrict__ tbar, uint32_t* __restrict__ Bp, uint32_t* __restrict__ Ap) {
   extern __shared__ __align__(16) unsigned char smem_pack[];
   float2* tile = reinterpret_cast<float2*>(smem_pack);          // [64][33]
   float2* fs = tile + 64 * 33;                                 // [n_freq][64]
@@ -178,7 +230,9 @@ k_pack(const float2* __restrict__ M, int nG, int64_t K, int nGp, int Kp, const d
     if (p < K) {
       const double2 d = f[(int64_t)iw * K + p];
       const float sW = scale[1 + iw], sW2 = herm ? scale[1 + n_freq + iw] : sW;
-      v = make_float2((float)d.x * sW, (float)d.y * sW2);
+      // Hermitian mode: the W2 weight is g = Im f - t Re f (in FP64, the t of the merge)
+      const double im = herm ? d.y - tbar[iw] * d.x : d.y;
+      v = make_float2((float)d.x * sW, (float)im * sW2);
     }
     fs[e] = v;
   }
@@ -209,7 +263,8 @@ k_pack(const float2* __restrict__ M, int nG, int64_t K, int nGp, int Kp, const d
 #pragma unroll
         for (int t = 0; t < NT; ++t) a[(NT + t) * plane] = w[t];
         uint32_t* a2 = a + (size_t)n_freq * 2 * NT * plane;
-        const int nt2 = (NT == 3 && h2np[iw] != 6) ? 2 : NT;   // terms the W2 part reads
+        const int np2 = h2np[iw] & 15;
+        const int nt2 = np2 == 1 ? 1 : ((NT == 3 && np2 != 6) ? 2 : NT);   // terms the W2 part reads
         splitn<BF16, NT>(f0.y * m0.x, f1.y * m1.x, w);
 #pragma unroll
         for (int t = 0; t < NT; ++t)
@@ -269,8 +324,9 @@ __device__ __forceinline__ void issue_stage_np(const unsigned char* st, uint32_t
       for (int i = 0; i < NT; ++i) {
         const int j = order - i;
         if (j < 0 || j >= NT) continue;
-        // 3: t0t0, t0t1, t1t0; 4: adds t1t1; 6: all t_i t_j with i + j <= 2
-        const bool keep = (i + j < 2) || (i + j == 2 && (NPROD == 6 || (NPROD == 4 && i == 1)));
+        // 1: t0t0; 3: t0t0, t0t1, t1t0; 4: adds t1t1; 6: all t_i t_j with i + j <= 2
+        const bool keep = NPROD == 1 ? (i + j == 0)
+                                     : (i + j < 2) || (i + j == 2 && (NPROD == 6 || (NPROD == 4 && i == 1)));
         if (!keep) continue;
         // planes: Re terms 0..NT-1, Im terms NT..2NT-1; K step ks is +32 bytes
         const uint64_t ar = d0 + (uint64_t)i * kTile + (uint64_t)(ks * 2);
@@ -305,6 +361,7 @@ __device__ __forceinline__ void issue_stage(const unsigned char* st, uint32_t d_
                                             int n_products) {
   if (n_products == 6) issue_stage_np<BF16, NT, PAIR, 6>(st, d_re, d_im, first);
   else if (n_products == 4) issue_stage_np<BF16, NT, PAIR, 4>(st, d_re, d_im, first);
+  else if (n_products == 1) issue_stage_np<BF16, NT, PAIR, 1>(st, d_re, d_im, first);
   else issue_stage_np<BF16, NT, PAIR, 3>(st, d_re, d_im, first);
 }
 
@@ -321,6 +378,7 @@ struct TcBatch {
   double2* chi[MAXQ];
   const double* inv[MAXQ];   // [n_parts * n_freq] inverse operand scales
   const int* h2np[MAXQ];     // Hermitian mode: [n_freq] product count of the W2 part (+16 if small)
+  const double* tbar[MAXQ];  // Hermitian mode: [n_freq] ratio t of chi0 = (1 + i t) H1 + i H2
   int nG[MAXQ];
   int tiles_m[MAXQ];         // tiles along G (rows of chi0)
   int tiles_n[MAXQ];         // tiles along G' (columns)
@@ -376,10 +434,10 @@ __device__ __forceinline__ void decode_item(const TcBatch& P, int64_t item, int&
 
 // Add one drained part of a tile row (row G, columns Hb..Hb+63) into chi0 of
 // one frequency.  Plain mode: chi[G][H] += s (re + i im).  Hermitian mode: part 0
-// holds H1(G, H), part 1 holds H2(G, H); chi[G][H] += H1 + i H2 for G <= H and
-// chi[H][G] += conj(H1) + i conj(H2) for G < H.
+// holds H1(G, H), part 1 holds H2(G, H); chi[G][H] += (1 + i t) H1 + i H2 for
+// G <= H and chi[H][G] += (1 + i t) conj(H1) + i conj(H2) for G < H.
 __device__ __forceinline__ void merge_row(double2* __restrict__ chi_w, int nG, int G, int Hb, const float (&sre)[64],
-                                          const float (&sim)[64], double sc, bool herm, int part) {
+                                          const float (&sim)[64], double sc, bool herm, int part, double t) {
   double2* row = chi_w + (size_t)G * nG;
   if (!herm) {
 #pragma unroll
@@ -399,12 +457,12 @@ __device__ __forceinline__ void merge_row(double2* __restrict__ chi_w, int nG, i
     if (H < nG && G <= H) {
       const double a = (double)sre[i] * sc, b = (double)sim[i] * sc;
       double2 o = row[H];
-      if (part == 0) { o.x += a; o.y += b; } else { o.x -= b; o.y += a; }
+      if (part == 0) { o.x += a - t * b; o.y += b + t * a; } else { o.x -= b; o.y += a; }
       row[H] = o;
       if (G < H) {
         double2* m = chi_w + (size_t)H * nG + G;
         double2 u = *m;
-        if (part == 0) { u.x += a; u.y -= b; } else { u.x += b; u.y += a; }
+        if (part == 0) { u.x += a + t * b; u.y += t * a - b; } else { u.x += b; u.y += a; }
         *m = u;
       }
     }
@@ -460,7 +518,8 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
         decode_item(P, item, q, iw, tm, tn);
         for (int part = 0; part < P.n_parts && ok; ++part) {
           // planes of the terms the part's products read (t2 only with six products)
-          const int nt = (NT == 3 && part_products(P, q, iw, part) != 6) ? 2 : NT;
+          const int npp = part_products(P, q, iw, part);
+          const int nt = npp == 1 ? 1 : ((NT == 3 && npp != 6) ? 2 : NT);
           const int plane0 = (part * P.n_freq + iw) * PL;
           const int row_a = tm * BM, row_b = tn * BN;
           for (int kc = 0; kc < nK; ++kc, ++gs) {
@@ -582,7 +641,7 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
       const int G = tm * BM + row;
       if (ok && G < nG)
         merge_row(P.chi[q] + (size_t)iw * nG * nG, nG, G, tn * BN + half * 64, sre, sim,
-                  P.inv[q][part * P.n_freq + iw], P.n_parts == 2, part);
+                  P.inv[q][part * P.n_freq + iw], P.n_parts == 2, part, P.n_parts == 2 ? P.tbar[q][iw] : 0.0);
       }
     }
   }
@@ -671,7 +730,8 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
         const int arow = tm * 2 * BM + (int)rank * BM;     // this CTA's 128 rows of A
         const int brow = tn * BN + (int)rank * (BN / 2);   // this CTA's 64 rows of B
         for (int part = 0; part < P.n_parts && ok; ++part) {
-          const int nt = (NT == 3 && part_products(P, q, iw, part) != 6) ? 2 : NT;
+          const int npp = part_products(P, q, iw, part);
+          const int nt = npp == 1 ? 1 : ((NT == 3 && npp != 6) ? 2 : NT);
           const int plane0 = (part * P.n_freq + iw) * PL;
           for (int kc = 0; kc < nK; ++kc, ++gs) {
             const int s = slot;
@@ -795,7 +855,7 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
       const int G = tm * 2 * BM + (int)rank * BM + row;
       if (ok && G < nG)
         merge_row(P.chi[q] + (size_t)iw * nG * nG, nG, G, tn * BN + half * 64, sre, sim,
-                  P.inv[q][part * P.n_freq + iw], P.n_parts == 2, part);
+                  P.inv[q][part * P.n_freq + iw], P.n_parts == 2, part, P.n_parts == 2 ? P.tbar[q][iw] : 0.0);
       }
     }
   }
@@ -888,20 +948,29 @@ size_t tc_pack_bytes(const chi0_plan_s* p, int64_t max_pairs, int max_nG) {
   const size_t nGp = (size_t)round_up_i(max_nG, 2 * BM);
   const size_t Kp = (size_t)((max_pairs + 63) / 64 * 64);
   const size_t planes = 2 * (size_t)n_terms(p) * (1 + (size_t)n_parts(p) * p->n_freq);
-  const size_t scal = 256 + 48 * (size_t)(p->n_freq + 1);   // amax, scales, inverse scales, W2 products
+  // amax, ratio range, scales, inverse scales, W2 products, ratios t
+  const size_t scal = 256 + 64 * (size_t)(p->n_freq + 1);
   return planes * nGp * Kp * 2 + scal;
 }
 
-// workspace of one q-point's split planes: B, A, then amax / scales / inverse
-// scales / W2 product counts (each part sized for two values per frequency)
+// workspace of one q-point's split planes: B, A, then amax / ratio range /
+// scales / inverse scales / W2 product counts / ratios t (each part sized for
+// two values per frequency)
 struct PackWs {
   uint16_t* Bp;
   uint16_t* Ap;
   unsigned int* amax;
+  unsigned int* tr;
   float* scale;
   double* inv;
   int* h2np;
+  double* tbar;
 };
+
+static cudaError_t fill_ratio_min(unsigned int* tr, int n_freq, cudaStream_t s) {
+  k_ratio_init<<<1, 128, 0, s>>>(tr, n_freq);
+  return cudaGetLastError();
+}
 
 static PackWs pack_ws(const chi0_plan_s* p, void* base, int nGp, int Kp) {
   const size_t nf1 = (size_t)(p->n_freq + 1);
@@ -910,26 +979,35 @@ static PackWs pack_ws(const chi0_plan_s* p, void* base, int nGp, int Kp) {
   w.Ap = w.Bp + (size_t)2 * n_terms(p) * nGp * Kp;
   unsigned char* tail = reinterpret_cast<unsigned char*>(base) + planes_bytes(p);
   w.amax = reinterpret_cast<unsigned int*>(tail);            // 1 + 2 n_freq words
-  w.scale = reinterpret_cast<float*>(tail + 8 * nf1);         // 1 + 2 n_freq floats
-  w.inv = reinterpret_cast<double*>(tail + 16 * nf1);         // 2 n_freq doubles
-  w.h2np = reinterpret_cast<int*>(tail + 32 * nf1);           // n_freq ints
+  w.tr = reinterpret_cast<unsigned int*>(tail + 8 * nf1);     // 2 n_freq words
+  w.scale = reinterpret_cast<float*>(tail + 16 * nf1);        // 1 + 2 n_freq floats
+  w.inv = reinterpret_cast<double*>(tail + 24 * nf1);         // 2 n_freq doubles
+  w.h2np = reinterpret_cast<int*>(tail + 40 * nf1);           // n_freq ints
+  w.tbar = reinterpret_cast<double*>(tail + 48 * nf1);        // n_freq doubles
   return w;
 }
 
 template <bool BF16, int NT>
 static cudaError_t pack_one(chi0_plan_s* p, int nG, const float2* M, int64_t K, const double2* f, const PackWs& w,
                             int nGp, int Kp, cudaStream_t s) {
-  ProfScope ps(p, CHI0_K_PACK, s, 3);
+  ProfScope ps(p, CHI0_K_PACK, s, p->tc_herm ? 4 : 3);
   cudaError_t e = cudaMemsetAsync(w.amax, 0, sizeof(unsigned int) * (2 * p->n_freq + 1), s);
   if (e != cudaSuccess) return e;
-  k_absmax<<<2 * 152, 256, 0, s>>>(M, K * nG, f, K, p->n_freq, w.amax);
-  k_scales<<<1, 128, 0, s>>>(w.amax, p->n_freq, p->tc_herm ? 1 : 0, p->n_products, w.scale, w.inv, w.h2np);
+  if (p->tc_herm) {
+    // ratio range: minimum starts at the largest order value, maximum at the smallest
+    e = cudaMemsetAsync(w.tr, 0, sizeof(unsigned int) * 2 * p->n_freq, s);
+    if (e == cudaSuccess) e = fill_ratio_min(w.tr, p->n_freq, s);
+    if (e != cudaSuccess) return e;
+  }
+  k_absmax<<<2 * 152, 256, 0, s>>>(M, K * nG, f, K, p->n_freq, w.amax, p->tc_herm ? w.tr : nullptr);
+  k_scales<<<1, 128, 0, s>>>(w.amax, w.tr, p->n_freq, p->tc_herm ? 1 : 0, p->n_products, BF16 ? 1 : 0, w.scale,
+                             w.inv, w.h2np, w.tbar);
   dim3 gpk(nGp / 32, Kp / 64);
   const size_t smp = (size_t)(64 * 33 + 64 * p->n_freq) * sizeof(float2);
   e = cudaFuncSetAttribute(k_pack<BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
   if (e != cudaSuccess) return e;
   k_pack<BF16, NT><<<gpk, 256, smp, s>>>(M, nG, K, nGp, Kp, f, p->n_freq, p->tc_herm ? 1 : 0, w.scale, w.h2np,
-                                         (uint32_t*)w.Bp, (uint32_t*)w.Ap);
+                                         w.tbar, (uint32_t*)w.Bp, (uint32_t*)w.Ap);
   return cudaGetLastError();
 }
 
@@ -958,6 +1036,7 @@ static cudaError_t run_tc(chi0_plan_s* p, const TcJob* jobs, int n_jobs, int64_t
     P->chi[j] = jb.chi;
     P->inv[j] = w.inv;
     P->h2np[j] = w.h2np;
+    P->tbar[j] = w.tbar;
     P->nG[j] = jb.nG;
     const int TM = nGp / (pair ? 2 * BM : BM), TN = nGp / BN;
     P->tiles_m[j] = TM;

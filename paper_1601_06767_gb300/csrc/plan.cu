@@ -313,7 +313,7 @@ chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* d) {
   p->om_re.assign(d->freq_re, d->freq_re + d->n_freq);
   p->om_im.assign(d->freq_im, d->freq_im + d->n_freq);
   p->chain_pairs = d->chain_pairs ? d->chain_pairs : 32;
-  p->tc_herm = chi0::is_split(p) && (d->hermitian == 1 || (d->hermitian == 0 && p->n_products == 6));
+  p->tc_herm = chi0::is_split(p) && (d->hermitian == 1 || (d->hermitian == 0 && p->n_products != 4));
 
   chi0_status st = CHI0_OK;
   auto bail = [&](chi0_status s) {
