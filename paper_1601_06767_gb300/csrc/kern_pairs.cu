@@ -668,10 +668,14 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
 
 // per-lane constants of the group transform: stage twiddles e^{2 pi i (b mod h)/(2h)} for
 // h = Q/2, ..., 1 and the combination factors e^{2 pi i kk/n}, e^{4 pi i kk/n} of both output sets
-// NS output sets: lane b forms y(bitrev(b) + Q t) for t < NS
+// NS output sets: lane b forms y(bitrev(b) + Q t) for t < NS.  Per stage of span h
+// the lane keeps its sign (+1 for the lower lane of a pair, -1 for the upper one)
+// and its twiddle (1 for the lower lane), so that a butterfly is
+// x <- (x sign + partner) twiddle: two fused multiply-adds and a complex product.
 template <int Q, int NS = 2> struct WLConsts {
   static constexpr int LOGQ = Q == 32 ? 5 : 4;
   float2 tw[LOGQ];
+  float sg[LOGQ];
   float2 c1[NS], c2[NS];
   int kk;
 };
@@ -682,7 +686,10 @@ __device__ __forceinline__ WLConsts<Q, NS> wl_consts(int b) {
 #pragma unroll
   for (int s = 0; s < WLConsts<Q, NS>::LOGQ; ++s) {
     const int h = (Q / 2) >> s;
-    c.tw[s] = root<n>((b % h) * (n / (2 * h)));      // (b mod h)/(2h) of a turn
+    const bool upper = (b & h) != 0;
+    c.sg[s] = upper ? -1.f : 1.f;
+    // the upper lane's twiddle: (b mod h)/(2h) of a turn
+    c.tw[s] = upper ? root<n>((b % h) * (n / (2 * h))) : make_float2(1.f, 0.f);
   }
   c.kk = bitrev<Q>(b);
 #pragma unroll
@@ -699,16 +706,15 @@ __device__ __forceinline__ WLConsts<Q, NS> wl_consts(int b) {
 // x(a + 3b) lane b holds in x[a]
 template <int Q, int NS>
 __device__ __forceinline__ void wl_line(float2 (&x)[3], const WLConsts<Q, NS>& c, int b, float2 (&y)[NS]) {
+  // lower lane of a pair: x + partner; upper lane: (partner - x) twiddle
 #pragma unroll
   for (int s = 0; s < WLConsts<Q, NS>::LOGQ; ++s) {
     const int h = (Q / 2) >> s;
-    const bool upper = (b & h) != 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const float2 p = shfl_xor2(x[a], h);
-      const float2 sum = make_float2(x[a].x + p.x, x[a].y + p.y);
-      const float2 dif = cmul(make_float2(p.x - x[a].x, p.y - x[a].y), c.tw[s]);
-      x[a] = upper ? dif : sum;
+      const float2 u = make_float2(fmaf(c.sg[s], x[a].x, p.x), fmaf(c.sg[s], x[a].y, p.y));
+      x[a] = (h == 1) ? u : cmul(u, c.tw[s]);     // the last stage's twiddle is 1
     }
   }
 #pragma unroll
@@ -735,8 +741,8 @@ k_pair_planes_wl(const float2* __restrict__ psi_v, const int32_t* __restrict__ v
   float2* Uv = reinterpret_cast<float2*>(smem_raw);   // [n][ld]
   float2* X = Uv + n * ld;                            // [n][ldx]
   float2* Y = X + n * ldx;                            // [nk2][nk3]
-  const int i1 = blockIdx.x;
-  const int jv = blockIdx.y;
+  const int jv = blockIdx.x;
+  const int i1 = blockIdx.y;
   const int jc_begin = blockIdx.z * c_per_cta;
   const int jc_end = min(nc, jc_begin + c_per_cta);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -801,7 +807,8 @@ cudaError_t launch_planes_wl(const chi0_plan_s* p, const SphereQ& s, const void*
   // long conduction runs per CTA (the valence plane is loaded once per run), but enough CTAs
   int cpc = 16;
   while (cpc > 1 && (int64_t)p->n1 * nv * ((nc + cpc - 1) / cpc) < 4 * 152) cpc >>= 1;
-  dim3 grid(p->n1, nv, (nc + cpc - 1) / cpc);
+  // valence bands fastest: the CTAs running at a time share one plane's conduction rows in L2
+  dim3 grid(nv, p->n1, (nc + cpc - 1) / cpc);
   k_pair_planes_wl<Q><<<grid, WL_WARPS * 32, sm, st>>>((const float2*)psi_v, v_idx, v0, nv, (const float2*)psi_c,
                                                        c_idx, c0, nc, cpc, s.nk2, s.nk3, s.nk2p, s.nk3p, s.T2f,
                                                        s.T3f, (float2*)D);
@@ -904,7 +911,7 @@ cudaError_t try_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void* p
                            cudaStream_t st) {
   const int nk = std::max(s.nk2, s.nk3);
   if (!(p->n1 == p->n2 && p->n2 == p->n3)) return cudaErrorNotSupported;
-  if (p->n3 == 96 && nk <= WL_NKMAX && nv <= 65535)
+  if (p->n3 == 96 && nk <= WL_NKMAX)
     return launch_planes_wl<32>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
   if (nk > NKMAX) return cudaErrorNotSupported;
 #define CHI0_FFT_CASE(P, Q, TV, NCB)                                                                    \

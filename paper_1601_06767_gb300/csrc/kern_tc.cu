@@ -402,8 +402,10 @@ __device__ __forceinline__ int part_chain(const TcBatch& P, int q, int iw, int p
 
 // item -> (q, frequency, tile row, tile column); tiles are visited in groups of
 // `group` tile rows, column by column inside a group (keeps A and B tiles of
-// concurrently running CTAs close together in L2).  Hermitian mode visits the
-// tiles on or above the diagonal row by row: row tm starts at column rr * tm.
+// concurrently running CTAs close together in L2).  Hermitian mode visits only
+// the tiles on or above the diagonal (row tm from column rr * tm on), in the
+// same order: inside a group of rows, column by column, each column holding
+// the group's rows tm with rr * tm <= tn (a staircase over the first columns).
 __device__ __forceinline__ void decode_item(const TcBatch& P, int64_t item, int& q, int& iw, int& tm, int& tn) {
   q = 0;
   while (q + 1 < P.n_q && item >= P.item0[q + 1]) ++q;
@@ -413,14 +415,33 @@ __device__ __forceinline__ void decode_item(const TcBatch& P, int64_t item, int&
   iw = (int)(r / tt);
   int t = (int)(r - (int64_t)iw * tt);
   if (P.n_parts == 2) {
-    int row = 0, len = TN;
-    while (t >= len && row + 1 < TM) {
-      t -= len;
-      ++row;
-      len -= P.rr;
+    const int rr = P.rr, g = max(1, min(P.group, TM));
+    int r0 = 0, r1 = min(g, TM);
+    for (;;) {                                     // the group of rows holding item t
+      int cnt = 0;
+      for (int m = r0; m < r1; ++m) cnt += TN - rr * m;
+      if (t < cnt || r1 >= TM) break;
+      t -= cnt;
+      r0 = r1;
+      r1 = min(r1 + g, TM);
     }
-    tm = row;
-    tn = P.rr * row + t;
+    int col = rr * r0;
+    for (;;) {                                     // staircase columns: rows r0 .. min(r1, col/rr + 1) - 1
+      const int nrow = min(r1, col / rr + 1) - r0;
+      if (nrow >= r1 - r0 || t < nrow) {
+        if (t < nrow) {
+          tm = r0 + t;
+          tn = col;
+          return;
+        }
+        break;
+      }
+      t -= nrow;
+      ++col;
+    }
+    const int nrow = r1 - r0;                      // full columns from here on
+    tn = col + t / nrow;
+    tm = r0 + t % nrow;
     return;
   }
   const int g = min(P.group, TM);
