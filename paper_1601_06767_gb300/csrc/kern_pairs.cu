@@ -659,7 +659,7 @@ cudaError_t launch_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void
 // The shifted valence plane u_v' stays in shared memory for the whole run.
 // Shared memory: Uv[n][n+1], X[n][nk3|1], Y[nk2][nk3].
 // ---------------------------------------------------------------------------
-constexpr int WL_WARPS = 8;
+constexpr int WL_WARPS = 12;
 constexpr int WL_NKMAX = 32;
 
 __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
