@@ -355,6 +355,45 @@ __device__ __forceinline__ void issue_stage_np(const unsigned char* st, uint32_t
   }
 }
 
+// One-product stage holding ns <= NT k-slices of term 0 (slice t in the slots of
+// term t): t0 t0 for each slice, into the (Re, Im) accumulator pair.
+template <bool BF16, int NT, bool PAIR>
+__device__ __forceinline__ void issue_stage_1p(const unsigned char* st, uint32_t d_re, uint32_t d_im, bool first,
+                                               int ns) {
+  constexpr int B_BYTES = PAIR ? TILE_BYTES / 2 : TILE_BYTES;
+  const uint32_t id_pos = tc::idesc_f16(BF16, false, PAIR ? 2 * BM : BM, BN);
+  const uint32_t id_neg = tc::idesc_f16(BF16, true, PAIR ? 2 * BM : BM, BN);
+  const uint64_t d0 = tc::sdesc_kmajor_sw64(st);
+  constexpr uint64_t kTile = TILE_BYTES >> 4, kBTile = B_BYTES >> 4, kB0 = (uint64_t)(2 * NT * TILE_BYTES) >> 4;
+  uint32_t acc_re = first ? 0u : 1u, acc_im = acc_re;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    if (t >= ns) break;
+#pragma unroll
+    for (int ks = 0; ks < BK / 16; ++ks) {
+      const uint64_t ar = d0 + (uint64_t)t * kTile + (uint64_t)(ks * 2);
+      const uint64_t ai = d0 + (uint64_t)(NT + t) * kTile + (uint64_t)(ks * 2);
+      const uint64_t br = d0 + kB0 + (uint64_t)t * kBTile + (uint64_t)(ks * 2);
+      const uint64_t bi = d0 + kB0 + (uint64_t)(NT + t) * kBTile + (uint64_t)(ks * 2);
+      if constexpr (PAIR) {
+        tc::mma_f16_pair(d_re, ar, br, id_pos, acc_re);
+        acc_re = 1u;
+        tc::mma_f16_pair(d_re, ai, bi, id_pos, 1u);
+        tc::mma_f16_pair(d_im, ai, br, id_pos, acc_im);
+        acc_im = 1u;
+        tc::mma_f16_pair(d_im, ar, bi, id_neg, 1u);
+      } else {
+        tc::mma_f16(d_re, ar, br, id_pos, acc_re);
+        acc_re = 1u;
+        tc::mma_f16(d_re, ai, bi, id_pos, 1u);
+        tc::mma_f16(d_im, ai, br, id_pos, acc_im);
+        acc_im = 1u;
+        tc::mma_f16(d_im, ar, bi, id_neg, 1u);
+      }
+    }
+  }
+}
+
 // the product count as a compile-time constant: no per-MMA test in the issue loop
 template <bool BF16, int NT, bool PAIR = false>
 __device__ __forceinline__ void issue_stage(const unsigned char* st, uint32_t d_re, uint32_t d_im, bool first,
@@ -390,14 +429,21 @@ struct TcBatch {
   int64_t total_items;
 };
 
-// products of part `part` of an item, and its chain length in stages.  The W2
-// part of Hermitian mode with three products is below 2^-6 of chi0, so its
-// round-toward-zero bias allows chains eight times longer.
+// products of part `part` of an item, its stages and its chain length in stages.
+// A one-product part reads only term 0, so its stage holds NT consecutive
+// k-slices of term 0 in the slots of the NT terms (NT times fewer stages, the
+// same bytes per MMA).  The W2 part of Hermitian mode with one or three
+// products is below 2^-6 of chi0, so its round-toward-zero bias allows chains
+// eight times longer.
 __device__ __forceinline__ int part_products(const TcBatch& P, int q, int iw, int part) {
   return part ? (P.h2np[q][iw] & 15) : P.n_products;
 }
-__device__ __forceinline__ int part_chain(const TcBatch& P, int q, int iw, int part) {
-  return (part && P.h2np[q][iw] >= 16) ? min(P.nK, 8 * P.chain_k) : P.chain_k;
+template <int NT>
+__device__ __forceinline__ int part_stages(const TcBatch& P, int q, int iw, int part) {
+  return part_products(P, q, iw, part) == 1 ? (P.nK + NT - 1) / NT : P.nK;
+}
+__device__ __forceinline__ int part_chain(const TcBatch& P, int q, int iw, int part, int n_stages) {
+  return (part && P.h2np[q][iw] >= 16) ? min(n_stages, 8 * P.chain_k) : P.chain_k;
 }
 
 // item -> (q, frequency, tile row, tile column); tiles are visited in groups of
@@ -540,23 +586,30 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
         for (int part = 0; part < P.n_parts && ok; ++part) {
           // planes of the terms the part's products read (t2 only with six products)
           const int npp = part_products(P, q, iw, part);
-          const int nt = npp == 1 ? 1 : ((NT == 3 && npp != 6) ? 2 : NT);
+          const bool one = npp == 1;                  // k-slices of term 0 in the term slots
+          const int nt = one ? 1 : ((NT == 3 && npp != 6) ? 2 : NT);
+          const int nks = part_stages<NT>(P, q, iw, part);
           const int plane0 = (part * P.n_freq + iw) * PL;
           const int row_a = tm * BM, row_b = tn * BN;
-          for (int kc = 0; kc < nK; ++kc, ++gs) {
+          for (int kc = 0; kc < nks; ++kc, ++gs) {
             const int s = slot;
             if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, status, 1, WAIT_BUDGET_NS)) { ok = false; break; }
             if (++slot == STAGES) {
               slot = 0;
               ph ^= 1u;
             }
-            tc::mbar_arrive_expect_tx(&bar->full[s], 4 * nt * TILE_BYTES);
+            const int ns = one ? min(NT, nK - kc * NT) : nt;   // slices (one product) or terms loaded
+            tc::mbar_arrive_expect_tx(&bar->full[s], 4 * ns * TILE_BYTES);
             unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
 #pragma unroll
             for (int j = 0; j < PL; ++j) {
-              if (j % NT >= nt) continue;
-              tc::tma_load_3d(st + j * TILE_BYTES, &P.tmA[q], &bar->full[s], kc * BK, row_a, plane0 + j);
-              tc::tma_load_3d(st + (PL + j) * TILE_BYTES, &P.tmB[q], &bar->full[s], kc * BK, row_b, j);
+              const int t = j % NT;
+              if (t >= ns) continue;
+              // one product: slot j takes term 0 of its re/im half at k-slice kc NT + t
+              const int pa = one ? (j / NT) * NT : j;
+              const int kx = one ? (kc * NT + t) * BK : kc * BK;
+              tc::tma_load_3d(st + j * TILE_BYTES, &P.tmA[q], &bar->full[s], kx, row_a, plane0 + pa);
+              tc::tma_load_3d(st + (PL + j) * TILE_BYTES, &P.tmB[q], &bar->full[s], kx, row_b, pa);
             }
           }
         }
@@ -576,10 +629,11 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
         int q, iw, tm, tn;
         decode_item(P, item, q, iw, tm, tn);
         for (int part = 0; part < P.n_parts && ok; ++part) {
-          const int np = part_products(P, q, iw, part), ck = part_chain(P, q, iw, part);
+          const int np = part_products(P, q, iw, part), nks = part_stages<NT>(P, q, iw, part);
+          const int ck = part_chain(P, q, iw, part, nks);
           // pos: stage within the accumulation chain; s, ph: ring slot and its phase (counters,
           // not divisions, on this single issuing thread)
-          for (int kc = 0, pos = 0; kc < nK; ++kc, ++gs) {
+          for (int kc = 0, pos = 0; kc < nks; ++kc, ++gs) {
             const int buf = (int)(gc & 1);
             const bool first = pos == 0;
             if (first) {
@@ -601,9 +655,10 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
             tc::fence_after();
             const unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
             const uint32_t d_re = tbase + buf * 256, d_im = d_re + 128;
-            issue_stage<BF16, NT>(st, d_re, d_im, first, np);
+            if (np == 1) issue_stage_1p<BF16, NT, false>(st, d_re, d_im, first, min(NT, nK - kc * NT));
+            else issue_stage<BF16, NT>(st, d_re, d_im, first, np);
             tc::mma_commit(&bar->empty[s]);
-            if (++pos == ck || kc == nK - 1) {
+            if (++pos == ck || kc == nks - 1) {
               tc::mma_commit(&bar->tfull[buf]);
               ++gc;
               pos = 0;
@@ -624,8 +679,9 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
       int q, iw, tm, tn;
       decode_item(P, item, q, iw, tm, tn);
       for (int part = 0; part < P.n_parts && ok; ++part) {
-      const int ck = part_chain(P, q, iw, part);
-      const int nch = (nK + ck - 1) / ck;
+      const int nks = part_stages<NT>(P, q, iw, part);
+      const int ck = part_chain(P, q, iw, part, nks);
+      const int nch = (nks + ck - 1) / ck;
       float sre[64], sim[64];
 #pragma unroll
       for (int i = 0; i < 64; ++i) { sre[i] = 0.f; sim[i] = 0.f; }
@@ -752,24 +808,30 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
         const int brow = tn * BN + (int)rank * (BN / 2);   // this CTA's 64 rows of B
         for (int part = 0; part < P.n_parts && ok; ++part) {
           const int npp = part_products(P, q, iw, part);
-          const int nt = npp == 1 ? 1 : ((NT == 3 && npp != 6) ? 2 : NT);
+          const bool one = npp == 1;                  // k-slices of term 0 in the term slots
+          const int nt = one ? 1 : ((NT == 3 && npp != 6) ? 2 : NT);
+          const int nks = part_stages<NT>(P, q, iw, part);
           const int plane0 = (part * P.n_freq + iw) * PL;
-          for (int kc = 0; kc < nK; ++kc, ++gs) {
+          for (int kc = 0; kc < nks; ++kc, ++gs) {
             const int s = slot;
             if (!tc::mbar_wait(&bar->empty[s], ph ^ 1u, status, 1, WAIT_BUDGET_NS)) { ok = false; break; }
             if (++slot == STAGES) {
               slot = 0;
               ph ^= 1u;
             }
+            const int ns = one ? min(NT, nK - kc * NT) : nt;
             // the first CTA's barrier counts the loads of both CTAs
-            if (leader) tc::mbar_arrive_expect_tx(&bar->full[s], 4 * nt * (RG::A_BYTES + RG::B_BYTES));
+            if (leader) tc::mbar_arrive_expect_tx(&bar->full[s], 4 * ns * (RG::A_BYTES + RG::B_BYTES));
             const uint32_t fb = tc::mapa(&bar->full[s], 0);
             unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
 #pragma unroll
             for (int j = 0; j < PL; ++j) {
-              if (j % NT >= nt) continue;
-              tc::tma_load_3d_pair(st + j * RG::A_BYTES, &P.tmA[q], fb, kc * BK, arow, plane0 + j);
-              tc::tma_load_3d_pair(st + PL * RG::A_BYTES + j * RG::B_BYTES, &P.tmB[q], fb, kc * BK, brow, j);
+              const int t = j % NT;
+              if (t >= ns) continue;
+              const int pa = one ? (j / NT) * NT : j;
+              const int kx = one ? (kc * NT + t) * BK : kc * BK;
+              tc::tma_load_3d_pair(st + j * RG::A_BYTES, &P.tmA[q], fb, kx, arow, plane0 + pa);
+              tc::tma_load_3d_pair(st + PL * RG::A_BYTES + j * RG::B_BYTES, &P.tmB[q], fb, kx, brow, pa);
             }
           }
         }
@@ -790,10 +852,11 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
         int q, iw, tm, tn;
         decode_item(P, item, q, iw, tm, tn);
         for (int part = 0; part < P.n_parts && ok; ++part) {
-          const int np = part_products(P, q, iw, part), ck = part_chain(P, q, iw, part);
+          const int np = part_products(P, q, iw, part), nks = part_stages<NT>(P, q, iw, part);
+          const int ck = part_chain(P, q, iw, part, nks);
           // pos: stage within the accumulation chain; s, ph: ring slot and its phase (counters,
           // not divisions, on this single issuing thread)
-          for (int kc = 0, pos = 0; kc < nK; ++kc, ++gs) {
+          for (int kc = 0, pos = 0; kc < nks; ++kc, ++gs) {
             const int buf = (int)(gc & 1);
             const bool first = pos == 0;
             if (first) {
@@ -815,9 +878,10 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
             tc::fence_after();
             const unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
             const uint32_t d_re = tbase + buf * 256, d_im = d_re + 128;
-            issue_stage<BF16, NT, true>(st, d_re, d_im, first, np);
+            if (np == 1) issue_stage_1p<BF16, NT, true>(st, d_re, d_im, first, min(NT, nK - kc * NT));
+            else issue_stage<BF16, NT, true>(st, d_re, d_im, first, np);
             tc::mma_commit_pair(&bar->empty[s], 0x3);
-            if (++pos == ck || kc == nK - 1) {
+            if (++pos == ck || kc == nks - 1) {
               tc::mma_commit_pair(&bar->tfull[buf], 0x3);
               ++gc;
               pos = 0;
@@ -838,8 +902,9 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
       int q, iw, tm, tn;
       decode_item(P, item, q, iw, tm, tn);
       for (int part = 0; part < P.n_parts && ok; ++part) {
-      const int ck = part_chain(P, q, iw, part);
-      const int nch = (nK + ck - 1) / ck;
+      const int nks = part_stages<NT>(P, q, iw, part);
+      const int ck = part_chain(P, q, iw, part, nks);
+      const int nch = (nks + ck - 1) / ck;
       float sre[64], sim[64];
 #pragma unroll
       for (int i = 0; i < 64; ++i) { sre[i] = 0.f; sim[i] = 0.f; }
