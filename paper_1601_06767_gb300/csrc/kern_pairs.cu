@@ -642,24 +642,16 @@ cudaError_t launch_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void
 }
 
 // ---------------------------------------------------------------------------
-// Stages 1+2 on the n^3 grids n = 3Q with group-cooperative transforms (used
-// for 96^3, Q = 32; on 48^3 the per-thread register FFTs above measured faster
-// than Q = 16): a group of Q lanes transforms one line (a warp holds 32/Q lines).  A line is split as i = a + 3b (a < 3, b < Q): lane
-// b of the group holds x(3b), x(3b+1), x(3b+2) (24 contiguous bytes, so the
-// group reads its row at once), the three Q-point transforms
-// F_a(m) = sum_b x(a+3b) e^{2 pi i m b/Q} run across the group's lanes by
-// radix-2 decimation in frequency (one shuffle per value and stage; lane b
-// ends with F_a(bitrev(b))), and lane b forms, for kk = bitrev(b) + Q t,
-//   y(kk) = F_0(kk mod Q) + e^{2 pi i kk/n} F_1(kk mod Q) + e^{4 pi i kk/n} F_2(kk mod Q)
-// (t = 0, 1: the kept extents are below 32).
-// One CTA per (plane i1, valence band) and a run of conduction bands:
-//   stage 1: rows i2 of conj(u_v') u_c, transformed along i3 into X[i2][k3];
-//   stage 2: the kept columns k3 of X, transformed along i2 into Y[k2][k3];
-//   Y is copied to D[pair][i1] (contiguous nk2 x nk3 values).
-// The shifted valence plane u_v' stays in shared memory for the whole run.
-// Shared memory: Uv[n][n+1], X[n][nk3|1], Y[nk2][nk3].
-// ---------------------------------------------------------------------------
-constexpr int WL_WARPS = 12;
+// Stages 1+2 on the 96^3 grid (n = 3Q, Q = 32) with warp-cooperative
+// transforms: a warp transforms one line.  A line is split as i = a + 3b
+// (a < 3, b < Q): lane b holds x(3b), x(3b+1), x(3b+2) (24 contiguous bytes,
+// so the warp reads its row at once), the three Q-point transforms
+// F_a(m) = sum_b x(a+3b) e^{2 pi i m b/Q} run across the lanes by radix-2
+// decimation in frequency (one shuffle per value and stage; lane b ends with
+// F_a(bitrev(b))), and lane b forms, for kk = bitrev(b) + Q t (t < 3),
+//   y(kk) = F_0(kk mod Q) + e^{2 pi i kk/n} F_1(kk mod Q) + e^{4 pi i kk/n} F_2(kk mod Q).
+// (On 48^3, Q = 16 with two lines per warp measured slower than the
+// per-thread register FFTs above, so 48^3 keeps those.)
 constexpr int WL_NKMAX = 32;
 
 __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
@@ -725,93 +717,96 @@ __device__ __forceinline__ void wl_line(float2 (&x)[3], const WLConsts<Q, NS>& c
   }
 }
 
+// One CTA per (valence band, plane i1) and a run of conduction bands:
+//   stage 1: warp w transforms rows i2 = w, w+8, ... of conj(u_v) u_c along i3 into X[i2][k3];
+//   stage 2: warp w transforms the kept columns k3 = w, w+8, ... of X along i2 into Y[k2][k3];
+//   Y is copied to D[pair][i1] (contiguous nk2 x nk3 values).
+// No frequency shift is applied to the inputs: a line keeps the outputs y(k)
+// for k in [kmin, kmin + nk) mod n, which lie in at most two of the three output
+// sets y(bitrev(b) + Q t) (all three are formed).  Both rows of a pair are read
+// from global memory (the valence row once per conduction band, from L2), so
+// the CTA holds only X and Y (24 KB) and several CTAs fit on an SM.
+constexpr int WN_WARPS = 8;
+
 template <int Q>
-__global__ void __launch_bounds__(WL_WARPS * 32, 2)
-k_pair_planes_wl(const float2* __restrict__ psi_v, const int32_t* __restrict__ v_idx, int v0, int nv,
+__global__ void __launch_bounds__(WN_WARPS * 32)
+k_pair_planes_wn(const float2* __restrict__ psi_v, const int32_t* __restrict__ v_idx, int v0, int nv,
                  const float2* __restrict__ psi_c, const int32_t* __restrict__ c_idx, int c0, int nc, int c_per_cta,
-                 int nk2, int nk3, int nk2p, int nk3p, const float2* __restrict__ T2, const float2* __restrict__ T3,
-                 float2* __restrict__ D) {
-  constexpr int n = 3 * Q, ld = n + 1;
-  constexpr int G = 32 / Q;                           // lines per warp
-  constexpr int LINES = WL_WARPS * G;                 // lines per CTA pass
+                 int k2min, int k3min, int nk2, int nk3, float2* __restrict__ D) {
+  static_assert(Q == 32, "one line per warp");
+  constexpr int n = 3 * Q;
   constexpr int64_t nr = (int64_t)n * n * n;
   constexpr int plane = n * n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ldx = nk3 | 1;
-  float2* Uv = reinterpret_cast<float2*>(smem_raw);   // [n][ld]
-  float2* X = Uv + n * ld;                            // [n][ldx]
+  float2* X = reinterpret_cast<float2*>(smem_raw);   // [n][ldx]
   float2* Y = X + n * ldx;                            // [nk2][nk3]
   const int jv = blockIdx.x;
   const int i1 = blockIdx.y;
   const int jc_begin = blockIdx.z * c_per_cta;
   const int jc_end = min(nc, jc_begin + c_per_cta);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b = lane % Q, line0 = warp * G + lane / Q;
   const int box = nk2 * nk3;
   if (jv >= nv || jc_begin >= jc_end) return;
-  const WLConsts<Q, 2> cst = wl_consts<Q, 2>(b);
-  {
-    const int64_t band = v_idx ? v_idx[v0 + jv] : v0 + jv;
-    const float2* src = psi_v + band * nr + (int64_t)i1 * plane;
-    for (int e = threadIdx.x; e < plane; e += blockDim.x) {
-      const int i2 = e / n, i3 = e - i2 * n;
-      // shift to the lowest kept frequencies: u_v * conj(e^{2 pi i (k3min i3 + k2min i2)/n})
-      const float2 sh = cmul(T3[(size_t)i3 * nk3p], T2[(size_t)i2 * nk2p]);
-      Uv[i2 * ld + i3] = cmul(src[e], make_float2(sh.x, -sh.y));
-    }
+  const WLConsts<Q, 3> cst = wl_consts<Q, 3>(lane);
+  // slot of output set t in the kept range along i3 / i2, or -1
+  int o3[3], o2[3];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const int k = cst.kk + Q * t;
+    const int d3 = ((k - k3min) % n + n) % n, d2 = ((k - k2min) % n + n) % n;
+    o3[t] = d3 < nk3 ? d3 : -1;
+    o2[t] = d2 < nk2 ? d2 : -1;
   }
-  __syncthreads();
+  const int64_t vband = v_idx ? v_idx[v0 + jv] : v0 + jv;
+  const float2* vsrc = psi_v + vband * nr + (int64_t)i1 * plane;
   for (int jc = jc_begin; jc < jc_end; ++jc) {
     const int64_t band = c_idx ? c_idx[c0 + jc] : c0 + jc;
     const float2* csrc = psi_c + band * nr + (int64_t)i1 * plane;
-    // stage 1: rows (n is a multiple of the lines per pass)
-    for (int i2 = line0; i2 < n; i2 += LINES) {
-      const float2* uc = csrc + i2 * n + 3 * b;
-      const float2* uv = Uv + i2 * ld + 3 * b;
-      float2 x[3];
+    // stage 1: rows
+    for (int i2 = warp; i2 < n; i2 += WN_WARPS) {
+      const float2* uc = csrc + i2 * n + 3 * lane;
+      const float2* uv = vsrc + i2 * n + 3 * lane;
+      float2 x[3], y[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) x[a] = cconjmul(uv[a], __ldg(uc + a));
-      float2 y[2];
-      wl_line<Q, 2>(x, cst, b, y);
-      if (cst.kk < nk3) X[i2 * ldx + cst.kk] = y[0];
-      if (cst.kk + Q < nk3) X[i2 * ldx + cst.kk + Q] = y[1];
+      for (int a = 0; a < 3; ++a) x[a] = cconjmul(__ldg(uv + a), __ldg(uc + a));
+      wl_line<Q, 3>(x, cst, lane, y);
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+        if (o3[t] >= 0) X[i2 * ldx + o3[t]] = y[t];
     }
     __syncthreads();
-    // stage 2: kept columns; a pass runs warp-uniformly, groups past the last column idle
-    for (int k30 = 0; k30 < nk3; k30 += LINES) {
-      const int k3 = k30 + line0;
-      const bool ok = k3 < nk3;
-      float2 x[3];
+    // stage 2: kept columns
+    for (int k3 = warp; k3 < nk3; k3 += WN_WARPS) {
+      float2 x[3], y[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) x[a] = ok ? X[(3 * b + a) * ldx + k3] : make_float2(0.f, 0.f);
-      float2 y[2];
-      wl_line<Q, 2>(x, cst, b, y);
-      if (ok && cst.kk < nk2) Y[cst.kk * nk3 + k3] = y[0];
-      if (ok && cst.kk + Q < nk2) Y[(cst.kk + Q) * nk3 + k3] = y[1];
+      for (int a = 0; a < 3; ++a) x[a] = X[(3 * lane + a) * ldx + k3];
+      wl_line<Q, 3>(x, cst, lane, y);
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+        if (o2[t] >= 0) Y[o2[t] * nk3 + k3] = y[t];
     }
     __syncthreads();
     float2* dst = D + ((int64_t)(jv * nc + jc) * n + i1) * box;
     for (int e = threadIdx.x; e < box; e += blockDim.x) dst[e] = Y[e];
-    // the next run's stage 1 writes X only after the barrier above, and Y after its own first barrier
   }
 }
 
 template <int Q>
-cudaError_t launch_planes_wl(const chi0_plan_s* p, const SphereQ& s, const void* psi_v, const int32_t* v_idx,
+cudaError_t launch_planes_wn(const chi0_plan_s* p, const SphereQ& s, const void* psi_v, const int32_t* v_idx,
                              int v0, int nv, const void* psi_c, const int32_t* c_idx, int c0, int nc, void* D,
                              cudaStream_t st) {
   constexpr int n = 3 * Q;
-  const size_t sm = ((size_t)n * (n + 1) + (size_t)n * (s.nk3 | 1) + (size_t)s.nk2 * s.nk3) * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(k_pair_planes_wl<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const size_t sm = ((size_t)n * (s.nk3 | 1) + (size_t)s.nk2 * s.nk3) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_pair_planes_wn<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  // long conduction runs per CTA (the valence plane is loaded once per run), but enough CTAs
   int cpc = 16;
-  while (cpc > 1 && (int64_t)p->n1 * nv * ((nc + cpc - 1) / cpc) < 4 * 152) cpc >>= 1;
+  while (cpc > 1 && (int64_t)p->n1 * nv * ((nc + cpc - 1) / cpc) < 8 * 152) cpc >>= 1;
   // valence bands fastest: the CTAs running at a time share one plane's conduction rows in L2
   dim3 grid(nv, p->n1, (nc + cpc - 1) / cpc);
-  k_pair_planes_wl<Q><<<grid, WL_WARPS * 32, sm, st>>>((const float2*)psi_v, v_idx, v0, nv, (const float2*)psi_c,
-                                                       c_idx, c0, nc, cpc, s.nk2, s.nk3, s.nk2p, s.nk3p, s.T2f,
-                                                       s.T3f, (float2*)D);
+  k_pair_planes_wn<Q><<<grid, WN_WARPS * 32, sm, st>>>((const float2*)psi_v, v_idx, v0, nv, (const float2*)psi_c,
+                                                       c_idx, c0, nc, cpc, s.k2min, s.k3min, s.nk2, s.nk3,
+                                                       (float2*)D);
   return cudaGetLastError();
 }
 
@@ -912,7 +907,7 @@ cudaError_t try_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void* p
   const int nk = std::max(s.nk2, s.nk3);
   if (!(p->n1 == p->n2 && p->n2 == p->n3)) return cudaErrorNotSupported;
   if (p->n3 == 96 && nk <= WL_NKMAX)
-    return launch_planes_wl<32>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
+    return launch_planes_wn<32>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
   if (nk > NKMAX) return cudaErrorNotSupported;
 #define CHI0_FFT_CASE(P, Q, TV, NCB)                                                                    \
   if (nk <= 12) return launch_fft_planes<P, Q, 12, TV, NCB>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st); \
