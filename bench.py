@@ -923,7 +923,7 @@ def run_case(args):
     g.manual_seed(0)
     herm = {"auto": None, "on": True, "off": False}[args.hermitian]
     with pkg.Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision=args.precision, max_pairs=K,
-                      gw=prob.gw, n_products=args.n_products, hermitian=herm) as plan:
+                      gw=prob.gw, n_products=args.n_products, hermitian=herm, chain_pairs=args.chain_pairs) as plan:
         if args.case == "contract" and not args.no_tune:
             plan.autotune(0)          # the variant the benchmark runs
         if args.case == "wfn":
@@ -1169,6 +1169,8 @@ def main(argv=None):
                     help="split precision of the headline (256-atom-sized) build")
     ap.add_argument("--n-products", type=int, default=0)
     ap.add_argument("--hermitian", choices=["auto", "on", "off"], default="auto")
+    ap.add_argument("--chain-pairs", type=int, default=0,
+                    help="pairs per TMEM accumulation chain (multiple of 32; 0 = the library's default)")
     ap.add_argument("--c5-blocks", type=int, default=12,
                     help="conduction blocks (16 bands, 8192 pairs) of the 256-atom-sized workload per step")
     ap.add_argument("--c2-precision", choices=["bf16", "fp16"], default="bf16",

@@ -693,26 +693,32 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
         }
         tc::fence_after();
         const uint32_t ta = tbase + ((uint32_t)(quad * 32) << 16) + buf * 256 + half * 64;
+        // one load in flight (the epilogue's sums fill the registers); the buffer is
+        // released as soon as its last values are in registers, before they are added
         float v[32];
         tc::tmem_ld32(ta, v);
         tc::tmem_ld_wait();
+        tc::reg_after_wait(v);
 #pragma unroll
         for (int i = 0; i < 32; ++i) sre[i] += v[i];
         tc::tmem_ld32(ta + 32, v);
         tc::tmem_ld_wait();
+        tc::reg_after_wait(v);
 #pragma unroll
         for (int i = 0; i < 32; ++i) sre[32 + i] += v[i];
         tc::tmem_ld32(ta + 128, v);
         tc::tmem_ld_wait();
+        tc::reg_after_wait(v);
 #pragma unroll
         for (int i = 0; i < 32; ++i) sim[i] += v[i];
         tc::tmem_ld32(ta + 160, v);
         tc::tmem_ld_wait();
-#pragma unroll
-        for (int i = 0; i < 32; ++i) sim[32 + i] += v[i];
+        tc::reg_after_wait(v);
         tc::fence_before();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&bar->tempty[buf]);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) sim[32 + i] += v[i];
       }
       const int nG = P.nG[q];
       const int G = tm * BM + row;
@@ -916,26 +922,32 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
         }
         tc::fence_after();
         const uint32_t ta = tbase + ((uint32_t)(quad * 32) << 16) + buf * 256 + half * 64;
+                // one load in flight (the epilogue's sums fill the registers); the buffer is
+        // released as soon as its last values are in registers, before they are added
         float v[32];
         tc::tmem_ld32(ta, v);
         tc::tmem_ld_wait();
+        tc::reg_after_wait(v);
 #pragma unroll
         for (int i = 0; i < 32; ++i) sre[i] += v[i];
         tc::tmem_ld32(ta + 32, v);
         tc::tmem_ld_wait();
+        tc::reg_after_wait(v);
 #pragma unroll
         for (int i = 0; i < 32; ++i) sre[32 + i] += v[i];
         tc::tmem_ld32(ta + 128, v);
         tc::tmem_ld_wait();
+        tc::reg_after_wait(v);
 #pragma unroll
         for (int i = 0; i < 32; ++i) sim[i] += v[i];
         tc::tmem_ld32(ta + 160, v);
         tc::tmem_ld_wait();
-#pragma unroll
-        for (int i = 0; i < 32; ++i) sim[32 + i] += v[i];
+        tc::reg_after_wait(v);
         tc::fence_before();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive_cluster(tc::mapa(&bar->tempty[buf], 0));
+#pragma unroll
+        for (int i = 0; i < 32; ++i) sim[32 + i] += v[i];
       }
       const int nG = P.nG[q];
       const int G = tm * 2 * BM + (int)rank * BM + row;

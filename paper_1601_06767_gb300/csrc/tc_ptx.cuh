@@ -177,6 +177,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// After tmem_ld_wait: an empty statement per register that reads and "writes" it,
+// ordered after the wait (volatile statements keep their order), so that no use of
+// the loaded values is scheduled before the wait.
+__device__ __forceinline__ void reg_after_wait(float (&v)[32]) {
+#pragma unroll
+  for (int i = 0; i < 32; ++i) asm volatile("" : "+f"(v[i]));
+}
 
 // Shared-memory matrix descriptor (tcgen05): K-major tile whose rows are 64 bytes,
 // written by TMA with 64-byte swizzling; 8-row core groups are 512 bytes apart.
