@@ -917,6 +917,8 @@ def run_case(args):
     prob = make_problem("c5", n_imag=1) if big else make_problem("c2")
     nG = prob.gvec[0].shape[0]
     K, nv, nc = (8192, 512, 16) if big else (8192, 128, 64)
+    if big and args.case_pairs:
+        K, nc = args.case_pairs, args.case_pairs // 512
     if big:
         args.case = args.case[:-1]
     g = torch.Generator(device="cuda")
@@ -971,7 +973,8 @@ def run_case(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if args.case == "contract":
             # the 256-atom-sized case takes a block of the benchmark's sample from mid-spectrum
-            cols = c5_sample_bands(prob.n_c, 12, prob.seed + 5)[4 * 16:5 * 16] if big else np.arange(nc)
+            # (nc consecutive bands from the start of that block for --case-pairs)
+            cols = c5_sample_bands(prob.n_c, 12, prob.seed + 5)[4 * 16] + np.arange(nc) if big else np.arange(nc)
             Ev = torch.tensor(prob.E_v[:nv], device="cuda")
             Ec = torch.tensor(prob.E_c[cols], device="cuda")
             chi = plan.new_chi(0)
@@ -1192,6 +1195,8 @@ def main(argv=None):
                                        "peaks"],
                     default=None, help="run a small fixed case for profiling or a separate workload")
     ap.add_argument("--c5-frac", type=float, default=1.0, help="fraction of conduction bands timed in --case c3")
+    ap.add_argument("--case-pairs", type=int, default=0,
+                    help="--case contract5 / pairs5: pairs per call (a multiple of 512; 0 = 8192)")
     args = ap.parse_args(argv)
     if args.case == "c3":
         return run_c3(args)

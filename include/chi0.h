@@ -87,7 +87,11 @@ typedef struct {
                                 block (0 when that does not shrink the H2 weights) and rho bounds
                                 max|g| / max|Re f|: H2 takes one product where rho <= 2^-11 (FP16;
                                 2^-15 BF16), three where rho <= 2^-6, else n_products (its error scales
-                                with rho).  0 = automatic (on except for n_products 4), 1 = on, -1 = off */
+                                with rho).  0 = automatic: on except for n_products 4 and except where
+                                a launch would leave SMs idle (with T = ceil(n_G / 128) tiles, plain
+                                mode has n_freq T^2 work items, Hermitian mode n_freq T (T + 1) / 2, each
+                                a quarter dearer; the mode with fewer estimated waves over the SMs
+                                wins); 1 = on, -1 = off.  chi0_plan_hermitian reports the choice */
 } chi0_plan_desc;
 
 /* Create a plan: validates the description, analyses each G sphere for the
@@ -98,6 +102,10 @@ chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* desc);
 
 /* Release a plan and its workspace (synchronises the device first).  NULL is a no-op. */
 chi0_status chi0_plan_destroy(chi0_plan plan);
+
+/* *on = 1 when the plan contracts the Hermitian parts H1, H2 (the hermitian field
+ * of the description, with its automatic choice resolved), else 0. */
+chi0_status chi0_plan_hermitian(chi0_plan plan, int* on);
 
 /* Text of the last error of this plan (plan-owned, valid until the next call
  * on the plan), or of the last failed plan creation when plan is NULL. */

@@ -61,6 +61,7 @@ SIGNATURES = [
     ("chi0_sigma_coh", _I, [_VP, _I, _VP, _I, _I, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("chi0_autotune", _I, [_VP, _I, _I, _VP, _VP]),
     ("chi0_get_tuning", _I, [_VP, _VP, _VP, _VP]),
+    ("chi0_plan_hermitian", _I, [_VP, _VP]),
     ("chi0_profile_enable", _I, [_VP, _I]),
     ("chi0_profile_reset", _I, [_VP]),
     ("chi0_profile_read", _I, [_VP, _VP, _VP]),

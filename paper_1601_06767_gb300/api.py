@@ -65,12 +65,12 @@ class Chi0Plan:
         d.max_pairs = int(max_pairs)
         d.chain_pairs = int(chain_pairs)
         d.hermitian = 0 if hermitian is None else (1 if hermitian else -1)
-        # the library's rule: split precisions only; automatic means on except for four products
-        eff_np = int(n_products) or (3 if precision == "fp16" else 6)
-        self.hermitian = precision != "fp64" and (bool(hermitian) if hermitian is not None else eff_np != 4)
         h = C.c_void_p()
         L.check(lib.chi0_plan_create(C.byref(h), C.byref(d)), None)
         self._h = h
+        on = C.c_int(0)
+        L.check(lib.chi0_plan_hermitian(h, C.byref(on)), h)
+        self.hermitian = bool(on.value)   # the library's choice (split precisions only)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.cdtype = torch.complex128 if precision == "fp64" else torch.complex64
 

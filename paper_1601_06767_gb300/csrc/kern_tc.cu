@@ -7,7 +7,8 @@
 // a real product keeps the term products t_i t_j with i + j < NT (plus t1 t1
 // for the four-product two-term variant).  Operands are first scaled by exact
 // powers of two so that the largest magnitude of the block sits near 2^14
-// (keeps FP16 terms normal; harmless for BF16) and the scale is undone in FP64.
+// (keeps FP16 terms normal; harmless for BF16) and the scale is undone exactly
+// when the sums are widened to FP64.
 //
 // pack:     M block [K][nG] (FP32 complex) and f -> K-major 16-bit planes
 //           B = {Mr_t..., Mi_t...}[nGp][Kp], A_w = {Wr_t..., Wi_t...}[nGp][Kp].
@@ -15,7 +16,7 @@
 //           loads into a 3-stage ring, warp 1 issues tcgen05.mma into two
 //           double-buffered TMEM accumulator pairs (Re, Im), warps 2..9 drain
 //           finished accumulation chains into FP32 registers and finally add
-//           the tile into chi0 in FP64.
+//           the tile into chi0 by FP64 reductions (the additions run in L2).
 //
 // Hermitian mode: with a real ratio t per frequency and block of pairs,
 //   f_p = Re f_p (1 + i t) + i g_p,   g_p = Im f_p - t Re f_p,
@@ -181,9 +182,10 @@ __global__ void k_scales(const unsigned int* __restrict__ amax, const unsigned i
       const float tlo = float_of_ord(tr[2 * iw]), thi = float_of_ord(tr[2 * iw + 1]);
       const float half = 0.5f * (thi - tlo);
       const bool shift = isfinite(tlo) && isfinite(thi) && isfinite(half) && half * fr < fi;
-      const double t = shift ? 0.5 * ((double)tlo + (double)thi) : 0.0;
-      // the bound on |g| (with a margin for the FP32 ratio range), else max|Im f|
-      const float gmax = shift ? half * fr * 1.0001f + fr * 1e-7f : fi;
+      // t is rounded to FP32: the merge forms (1 + i t) H1 in FP32 with this same t
+      const float t = shift ? (float)(0.5 * ((double)tlo + (double)thi)) : 0.f;
+      // the bound on |g| (margins for the FP32 ratio range and the rounding of t), else max|Im f|
+      const float gmax = shift ? half * fr * 1.0001f + fr * 1e-7f * (1.f + fabsf(t)) : fi;
       const float rho = fr > 0.f ? gmax / fr : 0.f;
       // |components of W1| <= max|Re f| max|M|, of W2 <= gmax max|M|
       const float s1 = pow2_scale(fr * mM), s2 = pow2_scale(gmax * mM);
@@ -191,7 +193,7 @@ __global__ void k_scales(const unsigned int* __restrict__ amax, const unsigned i
       scale[1 + n_freq + iw] = s2;
       inv[iw] = 1.0 / ((double)sM * (double)s1);
       inv[n_freq + iw] = 1.0 / ((double)sM * (double)s2);
-      tbar[iw] = t;
+      tbar[iw] = (double)t;
       // a small W2 part needs fewer products (errors scale with rho) and takes long chains (flag 16)
       const float one_term = bf16 ? ldexpf(1.f, -15) : ldexpf(1.f, -11);
       h2np[iw] = rho <= one_term ? 1 + 16 : (rho <= ldexpf(1.f, -6) ? 3 + 16 : n_products);
@@ -499,21 +501,47 @@ __device__ __forceinline__ void decode_item(const TcBatch& P, int64_t item, int&
   tn = within / rows;
 }
 
-// Add one drained part of a tile row (row G, columns Hb..Hb+63) into chi0 of
-// one frequency.  Plain mode: chi[G][H] += s (re + i im).  Hermitian mode: part 0
-// holds H1(G, H), part 1 holds H2(G, H); chi[G][H] += (1 + i t) H1 + i H2 for
-// G <= H and chi[H][G] += (1 + i t) conj(H1) + i conj(H2) for G < H.
+// x 2^k as a double, exactly, by integer operations on the bits (the SM's FP64 pipe
+// is narrow): zero and subnormal x give a signed zero, a result below the
+// smallest normal double gives zero, Inf and NaN stay Inf and NaN.
+__device__ __forceinline__ double f64_of_f32_pow2(float x, int k) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t sign = u & 0x80000000u;
+  const int e = (int)((u >> 23) & 0xffu);
+  const int ed = e + (1023 - 127) + k;
+  uint32_t hi = sign | ((uint32_t)ed << 20) | ((u >> 3) & 0xfffffu);
+  uint32_t lo = u << 29;
+  if (e == 0 || ed <= 0) {
+    hi = sign;
+    lo = 0u;
+  } else if (e == 255 || ed >= 2047) {
+    hi = sign | 0x7ff00000u | (e == 255 ? (u >> 3) & 0xfffffu : 0u);
+    lo = e == 255 ? lo : 0u;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// chi0 element += v 2^k: the FP64 addition runs in L2 (a reduction, no value returned)
+__device__ __forceinline__ void red_add_pow2(double* a, float v, int k) {
+  atomicAdd(a, f64_of_f32_pow2(v, k));
+}
+
+// Add one drained part of a tile row (row G, columns Hb..Hb+63; FP32 sums whose
+// scale is 2^-k) into chi0 of one frequency.  Plain mode: chi[G][H] += 2^k (re +
+// i im).  Hermitian mode: part 0 holds H1(G, H), part 1 holds H2(G, H); chi[G][H]
+// += (1 + i t) H1 + i H2 for G <= H and chi[H][G] += (1 + i t) conj(H1) + i
+// conj(H2) for G < H.  Each (1 + i t) product is one FP32 fused multiply-add (one
+// rounding; t is an FP32 number), the power of two and the widening to FP64 are
+// exact, and the FP64 sums are reductions: the epilogue issues no FP64 arithmetic.
 __device__ __forceinline__ void merge_row(double2* __restrict__ chi_w, int nG, int G, int Hb, const float (&sre)[64],
-                                          const float (&sim)[64], double sc, bool herm, int part, double t) {
+                                          const float (&sim)[64], int k, bool herm, int part, float t) {
   double2* row = chi_w + (size_t)G * nG;
   if (!herm) {
 #pragma unroll
     for (int i = 0; i < 64; ++i) {
       if (Hb + i < nG) {
-        double2 o = row[Hb + i];
-        o.x += (double)sre[i] * sc;
-        o.y += (double)sim[i] * sc;
-        row[Hb + i] = o;
+        red_add_pow2(&row[Hb + i].x, sre[i], k);
+        red_add_pow2(&row[Hb + i].y, sim[i], k);
       }
     }
     return;
@@ -522,18 +550,30 @@ __device__ __forceinline__ void merge_row(double2* __restrict__ chi_w, int nG, i
   for (int i = 0; i < 64; ++i) {
     const int H = Hb + i;
     if (H < nG && G <= H) {
-      const double a = (double)sre[i] * sc, b = (double)sim[i] * sc;
-      double2 o = row[H];
-      if (part == 0) { o.x += a - t * b; o.y += b + t * a; } else { o.x -= b; o.y += a; }
-      row[H] = o;
-      if (G < H) {
-        double2* m = chi_w + (size_t)H * nG + G;
-        double2 u = *m;
-        if (part == 0) { u.x += a + t * b; u.y += t * a - b; } else { u.x += b; u.y += a; }
-        *m = u;
+      const float a = sre[i], b = sim[i];
+      double2* m = chi_w + (size_t)H * nG + G;
+      if (part == 0) {
+        red_add_pow2(&row[H].x, fmaf(-t, b, a), k);
+        red_add_pow2(&row[H].y, fmaf(t, a, b), k);
+        if (G < H) {
+          red_add_pow2(&m->x, fmaf(t, b, a), k);
+          red_add_pow2(&m->y, fmaf(t, a, -b), k);
+        }
+      } else {
+        red_add_pow2(&row[H].x, -b, k);
+        red_add_pow2(&row[H].y, a, k);
+        if (G < H) {
+          red_add_pow2(&m->x, b, k);
+          red_add_pow2(&m->y, a, k);
+        }
       }
     }
   }
+}
+
+// exponent k of a power of two 2^k held as a double
+__device__ __forceinline__ int exponent_of_pow2(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
 }
 
 template <bool BF16, int NT>
@@ -670,7 +710,7 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
       tc::mbar_wait(&bar->done, 0, status, 1, WAIT_BUDGET_NS);
     }
   } else {
-    // ---------------- epilogue: drain chains, then FP64 merge per item ----------------
+    // ---------------- epilogue: drain chains, then FP64 reductions per item ----------------
     const int ew = warp - 2, quad = warp & 3, half = ew >> 2;
     const int row = quad * 32 + lane;
     int64_t gc = 0;
@@ -724,7 +764,8 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
       const int G = tm * BM + row;
       if (ok && G < nG)
         merge_row(P.chi[q] + (size_t)iw * nG * nG, nG, G, tn * BN + half * 64, sre, sim,
-                  P.inv[q][part * P.n_freq + iw], P.n_parts == 2, part, P.n_parts == 2 ? P.tbar[q][iw] : 0.0);
+                  exponent_of_pow2(P.inv[q][part * P.n_freq + iw]), P.n_parts == 2, part,
+                  P.n_parts == 2 ? (float)P.tbar[q][iw] : 0.f);
       }
     }
   }
@@ -953,7 +994,8 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
       const int G = tm * 2 * BM + (int)rank * BM + row;
       if (ok && G < nG)
         merge_row(P.chi[q] + (size_t)iw * nG * nG, nG, G, tn * BN + half * 64, sre, sim,
-                  P.inv[q][part * P.n_freq + iw], P.n_parts == 2, part, P.n_parts == 2 ? P.tbar[q][iw] : 0.0);
+                  exponent_of_pow2(P.inv[q][part * P.n_freq + iw]), P.n_parts == 2, part,
+                  P.n_parts == 2 ? (float)P.tbar[q][iw] : 0.f);
       }
     }
   }

@@ -268,6 +268,24 @@ void set_global_error(const std::string& msg) { g_create_err = msg; }
 size_t cbytes(const chi0_plan_s* p) { return is_split(p) ? sizeof(float2) : sizeof(double2); }
 }  // namespace chi0
 
+// Automatic Hermitian mode pays where the GPU stays full: a launch of one sphere
+// has n_freq T^2 work items in plain mode and n_freq T (T + 1) / 2 in Hermitian mode
+// (T tiles of 128 along G), one item per SM at a time; a Hermitian item also
+// carries its H2 part (taken as a quarter of an item here).  Small spheres with
+// few frequencies (fewer items than SMs) run faster in plain mode.
+static bool herm_pays(const chi0_plan_s* p, const chi0_plan_desc* d) {
+  int n_sm = 0;
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess || n_sm < 1) n_sm = 1;
+  double plain = 0.0, herm = 0.0;
+  for (int i = 0; i < d->n_q; ++i) {
+    const int64_t T = (d->n_G[i] + 127) / 128;
+    const int64_t ip = (int64_t)d->n_freq * T * T, ih = (int64_t)d->n_freq * T * (T + 1) / 2;
+    plain += (double)((ip + n_sm - 1) / n_sm);
+    herm += 1.25 * (double)((ih + n_sm - 1) / n_sm);
+  }
+  return herm < plain;
+}
+
 extern "C" {
 
 const char* chi0_last_error(chi0_plan plan) {
@@ -313,7 +331,7 @@ chi0_status chi0_plan_create(chi0_plan* out, const chi0_plan_desc* d) {
   p->om_re.assign(d->freq_re, d->freq_re + d->n_freq);
   p->om_im.assign(d->freq_im, d->freq_im + d->n_freq);
   p->chain_pairs = d->chain_pairs ? d->chain_pairs : 32;
-  p->tc_herm = chi0::is_split(p) && (d->hermitian == 1 || (d->hermitian == 0 && p->n_products != 4));
+  p->tc_herm = chi0::is_split(p) && (d->hermitian == 1 || (d->hermitian == 0 && p->n_products != 4 && herm_pays(p, d)));
 
   chi0_status st = CHI0_OK;
   auto bail = [&](chi0_status s) {

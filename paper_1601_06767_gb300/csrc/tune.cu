@@ -199,6 +199,12 @@ extern "C" chi0_status chi0_autotune(chi0_plan p, int iq, int flags, double* bes
   return CHI0_OK;
 }
 
+extern "C" chi0_status chi0_plan_hermitian(chi0_plan p, int* on) {
+  if (!p || !on) return CHI0_ERR_INVALID;
+  *on = p->tc_herm ? 1 : 0;
+  return CHI0_OK;
+}
+
 extern "C" chi0_status chi0_get_tuning(chi0_plan p, int* group, int64_t* block_pairs, int* cta_pair) {
   if (!p) return CHI0_ERR_INVALID;
   if (group) *group = p->tc_group;

@@ -138,12 +138,43 @@ def test_tc_edge_shapes(nG, nv, nc, pair, monkeypatch):
     Ev, Ec = prob.E_v[:nv], prob.E_c[:nc]
     dE = (Ev[:, None] - Ec[None, :]).reshape(-1)
     ref = chi0_from_pairs(M, freq_factor(dE, np.ones_like(dE), prob.omega, prob.delta))
-    for prec, herm in (("fp16", None), ("bf16", None), ("fp16", False), ("bf16", False)):
+    for prec, herm in (("fp16", True), ("bf16", True), ("fp16", False), ("bf16", False)):
         with _plan(prob, precision=prec, max_pairs=64, hermitian=herm) as plan:
             chi = plan.accumulate(0, _dev(M.astype(np.complex64)), nv, nc, _dev(Ev), _dev(Ec))
             plan.sync_status()
             chi = chi.cpu().numpy()
         check_chi(chi, ref, TOL, label=f"edge {prec} herm={herm} nG={nG} {nv}x{nc}")
+
+
+def test_hermitian_automatic_choice():
+    """hermitian = automatic: the mode with fewer estimated waves of work items
+    over the SMs (T = ceil(N_G / 128): n_freq T^2 items in plain mode, n_freq
+    T (T + 1) / 2 in Hermitian mode at 1.25 items each); plain for four
+    products; FP64 never.  One frequency at N_G 1200 (55 items against 100) runs
+    plain on a GPU with 100 or more SMs, nine frequencies at N_G 2500 Hermitian."""
+    import math
+    import torch
+    from paper_1601_06767_gb300 import Chi0Plan
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+
+    def rule(nG, nf):
+        T = -(-nG // 128)
+        return 1.25 * math.ceil(nf * T * (T + 1) // 2 / n_sm) < math.ceil(nf * T * T / n_sm)
+
+    small, big = make_problem("c4"), make_problem("c2", n_imag=8)
+    assert small.omega.size == 1 and big.omega.size == 9
+    assert small.gvec[0].shape[0] == 1200 and big.gvec[0].shape[0] == 2500
+    if n_sm >= 100:
+        assert not rule(1200, 1) and rule(2500, 9)
+    cases = [(small, "fp16", 0, rule(1200, 1)), (big, "fp16", 0, rule(2500, 9)), (big, "bf16", 0, rule(2500, 9)),
+             (big, "bf16", 4, False), (big, "fp64", 0, False)]
+    for prob, prec, npr, want in cases:
+        with Chi0Plan(prob.n, prob.gvec, prob.omega, prob.delta, precision=prec, gw=prob.gw, n_products=npr,
+                      max_pairs=256) as plan:
+            assert plan.hermitian == want, (prob.gvec[0].shape[0], prob.omega.size, prec, npr)
+    with Chi0Plan(small.n, small.gvec, small.omega, small.delta, precision="fp16", gw=small.gw, max_pairs=256,
+                  hermitian=True) as plan:
+        assert plan.hermitian
 
 
 @pytest.mark.parametrize("pair", ["0", "1"])
