@@ -444,7 +444,16 @@ template <int NT>
 __device__ __forceinline__ int part_stages(const TcBatch& P, int q, int iw, int part) {
   return part_products(P, q, iw, part) == 1 ? (P.nK + NT - 1) / NT : P.nK;
 }
+// A one-product W2 part (rho <= 2^-11 FP16, 2^-15 BF16) of up to 512 stages (16384
+// pairs) is one chain over the whole K range and is added together with the W1 part
+// (h2_fused): the round-toward-zero bias of n accumulator additions is about
+// n 2^-25.5 of the part, the part is within a few rho of chi0, and a 16384-pair
+// FP16 part makes 2048 additions per accumulator: below 1e-7 of chi0.
+__device__ __forceinline__ bool h2_fused(const TcBatch& P, int q, int iw) {
+  return P.n_parts == 2 && P.h2np[q][iw] == 1 + 16 && P.nK <= 512;
+}
 __device__ __forceinline__ int part_chain(const TcBatch& P, int q, int iw, int part, int n_stages) {
+  if (part && h2_fused(P, q, iw)) return n_stages;
   return (part && P.h2np[q][iw] >= 16) ? min(n_stages, 8 * P.chain_k) : P.chain_k;
 }
 
@@ -574,6 +583,145 @@ __device__ __forceinline__ void merge_row(double2* __restrict__ chi_w, int nG, i
 // exponent k of a power of two 2^k held as a double
 __device__ __forceinline__ int exponent_of_pow2(double x) {
   return (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
+}
+
+// Hermitian mode with a one-product W2 part: add both parts of a tile row at once,
+// chi[G][H] += (1 + i t) H1 + i H2 for G <= H and chi[H][G] += (1 + i t) conj(H1) +
+// i conj(H2) for G < H, both read from tensor memory 16 columns at a time: the W1
+// sums (scale 2^-k1) at column address ta1 (Re) and ta1 + 128 (Im), the W2
+// accumulator at ta2, scaled to the W1 units by 2^(k2 - k1) (exact; a ratio
+// outside the FP32 exponent range drops H2: below 2^-126 it is negligible, above
+// 2^127 the W2 weights were zero).  Every lane of the warp runs the loads; `in`
+// masks the row.
+__device__ __forceinline__ void merge_row_fused(double2* __restrict__ chi_w, int nG, int G, int Hb, uint32_t ta1,
+                                                uint32_t ta2, int k1, int k2, float t, bool in) {
+  double2* row = chi_w + (size_t)G * nG;
+  const int d = k2 - k1;
+  const float r21 = d >= -126 && d <= 127 ? __int_as_float((d + 127) << 23) : 0.f;
+#pragma unroll 1
+  for (int j = 0; j < 64; j += 16) {
+    float re1[16], im1[16], re2[16], im2[16];
+    tc::tmem_ld16(ta1 + j, re1);
+    tc::tmem_ld16(ta1 + 128 + j, im1);
+    tc::tmem_ld16(ta2 + j, re2);
+    tc::tmem_ld16(ta2 + 128 + j, im2);
+    tc::tmem_ld_wait();
+    tc::reg_after_wait(re1);
+    tc::reg_after_wait(im1);
+    tc::reg_after_wait(re2);
+    tc::reg_after_wait(im2);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int H = Hb + j + i;
+      if (in && H < nG && G <= H) {
+        const float a1 = re1[i], b1 = im1[i], a2 = re2[i] * r21, b2 = im2[i] * r21;
+        red_add_pow2(&row[H].x, fmaf(-t, b1, a1) - b2, k1);
+        red_add_pow2(&row[H].y, fmaf(t, a1, b1) + a2, k1);
+        if (G < H) {
+          double2* m = chi_w + (size_t)H * nG + G;
+          red_add_pow2(&m->x, fmaf(t, b1, a1) + b2, k1);
+          red_add_pow2(&m->y, fmaf(t, a1, -b1) + a2, k1);
+        }
+      }
+    }
+  }
+}
+
+// Drain the nch accumulation chains of one part into the FP32 sums (zeroed first).
+// One 32-column load in flight (the sums fill the registers); each buffer is
+// released as soon as its last values are in registers, before they are added.
+// keep_last: the last chain's buffer receives the part's total (its accumulator
+// plus the sums of the earlier chains) and stays held.  Returns false when a
+// bounded wait ran out.
+template <bool PAIR, class BarT>
+__device__ __forceinline__ bool drain_part(BarT* bar, uint32_t tbase, int quad, int half, int lane, int nch,
+                                           bool keep_last, int64_t& gc, int* status, float (&sre)[64],
+                                           float (&sim)[64]) {
+#pragma unroll
+  for (int i = 0; i < 64; ++i) { sre[i] = 0.f; sim[i] = 0.f; }
+  for (int c = 0; c < nch; ++c, ++gc) {
+    const int buf = (int)(gc & 1);
+    if (!tc::mbar_wait(&bar->tfull[buf], (uint32_t)((gc >> 1) & 1), status, 1, WAIT_BUDGET_NS)) return false;
+    tc::fence_after();
+    const uint32_t ta = tbase + ((uint32_t)(quad * 32) << 16) + buf * 256 + half * 64;
+    const bool keep = keep_last && c == nch - 1;
+    float v[32];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      // column groups: Re 0..31, Re 32..63, Im 0..31, Im 32..63
+      const uint32_t col = (g >> 1) * 128 + (g & 1) * 32;
+      tc::tmem_ld32(ta + col, v);
+      tc::tmem_ld_wait();
+      tc::reg_after_wait(v);
+      float* acc = (g >> 1) ? sim + (g & 1) * 32 : sre + (g & 1) * 32;
+      if (keep) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] += acc[i];
+        tc::tmem_st32(ta + col, v);
+      } else {
+        if (g == 3) {
+          tc::fence_before();
+          __syncwarp();
+          if (lane == 0) {
+            if constexpr (PAIR) tc::mbar_arrive_cluster(tc::mapa(&bar->tempty[buf], 0));
+            else tc::mbar_arrive(&bar->tempty[buf]);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[i] += v[i];
+      }
+    }
+    if (keep) tc::tmem_st_wait();
+  }
+  return true;
+}
+
+// The epilogue of one item (q, frequency, tile): per part, its chains into FP32 sums
+// and their reductions into chi0.  In Hermitian mode with a one-product W2 part,
+// the W1 total stays in its last chain's buffer, the W2 part is a single chain in
+// the other buffer, and both are added in one pass (half the reductions).
+// Returns false when a bounded wait ran out.
+template <int NT, bool PAIR, class BarT>
+__device__ __forceinline__ bool epilogue_item(const TcBatch& P, BarT* bar, uint32_t tbase, int quad, int half,
+                                              int lane, int q, int iw, int G, int tn, int64_t& gc, int* status) {
+  // (everything else is read from the launch parameters after the drain, where the
+  // sums no longer fill the registers)
+  const bool fused = h2_fused(P, q, iw);
+  for (int part = 0; part < P.n_parts; ++part) {
+    const int nks = part_stages<NT>(P, q, iw, part);
+    const int ck = part_chain(P, q, iw, part, nks);
+    float sre[64], sim[64];
+    if (!drain_part<PAIR>(bar, tbase, quad, half, lane, (nks + ck - 1) / ck, fused, gc, status, sre, sim))
+      return false;
+    const int nG = P.nG[q];
+    double2* chi_w = P.chi[q] + (size_t)iw * nG * nG;
+    const bool herm = P.n_parts == 2;
+    const float t = herm ? (float)P.tbar[q][iw] : 0.f;
+    const int k = exponent_of_pow2(P.inv[q][part * P.n_freq + iw]);
+    if (fused) {
+      const int b1 = (int)((gc - 1) & 1), b2 = (int)(gc & 1);
+      if (!tc::mbar_wait(&bar->tfull[b2], (uint32_t)((gc >> 1) & 1), status, 1, WAIT_BUDGET_NS)) return false;
+      tc::fence_after();
+      const uint32_t tq = tbase + ((uint32_t)(quad * 32) << 16) + half * 64;
+      merge_row_fused(chi_w, nG, G, tn * BN + half * 64, tq + b1 * 256, tq + b2 * 256, k,
+                      exponent_of_pow2(P.inv[q][P.n_freq + iw]), t, G < nG);
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        if constexpr (PAIR) {
+          tc::mbar_arrive_cluster(tc::mapa(&bar->tempty[b1], 0));
+          tc::mbar_arrive_cluster(tc::mapa(&bar->tempty[b2], 0));
+        } else {
+          tc::mbar_arrive(&bar->tempty[b1]);
+          tc::mbar_arrive(&bar->tempty[b2]);
+        }
+      }
+      ++gc;
+      return true;
+    }
+    if (G < nG) merge_row(chi_w, nG, G, tn * BN + half * 64, sre, sim, k, herm, part, t);
+  }
+  return true;
 }
 
 template <bool BF16, int NT>
@@ -718,55 +866,7 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
     for (int64_t item = blockIdx.x; item < P.total_items && ok; item += gridDim.x) {
       int q, iw, tm, tn;
       decode_item(P, item, q, iw, tm, tn);
-      for (int part = 0; part < P.n_parts && ok; ++part) {
-      const int nks = part_stages<NT>(P, q, iw, part);
-      const int ck = part_chain(P, q, iw, part, nks);
-      const int nch = (nks + ck - 1) / ck;
-      float sre[64], sim[64];
-#pragma unroll
-      for (int i = 0; i < 64; ++i) { sre[i] = 0.f; sim[i] = 0.f; }
-      for (int c = 0; c < nch; ++c, ++gc) {
-        const int buf = (int)(gc & 1);
-        if (!tc::mbar_wait(&bar->tfull[buf], (uint32_t)((gc >> 1) & 1), status, 1, WAIT_BUDGET_NS)) {
-          ok = false;
-          break;
-        }
-        tc::fence_after();
-        const uint32_t ta = tbase + ((uint32_t)(quad * 32) << 16) + buf * 256 + half * 64;
-        // one load in flight (the epilogue's sums fill the registers); the buffer is
-        // released as soon as its last values are in registers, before they are added
-        float v[32];
-        tc::tmem_ld32(ta, v);
-        tc::tmem_ld_wait();
-        tc::reg_after_wait(v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) sre[i] += v[i];
-        tc::tmem_ld32(ta + 32, v);
-        tc::tmem_ld_wait();
-        tc::reg_after_wait(v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) sre[32 + i] += v[i];
-        tc::tmem_ld32(ta + 128, v);
-        tc::tmem_ld_wait();
-        tc::reg_after_wait(v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) sim[i] += v[i];
-        tc::tmem_ld32(ta + 160, v);
-        tc::tmem_ld_wait();
-        tc::reg_after_wait(v);
-        tc::fence_before();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&bar->tempty[buf]);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) sim[32 + i] += v[i];
-      }
-      const int nG = P.nG[q];
-      const int G = tm * BM + row;
-      if (ok && G < nG)
-        merge_row(P.chi[q] + (size_t)iw * nG * nG, nG, G, tn * BN + half * 64, sre, sim,
-                  exponent_of_pow2(P.inv[q][part * P.n_freq + iw]), P.n_parts == 2, part,
-                  P.n_parts == 2 ? (float)P.tbar[q][iw] : 0.f);
-      }
+      ok = epilogue_item<NT, false>(P, bar, tbase, quad, half, lane, q, iw, tm * BM + row, tn, gc, status);
     }
   }
   tc::fence_before();
@@ -948,55 +1048,7 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
     for (int64_t item = pair; item < P.total_items && ok; item += npairs) {
       int q, iw, tm, tn;
       decode_item(P, item, q, iw, tm, tn);
-      for (int part = 0; part < P.n_parts && ok; ++part) {
-      const int nks = part_stages<NT>(P, q, iw, part);
-      const int ck = part_chain(P, q, iw, part, nks);
-      const int nch = (nks + ck - 1) / ck;
-      float sre[64], sim[64];
-#pragma unroll
-      for (int i = 0; i < 64; ++i) { sre[i] = 0.f; sim[i] = 0.f; }
-      for (int c = 0; c < nch; ++c, ++gc) {
-        const int buf = (int)(gc & 1);
-        if (!tc::mbar_wait(&bar->tfull[buf], (uint32_t)((gc >> 1) & 1), status, 1, WAIT_BUDGET_NS)) {
-          ok = false;
-          break;
-        }
-        tc::fence_after();
-        const uint32_t ta = tbase + ((uint32_t)(quad * 32) << 16) + buf * 256 + half * 64;
-                // one load in flight (the epilogue's sums fill the registers); the buffer is
-        // released as soon as its last values are in registers, before they are added
-        float v[32];
-        tc::tmem_ld32(ta, v);
-        tc::tmem_ld_wait();
-        tc::reg_after_wait(v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) sre[i] += v[i];
-        tc::tmem_ld32(ta + 32, v);
-        tc::tmem_ld_wait();
-        tc::reg_after_wait(v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) sre[32 + i] += v[i];
-        tc::tmem_ld32(ta + 128, v);
-        tc::tmem_ld_wait();
-        tc::reg_after_wait(v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) sim[i] += v[i];
-        tc::tmem_ld32(ta + 160, v);
-        tc::tmem_ld_wait();
-        tc::reg_after_wait(v);
-        tc::fence_before();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive_cluster(tc::mapa(&bar->tempty[buf], 0));
-#pragma unroll
-        for (int i = 0; i < 32; ++i) sim[32 + i] += v[i];
-      }
-      const int nG = P.nG[q];
-      const int G = tm * 2 * BM + (int)rank * BM + row;
-      if (ok && G < nG)
-        merge_row(P.chi[q] + (size_t)iw * nG * nG, nG, G, tn * BN + half * 64, sre, sim,
-                  exponent_of_pow2(P.inv[q][part * P.n_freq + iw]), P.n_parts == 2, part,
-                  P.n_parts == 2 ? (float)P.tbar[q][iw] : 0.f);
-      }
+      ok = epilogue_item<NT, true>(P, bar, tbase, quad, half, lane, q, iw, tm * 2 * BM + (int)rank * BM + row, tn, gc, status);
     }
   }
   tc::fence_before();

@@ -315,14 +315,18 @@ def test_pipelined_build_equals_serial_build():
     check_chi(chi_p, ref, TOL, label="pipelined build (15 blocks)")
 
 
+@pytest.mark.parametrize("pair", ["0", "1"])
 @pytest.mark.parametrize("precision", ["fp16", "bf16"])
-def test_hermitian_shifted_h2_one_product(precision):
+def test_hermitian_shifted_h2_one_product(precision, pair, monkeypatch):
     """Hermitian mode with the H2 weights shifted by the block's ratio t
     (chi0 = (1 + i t) H1 + i H2, H2 with g = Im f - t Re f): a block of
     neighbouring conduction energies has a narrow range of Im f / Re f, so its H2
     part takes one product (FP16) or three; blocks of low-lying bands keep three.
-    Several blocks of each kind, ragged sphere, against the oracle and the plain
+    A one-product H2 part is a single chain added together with H1 (the fused
+    epilogue), the others are added part by part.  Several blocks of each kind,
+    ragged sphere, both kernel variants, against the oracle and the plain
     contraction."""
+    monkeypatch.setenv("CHI0_TC_PAIR", pair)
     prob = make_problem("c1", n_G=[203], n_imag=3)
     rng = np.random.default_rng(41)
     nv, nG = 4, 203
