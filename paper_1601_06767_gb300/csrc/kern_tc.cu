@@ -630,9 +630,8 @@ __device__ __forceinline__ void merge_row_fused(double2* __restrict__ chi_w, int
 // Drain the nch accumulation chains of one part into the FP32 sums (zeroed first).
 // One 32-column load in flight (the sums fill the registers); each buffer is
 // released as soon as its last values are in registers, before they are added.
-// keep_last: the last chain's buffer receives the part's total (its accumulator
-// plus the sums of the earlier chains) and stays held.  Returns false when a
-// bounded wait ran out.
+// keep_last: the last chain's buffer is not released and receives the part's
+// total sums (held for a later merge).  Returns false when a bounded wait ran out.
 template <bool PAIR, class BarT>
 __device__ __forceinline__ bool drain_part(BarT* bar, uint32_t tbase, int quad, int half, int lane, int nch,
                                            bool keep_last, int64_t& gc, int* status, float (&sre)[64],
@@ -644,34 +643,43 @@ __device__ __forceinline__ bool drain_part(BarT* bar, uint32_t tbase, int quad, 
     if (!tc::mbar_wait(&bar->tfull[buf], (uint32_t)((gc >> 1) & 1), status, 1, WAIT_BUDGET_NS)) return false;
     tc::fence_after();
     const uint32_t ta = tbase + ((uint32_t)(quad * 32) << 16) + buf * 256 + half * 64;
-    const bool keep = keep_last && c == nch - 1;
     float v[32];
+    tc::tmem_ld32(ta, v);
+    tc::tmem_ld_wait();
+    tc::reg_after_wait(v);
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      // column groups: Re 0..31, Re 32..63, Im 0..31, Im 32..63
-      const uint32_t col = (g >> 1) * 128 + (g & 1) * 32;
-      tc::tmem_ld32(ta + col, v);
-      tc::tmem_ld_wait();
-      tc::reg_after_wait(v);
-      float* acc = (g >> 1) ? sim + (g & 1) * 32 : sre + (g & 1) * 32;
-      if (keep) {
+    for (int i = 0; i < 32; ++i) sre[i] += v[i];
+    tc::tmem_ld32(ta + 32, v);
+    tc::tmem_ld_wait();
+    tc::reg_after_wait(v);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] += acc[i];
-        tc::tmem_st32(ta + col, v);
-      } else {
-        if (g == 3) {
-          tc::fence_before();
-          __syncwarp();
-          if (lane == 0) {
-            if constexpr (PAIR) tc::mbar_arrive_cluster(tc::mapa(&bar->tempty[buf], 0));
-            else tc::mbar_arrive(&bar->tempty[buf]);
-          }
-        }
+    for (int i = 0; i < 32; ++i) sre[32 + i] += v[i];
+    tc::tmem_ld32(ta + 128, v);
+    tc::tmem_ld_wait();
+    tc::reg_after_wait(v);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) acc[i] += v[i];
+    for (int i = 0; i < 32; ++i) sim[i] += v[i];
+    tc::tmem_ld32(ta + 160, v);
+    tc::tmem_ld_wait();
+    tc::reg_after_wait(v);
+    if (!(keep_last && c == nch - 1)) {
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        if constexpr (PAIR) tc::mbar_arrive_cluster(tc::mapa(&bar->tempty[buf], 0));
+        else tc::mbar_arrive(&bar->tempty[buf]);
       }
     }
-    if (keep) tc::tmem_st_wait();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) sim[32 + i] += v[i];
+  }
+  if (keep_last) {
+    const uint32_t ta = tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)((gc - 1) & 1) * 256 + half * 64;
+    tc::tmem_st32_part<0>(ta, sre);
+    tc::tmem_st32_part<1>(ta + 32, sre);
+    tc::tmem_st32_part<0>(ta + 128, sim);
+    tc::tmem_st32_part<1>(ta + 160, sim);
+    tc::tmem_st_wait();
   }
   return true;
 }

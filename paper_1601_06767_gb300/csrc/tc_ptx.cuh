@@ -209,6 +209,22 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) 
          "f"(v[24]), "f"(v[25]), "f"(v[26]), "f"(v[27]), "f"(v[28]), "f"(v[29]), "f"(v[30]), "f"(v[31])
       : "memory");
 }
+// the same from 32 consecutive values of a longer register array (v + 32 j, j constant)
+template <int J, int N>
+__device__ __forceinline__ void tmem_st32_part(uint32_t taddr, const float (&v)[N]) {
+  static_assert(32 * (J + 1) <= N, "part out of range");
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+      :: "r"(taddr), "f"(v[32 * J + 0]), "f"(v[32 * J + 1]), "f"(v[32 * J + 2]), "f"(v[32 * J + 3]),
+         "f"(v[32 * J + 4]), "f"(v[32 * J + 5]), "f"(v[32 * J + 6]), "f"(v[32 * J + 7]), "f"(v[32 * J + 8]),
+         "f"(v[32 * J + 9]), "f"(v[32 * J + 10]), "f"(v[32 * J + 11]), "f"(v[32 * J + 12]), "f"(v[32 * J + 13]),
+         "f"(v[32 * J + 14]), "f"(v[32 * J + 15]), "f"(v[32 * J + 16]), "f"(v[32 * J + 17]), "f"(v[32 * J + 18]),
+         "f"(v[32 * J + 19]), "f"(v[32 * J + 20]), "f"(v[32 * J + 21]), "f"(v[32 * J + 22]), "f"(v[32 * J + 23]),
+         "f"(v[32 * J + 24]), "f"(v[32 * J + 25]), "f"(v[32 * J + 26]), "f"(v[32 * J + 27]), "f"(v[32 * J + 28]),
+         "f"(v[32 * J + 29]), "f"(v[32 * J + 30]), "f"(v[32 * J + 31])
+      : "memory");
+}
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
