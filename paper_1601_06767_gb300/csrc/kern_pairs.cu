@@ -717,13 +717,40 @@ __device__ __forceinline__ void wl_line(float2 (&x)[3], const WLConsts<Q, NS>& c
   }
 }
 
+// The same length-3Q line with the other index split, i = b + Q a: lane b holds
+// x(b + Q a) in x[a] (a warp's load of x[a] is 8 Q contiguous bytes, against
+// 24 Q spread over the whole row for i = a + 3 b).  Per lane, the 3-point
+// transforms Z_k0 = sum_a x(b + Q a) e^{2 pi i a k0/3} times e^{2 pi i b k0/n},
+// then the Q-point transforms over b across the lanes; lane b ends with
+// y[k0] = y(k0 + 3 bitrev(b)).  tb1, tb2 = e^{2 pi i b/n}, e^{4 pi i b/n}.
+template <int Q, int NS>
+__device__ __forceinline__ void wl_line_t(float2 (&x)[3], const WLConsts<Q, NS>& c, float2 tb1, float2 tb2) {
+  constexpr float h = k_roots24.im[4];           // sin(pi/3)
+  const float2 s = make_float2(x[1].x + x[2].x, x[1].y + x[2].y);
+  const float2 d = make_float2(x[1].x - x[2].x, x[1].y - x[2].y);
+  const float2 m = make_float2(fmaf(-0.5f, s.x, x[0].x), fmaf(-0.5f, s.y, x[0].y));
+  x[0] = make_float2(x[0].x + s.x, x[0].y + s.y);
+  x[1] = cmul(make_float2(fmaf(-h, d.y, m.x), fmaf(h, d.x, m.y)), tb1);
+  x[2] = cmul(make_float2(fmaf(h, d.y, m.x), fmaf(-h, d.x, m.y)), tb2);
+#pragma unroll
+  for (int st = 0; st < WLConsts<Q, NS>::LOGQ; ++st) {
+    const int hh = (Q / 2) >> st;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float2 p = shfl_xor2(x[a], hh);
+      const float2 u = make_float2(fmaf(c.sg[st], x[a].x, p.x), fmaf(c.sg[st], x[a].y, p.y));
+      x[a] = (hh == 1) ? u : cmul(u, c.tw[st]);
+    }
+  }
+}
+
 // One CTA per (valence band, plane i1) and a run of conduction bands:
 //   stage 1: warp w transforms rows i2 = w, w+8, ... of conj(u_v) u_c along i3 into X[i2][k3];
 //   stage 2: warp w transforms the kept columns k3 = w, w+8, ... of X along i2 into Y[k2][k3];
 //   Y is copied to D[pair][i1] (contiguous nk2 x nk3 values).
-// No frequency shift is applied to the inputs: a line keeps the outputs y(k)
-// for k in [kmin, kmin + nk) mod n, which lie in at most two of the three output
-// sets y(bitrev(b) + Q t) (all three are formed).  Both rows of a pair are read
+// Lines are split as i = b + Q a (wl_line_t).  No frequency shift is applied to
+// the inputs: a line keeps the outputs y(k) for k in [kmin, kmin + nk) mod n,
+// lane b forming y(t + 3 bitrev(b)) for t < 3 and storing those in range.  Both rows of a pair are read
 // from global memory (the valence row once per conduction band, from L2), so
 // the CTA holds only X and Y (24 KB) and several CTAs fit on an SM.
 constexpr int WN_WARPS = 8;
@@ -749,11 +776,12 @@ k_pair_planes_wn(const float2* __restrict__ psi_v, const int32_t* __restrict__ v
   const int box = nk2 * nk3;
   if (jv >= nv || jc_begin >= jc_end) return;
   const WLConsts<Q, 3> cst = wl_consts<Q, 3>(lane);
-  // slot of output set t in the kept range along i3 / i2, or -1
+  const float2 tb1 = root<n>(lane), tb2 = root<n>(2 * lane);
+  // slot of output y(t + 3 bitrev(lane)) in the kept range along i3 / i2, or -1
   int o3[3], o2[3];
 #pragma unroll
   for (int t = 0; t < 3; ++t) {
-    const int k = cst.kk + Q * t;
+    const int k = t + 3 * cst.kk;
     const int d3 = ((k - k3min) % n + n) % n, d2 = ((k - k2min) % n + n) % n;
     o3[t] = d3 < nk3 ? d3 : -1;
     o2[t] = d2 < nk2 ? d2 : -1;
@@ -765,26 +793,26 @@ k_pair_planes_wn(const float2* __restrict__ psi_v, const int32_t* __restrict__ v
     const float2* csrc = psi_c + band * nr + (int64_t)i1 * plane;
     // stage 1: rows
     for (int i2 = warp; i2 < n; i2 += WN_WARPS) {
-      const float2* uc = csrc + i2 * n + 3 * lane;
-      const float2* uv = vsrc + i2 * n + 3 * lane;
-      float2 x[3], y[3];
+      const float2* uc = csrc + i2 * n + lane;
+      const float2* uv = vsrc + i2 * n + lane;
+      float2 x[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) x[a] = cconjmul(__ldg(uv + a), __ldg(uc + a));
-      wl_line<Q, 3>(x, cst, lane, y);
+      for (int a = 0; a < 3; ++a) x[a] = cconjmul(__ldg(uv + Q * a), __ldg(uc + Q * a));
+      wl_line_t<Q, 3>(x, cst, tb1, tb2);
 #pragma unroll
       for (int t = 0; t < 3; ++t)
-        if (o3[t] >= 0) X[i2 * ldx + o3[t]] = y[t];
+        if (o3[t] >= 0) X[i2 * ldx + o3[t]] = x[t];
     }
     __syncthreads();
     // stage 2: kept columns
     for (int k3 = warp; k3 < nk3; k3 += WN_WARPS) {
-      float2 x[3], y[3];
+      float2 x[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) x[a] = X[(3 * lane + a) * ldx + k3];
-      wl_line<Q, 3>(x, cst, lane, y);
+      for (int a = 0; a < 3; ++a) x[a] = X[(lane + Q * a) * ldx + k3];
+      wl_line_t<Q, 3>(x, cst, tb1, tb2);
 #pragma unroll
       for (int t = 0; t < 3; ++t)
-        if (o2[t] >= 0) Y[o2[t] * nk3 + k3] = y[t];
+        if (o2[t] >= 0) Y[o2[t] * nk3 + k3] = x[t];
     }
     __syncthreads();
     float2* dst = D + ((int64_t)(jv * nc + jc) * n + i1) * box;
