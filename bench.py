@@ -202,11 +202,11 @@ def h2_products(Ev, Ec, omega, delta, n_prod, precision, block_cols=None):
     decides them per block of conduction columns (block_cols columns with all
     valence bands; the mean over the blocks): with t the midrange of
     Im f / Re f over the block (when that shrinks the weights) and rho the
-    bound on max|Im f - t Re f| / max|Re f|, one product where rho <= 2^-11
-    (FP16; 2^-15 BF16), three where rho <= 2^-6, else n_prod."""
+    bound on max|Im f - t Re f| / max|Re f|, one product (FP16 operands in both
+    precisions) where rho <= 2^-11, three where rho <= 2^-6, else n_prod."""
     Ev, Ec = np.asarray(Ev), np.asarray(Ec)
     block_cols = block_cols or Ec.size
-    one = 2.0 ** (-15 if precision == "bf16" else -11)
+    one = 2.0 ** -11
     out = np.zeros(np.atleast_1d(omega).size)
     blocks = [Ec[c0:c0 + block_cols] for c0 in range(0, Ec.size, block_cols)]
     for blk in blocks:

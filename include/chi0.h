@@ -85,9 +85,9 @@ typedef struct {
                                 the diagonal, the lower triangle written as the conjugate transpose.
                                 Per frequency and pair block, t is the midrange of Im f / Re f over the
                                 block (0 when that does not shrink the H2 weights) and rho bounds
-                                max|g| / max|Re f|: H2 takes one product where rho <= 2^-11 (FP16;
-                                2^-15 BF16), three where rho <= 2^-6, else n_products (its error scales
-                                with rho).  0 = automatic: on except for n_products 4 and except where
+                                max|g| / max|Re f|: H2 takes one product where rho <= 2^-11 (FP16
+                                operands in both precisions), three where rho <= 2^-6, else n_products
+                                (its error scales with rho).  0 = automatic: on except for n_products 4 and except where
                                 a launch would leave SMs idle (with T = ceil(n_G / 128) tiles, plain
                                 mode has n_freq T^2 work items, Hermitian mode n_freq T (T + 1) / 2, each
                                 a quarter dearer; the mode with fewer estimated waves over the SMs

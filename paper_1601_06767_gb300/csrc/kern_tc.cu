@@ -28,9 +28,10 @@
 // Im f_p / Re f_p over the block (0 where that does not shrink the weights),
 // so max|g| <= rho max|Re f| with rho = half the range of the ratio: about
 // delta / |E_v - E_c| spread over the block's energies, 1e-4 for a block of
-// neighbouring conduction bands.  H2 takes one product (t0 t0) when rho <=
-// 2^-11 for FP16 (2^-15 for BF16), three products (two terms) when rho <=
-// 2^-6, else the full count; the first two with long chains.
+// neighbouring conduction bands.  H2 takes one product (t0 t0, FP16 operands in
+// both precisions: BF16 plans keep an FP16 term 0 of M for it) when rho <=
+// 2^-11, three products (two terms) when rho <= 2^-6, else the full count; the
+// first two with long chains.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -195,8 +196,9 @@ __global__ void k_scales(const unsigned int* __restrict__ amax, const unsigned i
       inv[n_freq + iw] = 1.0 / ((double)sM * (double)s2);
       tbar[iw] = (double)t;
       // a small W2 part needs fewer products (errors scale with rho) and takes long chains (flag 16)
-      const float one_term = bf16 ? ldexpf(1.f, -15) : ldexpf(1.f, -11);
-      h2np[iw] = rho <= one_term ? 1 + 16 : (rho <= ldexpf(1.f, -6) ? 3 + 16 : n_products);
+      // one product (FP16 operands in both precisions) where rho <= 2^-11
+      (void)bf16;
+      h2np[iw] = rho <= ldexpf(1.f, -11) ? 1 + 16 : (rho <= ldexpf(1.f, -6) ? 3 + 16 : n_products);
     } else {
       // |Re W|, |Im W| <= 2 max|f| max|M|
       const float sW = pow2_scale(2.f * fmaxf(fr, fi) * mM);
@@ -253,6 +255,14 @@ k_pack(const float2* __restrict__ M, int nG, int64_t K, int nGp, int Kp, const d
     splitn<BF16, NT>(m0.y * sM, m1.y * sM, w);
 #pragma unroll
     for (int t = 0; t < NT; ++t) Bp[(NT + t) * plane + row] = w[t];
+    if (BF16 && herm) {
+      // FP16 term 0 of M for one-product W2 parts: planes 2 NT (Re) and 2 NT + 1 (Im)
+      uint32_t w1[1];
+      splitn<false, 1>(m0.x * sM, m1.x * sM, w1);
+      Bp[(2 * NT) * plane + row] = w1[0];
+      splitn<false, 1>(m0.y * sM, m1.y * sM, w1);
+      Bp[(2 * NT + 1) * plane + row] = w1[0];
+    }
     for (int iw = 0; iw < n_freq; ++iw) {
       const float2 f0 = fs[iw * 64 + 2 * lane], f1 = fs[iw * 64 + 2 * lane + 1];
       uint32_t* a = Ap + (size_t)iw * 2 * NT * plane + row;
@@ -267,14 +277,23 @@ k_pack(const float2* __restrict__ M, int nG, int64_t K, int nGp, int Kp, const d
         uint32_t* a2 = a + (size_t)n_freq * 2 * NT * plane;
         const int np2 = h2np[iw] & 15;
         const int nt2 = np2 == 1 ? 1 : ((NT == 3 && np2 != 6) ? 2 : NT);   // terms the W2 part reads
-        splitn<BF16, NT>(f0.y * m0.x, f1.y * m1.x, w);
+        if (np2 == 1) {
+          // one product: an FP16 term (also in BF16 plans, 11 bits; the scaling keeps it in range)
+          uint32_t w1[1];
+          splitn<false, 1>(f0.y * m0.x, f1.y * m1.x, w1);
+          a2[0] = w1[0];
+          splitn<false, 1>(f0.y * m0.y, f1.y * m1.y, w1);
+          a2[(size_t)NT * plane] = w1[0];
+        } else {
+          splitn<BF16, NT>(f0.y * m0.x, f1.y * m1.x, w);
 #pragma unroll
-        for (int t = 0; t < NT; ++t)
-          if (t < nt2) a2[t * plane] = w[t];
-        splitn<BF16, NT>(f0.y * m0.y, f1.y * m1.y, w);
+          for (int t = 0; t < NT; ++t)
+            if (t < nt2) a2[t * plane] = w[t];
+          splitn<BF16, NT>(f0.y * m0.y, f1.y * m1.y, w);
 #pragma unroll
-        for (int t = 0; t < NT; ++t)
-          if (t < nt2) a2[(NT + t) * plane] = w[t];
+          for (int t = 0; t < NT; ++t)
+            if (t < nt2) a2[(NT + t) * plane] = w[t];
+        }
       } else {
         const float wr0 = f0.x * m0.x - f0.y * m0.y, wi0 = f0.x * m0.y + f0.y * m0.x;
         const float wr1 = f1.x * m1.x - f1.y * m1.y, wi1 = f1.x * m1.y + f1.y * m1.x;
@@ -803,9 +822,11 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
               if (t >= ns) continue;
               // one product: slot j takes term 0 of its re/im half at k-slice kc NT + t
               const int pa = one ? (j / NT) * NT : j;
+              // B of a one-product part: the FP16 term-0 planes of BF16 plans (2 NT, 2 NT + 1)
+              const int pb = (BF16 && one) ? 2 * NT + j / NT : pa;
               const int kx = one ? (kc * NT + t) * BK : kc * BK;
               tc::tma_load_3d(st + j * TILE_BYTES, &P.tmA[q], &bar->full[s], kx, row_a, plane0 + pa);
-              tc::tma_load_3d(st + (PL + j) * TILE_BYTES, &P.tmB[q], &bar->full[s], kx, row_b, pa);
+              tc::tma_load_3d(st + (PL + j) * TILE_BYTES, &P.tmB[q], &bar->full[s], kx, row_b, pb);
             }
           }
         }
@@ -851,7 +872,7 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
             tc::fence_after();
             const unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
             const uint32_t d_re = tbase + buf * 256, d_im = d_re + 128;
-            if (np == 1) issue_stage_1p<BF16, NT, false>(st, d_re, d_im, first, min(NT, nK - kc * NT));
+            if (np == 1) issue_stage_1p<false, NT, false>(st, d_re, d_im, first, min(NT, nK - kc * NT));
             else issue_stage<BF16, NT>(st, d_re, d_im, first, np);
             tc::mma_commit(&bar->empty[s]);
             if (++pos == ck || kc == nks - 1) {
@@ -984,9 +1005,10 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
               const int t = j % NT;
               if (t >= ns) continue;
               const int pa = one ? (j / NT) * NT : j;
+              const int pb = (BF16 && one) ? 2 * NT + j / NT : pa;
               const int kx = one ? (kc * NT + t) * BK : kc * BK;
               tc::tma_load_3d_pair(st + j * RG::A_BYTES, &P.tmA[q], fb, kx, arow, plane0 + pa);
-              tc::tma_load_3d_pair(st + PL * RG::A_BYTES + j * RG::B_BYTES, &P.tmB[q], fb, kx, brow, pa);
+              tc::tma_load_3d_pair(st + PL * RG::A_BYTES + j * RG::B_BYTES, &P.tmB[q], fb, kx, brow, pb);
             }
           }
         }
@@ -1033,7 +1055,7 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
             tc::fence_after();
             const unsigned char* st = tiles + (size_t)s * STAGE_BYTES;
             const uint32_t d_re = tbase + buf * 256, d_im = d_re + 128;
-            if (np == 1) issue_stage_1p<BF16, NT, true>(st, d_re, d_im, first, min(NT, nK - kc * NT));
+            if (np == 1) issue_stage_1p<false, NT, true>(st, d_re, d_im, first, min(NT, nK - kc * NT));
             else issue_stage<BF16, NT, true>(st, d_re, d_im, first, np);
             tc::mma_commit_pair(&bar->empty[s], 0x3);
             if (++pos == ck || kc == nks - 1) {
@@ -1135,19 +1157,25 @@ bool tc_supported(std::string* why) {
 
 int n_terms(const chi0_plan_s* p) { return p->n_products == 6 ? 3 : 2; }
 
+// B planes: the terms of Re M and Im M, and in BF16 Hermitian plans the FP16 term 0
+// of both (operands of the one-product W2 parts)
+int b_planes(const chi0_plan_s* p) {
+  return 2 * n_terms(p) + (p->prec == CHI0_SPLIT_BF16 && p->tc_herm ? 2 : 0);
+}
+
 // A planes per frequency and part: W (plain) or W1 and W2 (Hermitian mode)
 int n_parts(const chi0_plan_s* p) { return p->tc_herm ? 2 : 1; }
 
 size_t planes_bytes(const chi0_plan_s* p) {
   const size_t nGp = (size_t)round_up_i(p->max_nG, 2 * BM);
   const size_t Kp = (size_t)((p->max_pairs + 63) / 64 * 64);
-  return 2 * (size_t)n_terms(p) * (1 + (size_t)n_parts(p) * p->n_freq) * nGp * Kp * 2;
+  return ((size_t)b_planes(p) + 2 * (size_t)n_terms(p) * n_parts(p) * p->n_freq) * nGp * Kp * 2;
 }
 
 size_t tc_pack_bytes(const chi0_plan_s* p, int64_t max_pairs, int max_nG) {
   const size_t nGp = (size_t)round_up_i(max_nG, 2 * BM);
   const size_t Kp = (size_t)((max_pairs + 63) / 64 * 64);
-  const size_t planes = 2 * (size_t)n_terms(p) * (1 + (size_t)n_parts(p) * p->n_freq);
+  const size_t planes = (size_t)b_planes(p) + 2 * (size_t)n_terms(p) * n_parts(p) * p->n_freq;
   // amax, ratio range, scales, inverse scales, W2 products, ratios t
   const size_t scal = 256 + 64 * (size_t)(p->n_freq + 1);
   return planes * nGp * Kp * 2 + scal;
@@ -1176,7 +1204,7 @@ static PackWs pack_ws(const chi0_plan_s* p, void* base, int nGp, int Kp) {
   const size_t nf1 = (size_t)(p->n_freq + 1);
   PackWs w;
   w.Bp = reinterpret_cast<uint16_t*>(base);
-  w.Ap = w.Bp + (size_t)2 * n_terms(p) * nGp * Kp;
+  w.Ap = w.Bp + (size_t)b_planes(p) * nGp * Kp;
   unsigned char* tail = reinterpret_cast<unsigned char*>(base) + planes_bytes(p);
   w.amax = reinterpret_cast<unsigned int*>(tail);            // 1 + 2 n_freq words
   w.tr = reinterpret_cast<unsigned int*>(tail + 8 * nf1);     // 2 n_freq words
@@ -1228,7 +1256,7 @@ static cudaError_t run_tc(chi0_plan_s* p, const TcJob* jobs, int n_jobs, int64_t
       if (e != cudaSuccess) { delete P; return e; }
       if (mode == 1) continue;
     }
-    if (!encode_planes(&P->tmB[j], w.Bp, BF16, Kp, nGp, 2 * NT, why, pair ? BN / 2 : BN) ||
+    if (!encode_planes(&P->tmB[j], w.Bp, BF16, Kp, nGp, b_planes(p), why, pair ? BN / 2 : BN) ||
         !encode_planes(&P->tmA[j], w.Ap, BF16, Kp, nGp, 2 * NT * n_parts(p) * p->n_freq, why, BM)) {
       delete P;
       return cudaErrorInvalidValue;

@@ -321,7 +321,8 @@ def test_hermitian_shifted_h2_one_product(precision, pair, monkeypatch):
     """Hermitian mode with the H2 weights shifted by the block's ratio t
     (chi0 = (1 + i t) H1 + i H2, H2 with g = Im f - t Re f): a block of
     neighbouring conduction energies has a narrow range of Im f / Re f, so its H2
-    part takes one product (FP16) or three; blocks of low-lying bands keep three.
+    part takes one product (FP16 operands in both precisions); blocks of
+    low-lying bands keep three.
     A one-product H2 part is a single chain added together with H1 (the fused
     epilogue), the others are added part by part.  Several blocks of each kind,
     ragged sphere, both kernel variants, against the oracle and the plain
