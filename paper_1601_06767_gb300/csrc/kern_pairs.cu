@@ -642,8 +642,8 @@ cudaError_t launch_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void
 }
 
 // ---------------------------------------------------------------------------
-// Stages 1+2 on the 96^3 grid (n = 3Q, Q = 32) with warp-cooperative
-// transforms: a warp transforms one line.  A line is split as i = a + 3b
+// Warp-cooperative length-96 transforms (n = 3Q, Q = 32) of the 96^3
+// wavefunction passes: a warp transforms one line.  A line is split as i = a + 3b
 // (a < 3, b < Q): lane b holds x(3b), x(3b+1), x(3b+2) (24 contiguous bytes,
 // so the warp reads its row at once), the three Q-point transforms
 // F_a(m) = sum_b x(a+3b) e^{2 pi i m b/Q} run across the lanes by radix-2
@@ -651,7 +651,8 @@ cudaError_t launch_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void
 // F_a(bitrev(b))), and lane b forms, for kk = bitrev(b) + Q t (t < 3),
 //   y(kk) = F_0(kk mod Q) + e^{2 pi i kk/n} F_1(kk mod Q) + e^{4 pi i kk/n} F_2(kk mod Q).
 // (On 48^3, Q = 16 with two lines per warp measured slower than the
-// per-thread register FFTs above, so 48^3 keeps those.)
+// per-thread register FFTs above, so 48^3 keeps those.)  WL_NKMAX: the largest
+// kept extent along i2 and i3 that the 96^3 pair kernel below takes.
 constexpr int WL_NKMAX = 32;
 
 __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
@@ -717,53 +718,93 @@ __device__ __forceinline__ void wl_line(float2 (&x)[3], const WLConsts<Q, NS>& c
   }
 }
 
-// The same length-3Q line with the other index split, i = b + Q a: lane b holds
-// x(b + Q a) in x[a] (a warp's load of x[a] is 8 Q contiguous bytes, against
-// 24 Q spread over the whole row for i = a + 3 b).  Per lane, the 3-point
-// transforms Z_k0 = sum_a x(b + Q a) e^{2 pi i a k0/3} times e^{2 pi i b k0/n},
-// then the Q-point transforms over b across the lanes; lane b ends with
-// y[k0] = y(k0 + 3 bitrev(b)).  tb1, tb2 = e^{2 pi i b/n}, e^{4 pi i b/n}.
-template <int Q, int NS>
-__device__ __forceinline__ void wl_line_t(float2 (&x)[3], const WLConsts<Q, NS>& c, float2 tb1, float2 tb2) {
+// ---------------------------------------------------------------------------
+// Stages 1+2 on the 96^3 grid with 16 lanes per line (two lines per warp): a
+// line is split as i = b + 16 a (b < 16, a < 6), lane b of a half-warp holding
+// x(b + 16 a) (a half-warp's load of x[a] is 128 contiguous bytes).  Per lane,
+// the 6-point transforms Z_k0 = sum_a x(b + 16 a) e^{2 pi i a k0/6} (2 x 3:
+// sums and differences of x_a and x_{a+3}, two fixed twiddles, two 3-point
+// transforms), the twiddles e^{2 pi i b k0/96}, then the 16-point transforms
+// over b across the half-warp (4 shuffle stages, against 5 for 32 lanes; a
+// line moves 24 values per lane pair instead of 30); lane b ends with
+// y[k0] = y(k0 + 6 bitrev4(b)).
+struct W16Consts {
+  float2 tw[3];      // stage twiddles of the upper lane (1 for the lower), stages of span 8, 4, 2
+  float sg[4];       // +1 lower lane, -1 upper lane, spans 8, 4, 2, 1
+  float2 tb[6];      // e^{2 pi i b k0/96}
+  int kk;            // bitrev4(b)
+};
+__device__ __forceinline__ W16Consts w16_consts(int b) {
+  W16Consts c;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int h = 8 >> s;
+    const bool upper = (b & h) != 0;
+    c.sg[s] = upper ? -1.f : 1.f;
+    if (s < 3) c.tw[s] = upper ? root<96>((b % h) * (96 / (2 * h))) : make_float2(1.f, 0.f);
+  }
+  c.kk = bitrev<16>(b);
+#pragma unroll
+  for (int k0 = 0; k0 < 6; ++k0) c.tb[k0] = root<96>((b * k0) % 96);
+  return c;
+}
+
+// (a, b, c) <- Y_k = sum_j x_j e^{2 pi i jk/3}
+__device__ __forceinline__ void dft3p(float2& a, float2& b, float2& c) {
   constexpr float h = k_roots24.im[4];           // sin(pi/3)
-  const float2 s = make_float2(x[1].x + x[2].x, x[1].y + x[2].y);
-  const float2 d = make_float2(x[1].x - x[2].x, x[1].y - x[2].y);
-  const float2 m = make_float2(fmaf(-0.5f, s.x, x[0].x), fmaf(-0.5f, s.y, x[0].y));
-  x[0] = make_float2(x[0].x + s.x, x[0].y + s.y);
-  x[1] = cmul(make_float2(fmaf(-h, d.y, m.x), fmaf(h, d.x, m.y)), tb1);
-  x[2] = cmul(make_float2(fmaf(h, d.y, m.x), fmaf(-h, d.x, m.y)), tb2);
+  const float2 s = make_float2(b.x + c.x, b.y + c.y), d = make_float2(b.x - c.x, b.y - c.y);
+  const float2 m = make_float2(fmaf(-0.5f, s.x, a.x), fmaf(-0.5f, s.y, a.y));
+  a = make_float2(a.x + s.x, a.y + s.y);
+  b = make_float2(fmaf(-h, d.y, m.x), fmaf(h, d.x, m.y));
+  c = make_float2(fmaf(h, d.y, m.x), fmaf(-h, d.x, m.y));
+}
+
+__device__ __forceinline__ void w16_line(float2 (&x)[6], const W16Consts& c) {
+  // 6-point transform: even outputs from u_j = x_j + x_{j+3}, odd ones from
+  // v_j = (x_j - x_{j+3}) e^{2 pi i j/6}
+  float2 u0 = make_float2(x[0].x + x[3].x, x[0].y + x[3].y), v0 = make_float2(x[0].x - x[3].x, x[0].y - x[3].y);
+  float2 u1 = make_float2(x[1].x + x[4].x, x[1].y + x[4].y), v1 = make_float2(x[1].x - x[4].x, x[1].y - x[4].y);
+  float2 u2 = make_float2(x[2].x + x[5].x, x[2].y + x[5].y), v2 = make_float2(x[2].x - x[5].x, x[2].y - x[5].y);
+  v1 = cmul(v1, root<96>(16));
+  v2 = cmul(v2, root<96>(32));
+  dft3p(u0, u1, u2);
+  dft3p(v0, v1, v2);
+  x[0] = u0;
+  x[1] = cmul(v0, c.tb[1]);
+  x[2] = cmul(u1, c.tb[2]);
+  x[3] = cmul(v1, c.tb[3]);
+  x[4] = cmul(u2, c.tb[4]);
+  x[5] = cmul(v2, c.tb[5]);
+  // 16-point transforms across the half-warp: lower lane x + partner, upper lane (partner - x) twiddle
 #pragma unroll
-  for (int st = 0; st < WLConsts<Q, NS>::LOGQ; ++st) {
-    const int hh = (Q / 2) >> st;
+  for (int s = 0; s < 4; ++s) {
+    const int h = 8 >> s;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float2 p = shfl_xor2(x[a], hh);
-      const float2 u = make_float2(fmaf(c.sg[st], x[a].x, p.x), fmaf(c.sg[st], x[a].y, p.y));
-      x[a] = (hh == 1) ? u : cmul(u, c.tw[st]);
+    for (int a = 0; a < 6; ++a) {
+      const float2 p = shfl_xor2(x[a], h);
+      const float2 u = make_float2(fmaf(c.sg[s], x[a].x, p.x), fmaf(c.sg[s], x[a].y, p.y));
+      x[a] = (s < 3) ? cmul(u, c.tw[s < 3 ? s : 0]) : u;
     }
   }
 }
 
-// One CTA per (valence band, plane i1) and a run of conduction bands:
-//   stage 1: warp w transforms rows i2 = w, w+8, ... of conj(u_v) u_c along i3 into X[i2][k3];
-//   stage 2: warp w transforms the kept columns k3 = w, w+8, ... of X along i2 into Y[k2][k3];
-//   Y is copied to D[pair][i1] (contiguous nk2 x nk3 values).
-// Lines are split as i = b + Q a (wl_line_t).  No frequency shift is applied to
-// the inputs: a line keeps the outputs y(k) for k in [kmin, kmin + nk) mod n,
-// lane b forming y(t + 3 bitrev(b)) for t < 3 and storing those in range.  Both rows of a pair are read
-// from global memory (the valence row once per conduction band, from L2), so
-// the CTA holds only X and Y (24 KB) and several CTAs fit on an SM.
-constexpr int WN_WARPS = 8;
+constexpr int W16_WARPS = 8;
 
-template <int Q>
-__global__ void __launch_bounds__(WN_WARPS * 32)
-k_pair_planes_wn(const float2* __restrict__ psi_v, const int32_t* __restrict__ v_idx, int v0, int nv,
-                 const float2* __restrict__ psi_c, const int32_t* __restrict__ c_idx, int c0, int nc, int c_per_cta,
-                 int k2min, int k3min, int nk2, int nk3, float2* __restrict__ D) {
-  static_assert(Q == 32, "one line per warp");
-  constexpr int n = 3 * Q;
+// One CTA per (valence band, plane i1) and a run of conduction bands:
+//   stage 1: line slot l = 2 w + (lane / 16) transforms rows i2 = l + 16 j of
+//            conj(u_v) u_c along i3 into X[i2][k3];
+//   stage 2: the kept columns k3 of X along i2 into Y[k2][k3];
+//   Y is copied to D[pair][i1] (contiguous nk2 x nk3 values).
+// No frequency shift is applied to the inputs: a line keeps the outputs y(k) for
+// k in [kmin, kmin + nk) mod 96, lane b forming y(k0 + 6 bitrev4(b)), k0 < 6.
+__global__ void __launch_bounds__(W16_WARPS * 32)
+k_pair_planes_w16(const float2* __restrict__ psi_v, const int32_t* __restrict__ v_idx, int v0, int nv,
+                  const float2* __restrict__ psi_c, const int32_t* __restrict__ c_idx, int c0, int nc, int c_per_cta,
+                  int k2min, int k3min, int nk2, int nk3, float2* __restrict__ D) {
+  constexpr int n = 96;
   constexpr int64_t nr = (int64_t)n * n * n;
   constexpr int plane = n * n;
+  constexpr int LINES = W16_WARPS * 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ldx = nk3 | 1;
   float2* X = reinterpret_cast<float2*>(smem_raw);   // [n][ldx]
@@ -773,46 +814,51 @@ k_pair_planes_wn(const float2* __restrict__ psi_v, const int32_t* __restrict__ v
   const int jc_begin = blockIdx.z * c_per_cta;
   const int jc_end = min(nc, jc_begin + c_per_cta);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = lane & 15, slot = warp * 2 + (lane >> 4);
   const int box = nk2 * nk3;
   if (jv >= nv || jc_begin >= jc_end) return;
-  const WLConsts<Q, 3> cst = wl_consts<Q, 3>(lane);
-  const float2 tb1 = root<n>(lane), tb2 = root<n>(2 * lane);
-  // slot of output y(t + 3 bitrev(lane)) in the kept range along i3 / i2, or -1
-  int o3[3], o2[3];
+  const W16Consts cst = w16_consts(b);
+  // slot of output y(k0 + 6 bitrev4(b)) in the kept range along i3 / i2, or -1
+  int o3[6], o2[6];
 #pragma unroll
-  for (int t = 0; t < 3; ++t) {
-    const int k = t + 3 * cst.kk;
+  for (int k0 = 0; k0 < 6; ++k0) {
+    const int k = k0 + 6 * cst.kk;
     const int d3 = ((k - k3min) % n + n) % n, d2 = ((k - k2min) % n + n) % n;
-    o3[t] = d3 < nk3 ? d3 : -1;
-    o2[t] = d2 < nk2 ? d2 : -1;
+    o3[k0] = d3 < nk3 ? d3 : -1;
+    o2[k0] = d2 < nk2 ? d2 : -1;
   }
   const int64_t vband = v_idx ? v_idx[v0 + jv] : v0 + jv;
   const float2* vsrc = psi_v + vband * nr + (int64_t)i1 * plane;
   for (int jc = jc_begin; jc < jc_end; ++jc) {
     const int64_t band = c_idx ? c_idx[c0 + jc] : c0 + jc;
     const float2* csrc = psi_c + band * nr + (int64_t)i1 * plane;
-    // stage 1: rows
-    for (int i2 = warp; i2 < n; i2 += WN_WARPS) {
-      const float2* uc = csrc + i2 * n + lane;
-      const float2* uv = vsrc + i2 * n + lane;
-      float2 x[3];
+    // stage 1: rows (96 = 6 x 16 lines, the same count for every slot)
+    for (int i2 = slot; i2 < n; i2 += LINES) {
+      const float2* uc = csrc + i2 * n + b;
+      const float2* uv = vsrc + i2 * n + b;
+      float2 x[6];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) x[a] = cconjmul(__ldg(uv + Q * a), __ldg(uc + Q * a));
-      wl_line_t<Q, 3>(x, cst, tb1, tb2);
+      for (int a = 0; a < 6; ++a) x[a] = cconjmul(__ldg(uv + 16 * a), __ldg(uc + 16 * a));
+      w16_line(x, cst);
 #pragma unroll
-      for (int t = 0; t < 3; ++t)
-        if (o3[t] >= 0) X[i2 * ldx + o3[t]] = x[t];
+      for (int k0 = 0; k0 < 6; ++k0)
+        if (o3[k0] >= 0) X[i2 * ldx + o3[k0]] = x[k0];
     }
     __syncthreads();
-    // stage 2: kept columns
-    for (int k3 = warp; k3 < nk3; k3 += WN_WARPS) {
-      float2 x[3];
+    // stage 2: kept columns, a warp-uniform loop (a half-warp past nk3 transforms zeros)
+    for (int kb = warp * 2; kb < nk3; kb += LINES) {
+      const int k3 = kb + (lane >> 4);
+      const bool valid = k3 < nk3;
+      const float2* col = X + b * ldx + (valid ? k3 : 0);
+      float2 x[6];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) x[a] = X[(lane + Q * a) * ldx + k3];
-      wl_line_t<Q, 3>(x, cst, tb1, tb2);
+      for (int a = 0; a < 6; ++a) x[a] = col[16 * a * ldx];
+      w16_line(x, cst);
+      if (valid) {
 #pragma unroll
-      for (int t = 0; t < 3; ++t)
-        if (o2[t] >= 0) Y[o2[t] * nk3 + k3] = x[t];
+        for (int k0 = 0; k0 < 6; ++k0)
+          if (o2[k0] >= 0) Y[o2[k0] * nk3 + k3] = x[k0];
+      }
     }
     __syncthreads();
     float2* dst = D + ((int64_t)(jv * nc + jc) * n + i1) * box;
@@ -820,21 +866,19 @@ k_pair_planes_wn(const float2* __restrict__ psi_v, const int32_t* __restrict__ v
   }
 }
 
-template <int Q>
-cudaError_t launch_planes_wn(const chi0_plan_s* p, const SphereQ& s, const void* psi_v, const int32_t* v_idx,
-                             int v0, int nv, const void* psi_c, const int32_t* c_idx, int c0, int nc, void* D,
-                             cudaStream_t st) {
-  constexpr int n = 3 * Q;
+cudaError_t launch_planes_w16(const chi0_plan_s* p, const SphereQ& s, const void* psi_v, const int32_t* v_idx,
+                              int v0, int nv, const void* psi_c, const int32_t* c_idx, int c0, int nc, void* D,
+                              cudaStream_t st) {
+  constexpr int n = 96;
   const size_t sm = ((size_t)n * (s.nk3 | 1) + (size_t)s.nk2 * s.nk3) * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(k_pair_planes_wn<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(k_pair_planes_w16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int cpc = 16;
   while (cpc > 1 && (int64_t)p->n1 * nv * ((nc + cpc - 1) / cpc) < 8 * 152) cpc >>= 1;
   // valence bands fastest: the CTAs running at a time share one plane's conduction rows in L2
   dim3 grid(nv, p->n1, (nc + cpc - 1) / cpc);
-  k_pair_planes_wn<Q><<<grid, WN_WARPS * 32, sm, st>>>((const float2*)psi_v, v_idx, v0, nv, (const float2*)psi_c,
-                                                       c_idx, c0, nc, cpc, s.k2min, s.k3min, s.nk2, s.nk3,
-                                                       (float2*)D);
+  k_pair_planes_w16<<<grid, W16_WARPS * 32, sm, st>>>((const float2*)psi_v, v_idx, v0, nv, (const float2*)psi_c, c_idx,
+                                                      c0, nc, cpc, s.k2min, s.k3min, s.nk2, s.nk3, (float2*)D);
   return cudaGetLastError();
 }
 
@@ -935,7 +979,7 @@ cudaError_t try_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void* p
   const int nk = std::max(s.nk2, s.nk3);
   if (!(p->n1 == p->n2 && p->n2 == p->n3)) return cudaErrorNotSupported;
   if (p->n3 == 96 && nk <= WL_NKMAX)
-    return launch_planes_wn<32>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
+    return launch_planes_w16(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
   if (nk > NKMAX) return cudaErrorNotSupported;
 #define CHI0_FFT_CASE(P, Q, TV, NCB)                                                                    \
   if (nk <= 12) return launch_fft_planes<P, Q, 12, TV, NCB>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st); \
