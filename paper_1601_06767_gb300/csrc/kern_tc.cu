@@ -14,7 +14,8 @@
 //           B = {Mr_t..., Mi_t...}[nGp][Kp], A_w = {Wr_t..., Wi_t...}[nGp][Kp].
 // contract: one CTA per (128 x 128 output tile, frequency).  Warp 0 issues TMA
 //           loads into a 3-stage ring, warp 1 issues tcgen05.mma into two
-//           double-buffered TMEM accumulator pairs (Re, Im), warps 2..9 drain
+//           double-buffered TMEM accumulator pairs (Re, Im) (warps 0-3 on few
+//           registers, given to the epilogue by setmaxnreg), warps 4..11 drain
 //           finished accumulation chains into FP32 registers and finally add
 //           the tile into chi0 by FP64 reductions (the additions run in L2).
 //
@@ -52,7 +53,19 @@ constexpr int BM = 128, BN = 128, BK = 32;
 constexpr int TILE_BYTES = BM * BK * 2;           // 8 KB per plane tile
 constexpr int RING_BYTES = 6 * 32768;              // operand ring in shared memory
 constexpr int EPI_WARPS = 8;
-constexpr int THREADS = 64 + EPI_WARPS * 32;
+constexpr int EPI_WARP0 = 4;                       // warpgroup 0: TMA producer, MMA issuer, two idle warps
+constexpr int THREADS = EPI_WARP0 * 32 + EPI_WARPS * 32;
+// Register split between warpgroups (setmaxnreg): the launch gives every thread
+// REG_LAUNCH registers (the most 384 threads can have); warpgroup 0 gives back
+// down to REG_LOW and the two epilogue warpgroups take REG_HIGH, so that the
+// epilogue's FP32 sums (128 per thread) and a TMEM load buffer fit without
+// spilling.  The increase waits until the pool holds the registers, so the
+// shares must add up to no more than the launch's total; the host checks that
+// the compiled kernel uses exactly REG_LAUNCH before launching it.
+constexpr int REG_LAUNCH = 168, REG_LOW = 72, REG_HIGH = 216;
+static_assert(EPI_WARP0 * 32 * REG_LOW + EPI_WARPS * 32 * REG_HIGH <= THREADS * REG_LAUNCH,
+              "register split exceeds the launch's registers");
+static_assert(THREADS * REG_LAUNCH <= 65536 && REG_LAUNCH * THREADS / 4 <= 16384 * 4, "launch registers");
 constexpr int TMEM_COLS = 512;                     // 2 buffers x (Re, Im) x 128 columns
 constexpr uint64_t WAIT_BUDGET_NS = 2000000000ull; // 2 s per wait
 constexpr size_t SMEM_BYTES = (size_t)RING_BYTES + 1024 /*align*/ + 256 /*barriers*/;
@@ -646,9 +659,9 @@ __device__ __forceinline__ void merge_row_fused(double2* __restrict__ chi_w, int
   }
 }
 
-// Drain the nch accumulation chains of one part into the FP32 sums (zeroed first).
-// One 32-column load in flight (the sums fill the registers); each buffer is
-// released as soon as its last values are in registers, before they are added.
+// Drain the nch accumulation chains of one part into the FP32 sums (zeroed first),
+// two 32-column loads at a time; each buffer is released as soon as its last
+// values are in registers, before they are added.
 // keep_last: the last chain's buffer is not released and receives the part's
 // total sums (held for a later merge).  Returns false when a bounded wait ran out.
 template <bool PAIR, class BarT>
@@ -662,25 +675,23 @@ __device__ __forceinline__ bool drain_part(BarT* bar, uint32_t tbase, int quad, 
     if (!tc::mbar_wait(&bar->tfull[buf], (uint32_t)((gc >> 1) & 1), status, 1, WAIT_BUDGET_NS)) return false;
     tc::fence_after();
     const uint32_t ta = tbase + ((uint32_t)(quad * 32) << 16) + buf * 256 + half * 64;
-    float v[32];
+    // two loads in flight (the epilogue warps hold REG_HIGH registers); the buffer is
+    // released as soon as its last values are in registers, before they are added
+    float v[32], w[32];
     tc::tmem_ld32(ta, v);
+    tc::tmem_ld32(ta + 32, w);
     tc::tmem_ld_wait();
     tc::reg_after_wait(v);
+    tc::reg_after_wait(w);
 #pragma unroll
     for (int i = 0; i < 32; ++i) sre[i] += v[i];
-    tc::tmem_ld32(ta + 32, v);
-    tc::tmem_ld_wait();
-    tc::reg_after_wait(v);
 #pragma unroll
-    for (int i = 0; i < 32; ++i) sre[32 + i] += v[i];
+    for (int i = 0; i < 32; ++i) sre[32 + i] += w[i];
     tc::tmem_ld32(ta + 128, v);
+    tc::tmem_ld32(ta + 160, w);
     tc::tmem_ld_wait();
     tc::reg_after_wait(v);
-#pragma unroll
-    for (int i = 0; i < 32; ++i) sim[i] += v[i];
-    tc::tmem_ld32(ta + 160, v);
-    tc::tmem_ld_wait();
-    tc::reg_after_wait(v);
+    tc::reg_after_wait(w);
     if (!(keep_last && c == nch - 1)) {
       tc::fence_before();
       __syncwarp();
@@ -690,7 +701,9 @@ __device__ __forceinline__ bool drain_part(BarT* bar, uint32_t tbase, int quad, 
       }
     }
 #pragma unroll
-    for (int i = 0; i < 32; ++i) sim[32 + i] += v[i];
+    for (int i = 0; i < 32; ++i) sim[i] += v[i];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) sim[32 + i] += w[i];
   }
   if (keep_last) {
     const uint32_t ta = tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)((gc - 1) & 1) * 256 + half * 64;
@@ -788,6 +801,10 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
   tc::fence_after();
   const uint32_t tbase = bar->tmem_base;
 
+  // warpgroup 0 (producer, issuer, two idle warps) runs on REG_LOW registers,
+  // the epilogue warpgroups on REG_HIGH
+  if (warp < EPI_WARP0) {
+  tc::setmaxnreg_dec<REG_LOW>();
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer ----------------
@@ -886,9 +903,11 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
       tc::mma_commit(&bar->done);
       tc::mbar_wait(&bar->done, 0, status, 1, WAIT_BUDGET_NS);
     }
+  }
   } else {
+    tc::setmaxnreg_inc<REG_HIGH>();
     // ---------------- epilogue: drain chains, then FP64 reductions per item ----------------
-    const int ew = warp - 2, quad = warp & 3, half = ew >> 2;
+    const int ew = warp - EPI_WARP0, quad = warp & 3, half = ew >> 2;
     const int row = quad * 32 + lane;
     int64_t gc = 0;
     bool ok = true;
@@ -970,6 +989,10 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
   tc::fence_after();
   const uint32_t tbase = bar->tmem_base;
 
+  // warpgroup 0 (producer, issuer, two idle warps) runs on REG_LOW registers,
+  // the epilogue warpgroups on REG_HIGH
+  if (warp < EPI_WARP0) {
+  tc::setmaxnreg_dec<REG_LOW>();
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer (both CTAs) ----------------
@@ -1069,9 +1092,11 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
       tc::mma_commit_pair(&bar->done, 0x1);
       tc::mbar_wait(&bar->done, 0, status, 1, WAIT_BUDGET_NS);
     }
+  }
   } else {
+    tc::setmaxnreg_inc<REG_HIGH>();
     // ---------------- epilogue (both CTAs, own 128 rows) ----------------
-    const int ew = warp - 2, quad = warp & 3, half = ew >> 2;
+    const int ew = warp - EPI_WARP0, quad = warp & 3, half = ew >> 2;
     const int row = quad * 32 + lane;
     int64_t gc = 0;
     bool ok = true;
@@ -1239,6 +1264,27 @@ static cudaError_t pack_one(chi0_plan_s* p, int nG, const float2* M, int64_t K, 
   return cudaGetLastError();
 }
 
+// The warpgroups' register split inside the contraction kernels (REG_LOW, REG_HIGH)
+// adds up to the registers of a launch with REG_LAUNCH per thread; a build that
+// compiled the kernel with another count would make the increase wait forever,
+// so such a kernel is never launched.
+template <class Kern>
+static bool regs_match(Kern kern, std::string* why) {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, kern) != cudaSuccess) {
+    cudaGetLastError();
+    if (why) *why = "cannot read the contraction kernel's attributes";
+    return false;
+  }
+  if (a.numRegs != REG_LAUNCH) {
+    if (why)
+      *why = "contraction kernel compiled with " + std::to_string(a.numRegs) + " registers per thread; its "
+             "warpgroup register split needs " + std::to_string(REG_LAUNCH);
+    return false;
+  }
+  return true;
+}
+
 template <bool BF16, int NT>
 static cudaError_t run_tc(chi0_plan_s* p, const TcJob* jobs, int n_jobs, int64_t K, cudaStream_t s,
                           std::string* why, int mode) {
@@ -1293,6 +1339,7 @@ static cudaError_t run_tc(chi0_plan_s* p, const TcJob* jobs, int n_jobs, int64_t
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e;
   if (pair) {
+    if (!regs_match(k_contract_tc2<BF16, NT>, why)) { delete P; return cudaErrorNotSupported; }
     e = cudaFuncSetAttribute(k_contract_tc2<BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)SMEM2_BYTES);
     if (e != cudaSuccess) { delete P; return e; }
@@ -1300,6 +1347,7 @@ static cudaError_t run_tc(chi0_plan_s* p, const TcJob* jobs, int n_jobs, int64_t
     ProfScope ps(p, CHI0_K_CONTRACT_TC, s, 1);
     k_contract_tc2<BF16, NT><<<2 * pairs, THREADS, SMEM2_BYTES, s>>>(*P, p->d_status);
   } else {
+    if (!regs_match(k_contract_tc<BF16, NT>, why)) { delete P; return cudaErrorNotSupported; }
     e = cudaFuncSetAttribute(k_contract_tc<BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)SMEM_BYTES);
     if (e != cudaSuccess) { delete P; return e; }
