@@ -197,7 +197,7 @@ def algorithmic_flops(nG: int, n_pairs: int, n_freq: int) -> float:
 # ---------------------------------------------------------------------------
 # the oracle on host cores (cpu_baseline / reference arm)
 # ---------------------------------------------------------------------------
-def h2_products(Ev, Ec, omega, delta, n_prod, precision, block_cols=None):
+def h2_products(Ev, Ec, omega, delta, n_prod, block_cols=None):
     """Products of the H2 part per frequency in Hermitian mode, as the library
     decides them per block of conduction columns (block_cols columns with all
     valence bands; the mean over the blocks): with t the midrange of
@@ -704,7 +704,7 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (tensor-core contraction) ----
     n_prod = {"fp16": 3, "bf16": 6}[args.precision] if args.n_products == 0 else args.n_products
-    n2 = h2_products(prob.E_v, prob.E_c[bands], prob.omega, prob.delta, n_prod, args.precision,
+    n2 = h2_products(prob.E_v, prob.E_c[bands], prob.omega, prob.delta, n_prod,
                      max(1, tuning["block_pairs"] // prob.n_v))
     traffic = profiled_traffic("paper_1601_06767_gb300/csrc/kern_tc.cu", f"contract_tc_c5_{args.precision}.md")
     roof = contraction_roofline(prof, F * args.steps, n_pairs * args.steps, n_prod, n2, nG, nf, plan.hermitian,
@@ -818,7 +818,7 @@ def c2_study(args, pkg, dev, world):
 
     ms, prof = timed(plan, chi, args.c2_steps)
     n_prod = {"fp16": 3, "bf16": 6}[prec]
-    n2 = h2_products(prob.E_v, prob.E_c, prob.omega, prob.delta, n_prod, prec,
+    n2 = h2_products(prob.E_v, prob.E_c, prob.omega, prob.delta, n_prod,
                      max(1, tuning["block_pairs"] // prob.n_v))
     roof = contraction_roofline(prof, F * args.c2_steps, n_pairs * args.c2_steps, n_prod, n2, nG, nf,
                                 plan.hermitian, tuning["cta_pair"],
