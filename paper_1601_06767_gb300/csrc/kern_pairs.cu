@@ -719,36 +719,6 @@ __device__ __forceinline__ void wl_line(float2 (&x)[3], const WLConsts<Q, NS>& c
 }
 
 // ---------------------------------------------------------------------------
-// Stages 1+2 on the 96^3 grid with 16 lanes per line (two lines per warp): a
-// line is split as i = b + 16 a (b < 16, a < 6), lane b of a half-warp holding
-// x(b + 16 a) (a half-warp's load of x[a] is 128 contiguous bytes).  Per lane,
-// the 6-point transforms Z_k0 = sum_a x(b + 16 a) e^{2 pi i a k0/6} (2 x 3:
-// sums and differences of x_a and x_{a+3}, two fixed twiddles, two 3-point
-// transforms), the twiddles e^{2 pi i b k0/96}, then the 16-point transforms
-// over b across the half-warp (4 shuffle stages, against 5 for 32 lanes; a
-// line moves 24 values per lane pair instead of 30); lane b ends with
-// y[k0] = y(k0 + 6 bitrev4(b)).
-struct W16Consts {
-  float2 tw[3];      // stage twiddles of the upper lane (1 for the lower), stages of span 8, 4, 2
-  float sg[4];       // +1 lower lane, -1 upper lane, spans 8, 4, 2, 1
-  float2 tb[6];      // e^{2 pi i b k0/96}
-  int kk;            // bitrev4(b)
-};
-__device__ __forceinline__ W16Consts w16_consts(int b) {
-  W16Consts c;
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    const int h = 8 >> s;
-    const bool upper = (b & h) != 0;
-    c.sg[s] = upper ? -1.f : 1.f;
-    if (s < 3) c.tw[s] = upper ? root<96>((b % h) * (96 / (2 * h))) : make_float2(1.f, 0.f);
-  }
-  c.kk = bitrev<16>(b);
-#pragma unroll
-  for (int k0 = 0; k0 < 6; ++k0) c.tb[k0] = root<96>((b * k0) % 96);
-  return c;
-}
-
 // (a, b, c) <- Y_k = sum_j x_j e^{2 pi i jk/3}
 __device__ __forceinline__ void dft3p(float2& a, float2& b, float2& c) {
   constexpr float h = k_roots24.im[4];           // sin(pi/3)
@@ -759,9 +729,48 @@ __device__ __forceinline__ void dft3p(float2& a, float2& b, float2& c) {
   c = make_float2(fmaf(h, d.y, m.x), fmaf(-h, d.x, m.y));
 }
 
-__device__ __forceinline__ void w16_line(float2 (&x)[6], const W16Consts& c) {
-  // 6-point transform: even outputs from u_j = x_j + x_{j+3}, odd ones from
-  // v_j = (x_j - x_{j+3}) e^{2 pi i j/6}
+// ---------------------------------------------------------------------------
+// Stages 1+2 on the 96^3 grid with 8 lanes per line (four lines per warp).  A
+// line is split as i = c + 2 b + 16 j (c < 2, b < 8, j < 6): lane b of a group
+// of eight holds x(2 b + 16 j) and x(2 b + 16 j + 1) (one 16-byte load per j,
+// so a group's load of a row is 128 contiguous bytes).  With the output
+// k = kj + 6 kb + 48 kc (kj < 6, kb < 8, kc < 2) the exponent of e^{2 pi i/96}
+// reduces to c kj + 6 c kb + 48 c kc + 2 b kj + 12 b kb + 16 j kj, so per lane:
+// the 6-point transforms A_c(kj) = sum_j x(c + 2b + 16j) e^{2 pi i j kj/6}
+// times e^{2 pi i 2 b kj/96}; the 8-point transforms over b across the group (3
+// shuffle stages, against 4 for 16 lanes); then, lane b holding kb =
+// bitrev3(b), C_1 times e^{2 pi i (kj + 6 kb)/96} and the 2-point transform
+// over c: y(kj + 6 kb + 48 kc) = C_0 + (-1)^kc C_1.  A line moves 18 values
+// per lane pair through shuffles (24 with 16 lanes, 30 with a warp per line)
+// while its row loads still cover whole 128-byte lines.  128 registers, two
+// CTAs per SM: bounding the registers for three made it spill and run 1.7x
+// slower.
+struct W8Consts {
+  float2 t2b[6];     // e^{2 pi i 2 b kj/96}
+  float2 tkb[6];     // e^{2 pi i (kj + 6 kb)/96}
+  float2 tw4, tw2;   // stage twiddles of the upper lane (1 for the lower), spans 4 and 2
+  float sg4, sg2, sg1;
+  int kb;            // bitrev3(b)
+};
+__device__ __forceinline__ W8Consts w8_consts(int b) {
+  W8Consts c;
+  c.kb = bitrev<8>(b);
+#pragma unroll
+  for (int kj = 0; kj < 6; ++kj) {
+    c.t2b[kj] = root<96>((2 * b * kj) % 96);
+    c.tkb[kj] = root<96>((kj + 6 * c.kb) % 96);
+  }
+  c.sg4 = (b & 4) ? -1.f : 1.f;
+  c.sg2 = (b & 2) ? -1.f : 1.f;
+  c.sg1 = (b & 1) ? -1.f : 1.f;
+  c.tw4 = (b & 4) ? root<96>(12 * (b % 4)) : make_float2(1.f, 0.f);
+  c.tw2 = (b & 2) ? root<96>(24 * (b % 2)) : make_float2(1.f, 0.f);
+  return c;
+}
+
+// 6-point transform with e^{+2 pi i/6}: even outputs from u_j = x_j + x_{j+3}, odd
+// ones from v_j = (x_j - x_{j+3}) e^{2 pi i j/6}
+__device__ __forceinline__ void dft6p(float2 (&x)[6]) {
   float2 u0 = make_float2(x[0].x + x[3].x, x[0].y + x[3].y), v0 = make_float2(x[0].x - x[3].x, x[0].y - x[3].y);
   float2 u1 = make_float2(x[1].x + x[4].x, x[1].y + x[4].y), v1 = make_float2(x[1].x - x[4].x, x[1].y - x[4].y);
   float2 u2 = make_float2(x[2].x + x[5].x, x[2].y + x[5].y), v2 = make_float2(x[2].x - x[5].x, x[2].y - x[5].y);
@@ -770,41 +779,62 @@ __device__ __forceinline__ void w16_line(float2 (&x)[6], const W16Consts& c) {
   dft3p(u0, u1, u2);
   dft3p(v0, v1, v2);
   x[0] = u0;
-  x[1] = cmul(v0, c.tb[1]);
-  x[2] = cmul(u1, c.tb[2]);
-  x[3] = cmul(v1, c.tb[3]);
-  x[4] = cmul(u2, c.tb[4]);
-  x[5] = cmul(v2, c.tb[5]);
-  // 16-point transforms across the half-warp: lower lane x + partner, upper lane (partner - x) twiddle
+  x[1] = v0;
+  x[2] = u1;
+  x[3] = v1;
+  x[4] = u2;
+  x[5] = v2;
+}
+
+// x[c][j] = x(c + 2 b + 16 j) -> x[kc][kj] = y(kj + 6 bitrev3(b) + 48 kc)
+__device__ __forceinline__ void w8_line(float2 (&x)[2][6], const W8Consts& w) {
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    const int h = 8 >> s;
+  for (int c = 0; c < 2; ++c) {
+    dft6p(x[c]);
 #pragma unroll
-    for (int a = 0; a < 6; ++a) {
-      const float2 p = shfl_xor2(x[a], h);
-      const float2 u = make_float2(fmaf(c.sg[s], x[a].x, p.x), fmaf(c.sg[s], x[a].y, p.y));
-      x[a] = (s < 3) ? cmul(u, c.tw[s < 3 ? s : 0]) : u;
+    for (int kj = 1; kj < 6; ++kj) x[c][kj] = cmul(x[c][kj], w.t2b[kj]);
+  }
+  // 8-point transforms across the group: lower lane x + partner, upper lane (partner - x) twiddle
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int kj = 0; kj < 6; ++kj) {
+      float2 p = shfl_xor2(x[c][kj], 4);
+      float2 u = make_float2(fmaf(w.sg4, x[c][kj].x, p.x), fmaf(w.sg4, x[c][kj].y, p.y));
+      u = cmul(u, w.tw4);
+      p = shfl_xor2(u, 2);
+      u = make_float2(fmaf(w.sg2, u.x, p.x), fmaf(w.sg2, u.y, p.y));
+      u = cmul(u, w.tw2);
+      p = shfl_xor2(u, 1);
+      x[c][kj] = make_float2(fmaf(w.sg1, u.x, p.x), fmaf(w.sg1, u.y, p.y));
     }
+  // 2-point transforms over c
+#pragma unroll
+  for (int kj = 0; kj < 6; ++kj) {
+    const float2 t = cmul(x[1][kj], w.tkb[kj]);
+    const float2 a = x[0][kj];
+    x[0][kj] = make_float2(a.x + t.x, a.y + t.y);
+    x[1][kj] = make_float2(a.x - t.x, a.y - t.y);
   }
 }
 
-constexpr int W16_WARPS = 8;
+constexpr int W8_WARPS = 8;
 
 // One CTA per (valence band, plane i1) and a run of conduction bands:
-//   stage 1: line slot l = 2 w + (lane / 16) transforms rows i2 = l + 16 j of
+//   stage 1: line slot l = 4 w + (lane / 8) transforms rows i2 = l + 32 r of
 //            conj(u_v) u_c along i3 into X[i2][k3];
 //   stage 2: the kept columns k3 of X along i2 into Y[k2][k3];
 //   Y is copied to D[pair][i1] (contiguous nk2 x nk3 values).
 // No frequency shift is applied to the inputs: a line keeps the outputs y(k) for
-// k in [kmin, kmin + nk) mod 96, lane b forming y(k0 + 6 bitrev4(b)), k0 < 6.
-__global__ void __launch_bounds__(W16_WARPS * 32)
-k_pair_planes_w16(const float2* __restrict__ psi_v, const int32_t* __restrict__ v_idx, int v0, int nv,
-                  const float2* __restrict__ psi_c, const int32_t* __restrict__ c_idx, int c0, int nc, int c_per_cta,
-                  int k2min, int k3min, int nk2, int nk3, float2* __restrict__ D) {
+// k in [kmin, kmin + nk) mod 96.
+__global__ void __launch_bounds__(W8_WARPS * 32, 2)
+k_pair_planes_w8(const float2* __restrict__ psi_v, const int32_t* __restrict__ v_idx, int v0, int nv,
+                 const float2* __restrict__ psi_c, const int32_t* __restrict__ c_idx, int c0, int nc, int c_per_cta,
+                 int k2min, int k3min, int nk2, int nk3, float2* __restrict__ D) {
   constexpr int n = 96;
   constexpr int64_t nr = (int64_t)n * n * n;
   constexpr int plane = n * n;
-  constexpr int LINES = W16_WARPS * 2;
+  constexpr int LINES = W8_WARPS * 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ldx = nk3 | 1;
   float2* X = reinterpret_cast<float2*>(smem_raw);   // [n][ldx]
@@ -814,50 +844,60 @@ k_pair_planes_w16(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
   const int jc_begin = blockIdx.z * c_per_cta;
   const int jc_end = min(nc, jc_begin + c_per_cta);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b = lane & 15, slot = warp * 2 + (lane >> 4);
+  const int b = lane & 7, slot = warp * 4 + (lane >> 3);
   const int box = nk2 * nk3;
   if (jv >= nv || jc_begin >= jc_end) return;
-  const W16Consts cst = w16_consts(b);
-  // slot of output y(k0 + 6 bitrev4(b)) in the kept range along i3 / i2, or -1
-  int o3[6], o2[6];
-#pragma unroll
-  for (int k0 = 0; k0 < 6; ++k0) {
-    const int k = k0 + 6 * cst.kk;
-    const int d3 = ((k - k3min) % n + n) % n, d2 = ((k - k2min) % n + n) % n;
-    o3[k0] = d3 < nk3 ? d3 : -1;
-    o2[k0] = d2 < nk2 ? d2 : -1;
-  }
+  const W8Consts cst = w8_consts(b);
+  // kept-range slot of y(kj + 6 kb + 48 kc) is (base + kj + 48 kc) mod 96
+  const int base3 = ((6 * cst.kb - k3min) % n + n) % n, base2 = ((6 * cst.kb - k2min) % n + n) % n;
   const int64_t vband = v_idx ? v_idx[v0 + jv] : v0 + jv;
   const float2* vsrc = psi_v + vband * nr + (int64_t)i1 * plane;
   for (int jc = jc_begin; jc < jc_end; ++jc) {
     const int64_t band = c_idx ? c_idx[c0 + jc] : c0 + jc;
     const float2* csrc = psi_c + band * nr + (int64_t)i1 * plane;
-    // stage 1: rows (96 = 6 x 16 lines, the same count for every slot)
+    // stage 1: rows (96 = 3 x 32 lines, the same count for every slot)
     for (int i2 = slot; i2 < n; i2 += LINES) {
-      const float2* uc = csrc + i2 * n + b;
-      const float2* uv = vsrc + i2 * n + b;
-      float2 x[6];
+      const float4* uc = reinterpret_cast<const float4*>(csrc + i2 * n) + b;
+      const float4* uv = reinterpret_cast<const float4*>(vsrc + i2 * n) + b;
+      float2 x[2][6];
 #pragma unroll
-      for (int a = 0; a < 6; ++a) x[a] = cconjmul(__ldg(uv + 16 * a), __ldg(uc + 16 * a));
-      w16_line(x, cst);
+      for (int j = 0; j < 6; ++j) {
+        const float4 a = __ldg(uv + 8 * j), c = __ldg(uc + 8 * j);
+        x[0][j] = cconjmul(make_float2(a.x, a.y), make_float2(c.x, c.y));
+        x[1][j] = cconjmul(make_float2(a.z, a.w), make_float2(c.z, c.w));
+      }
+      w8_line(x, cst);
 #pragma unroll
-      for (int k0 = 0; k0 < 6; ++k0)
-        if (o3[k0] >= 0) X[i2 * ldx + o3[k0]] = x[k0];
+      for (int kc = 0; kc < 2; ++kc)
+#pragma unroll
+        for (int kj = 0; kj < 6; ++kj) {
+          int s = base3 + kj + 48 * kc;
+          s = s >= n ? s - n : s;
+          if (s < nk3) X[i2 * ldx + s] = x[kc][kj];
+        }
     }
     __syncthreads();
-    // stage 2: kept columns, a warp-uniform loop (a half-warp past nk3 transforms zeros)
-    for (int kb = warp * 2; kb < nk3; kb += LINES) {
-      const int k3 = kb + (lane >> 4);
+    // stage 2: kept columns, a warp-uniform loop (groups past nk3 transform zeros)
+    for (int kb0 = warp * 4; kb0 < nk3; kb0 += LINES) {
+      const int k3 = kb0 + (lane >> 3);
       const bool valid = k3 < nk3;
-      const float2* col = X + b * ldx + (valid ? k3 : 0);
-      float2 x[6];
+      const float2* col = X + 2 * b * ldx + (valid ? k3 : 0);
+      float2 x[2][6];
 #pragma unroll
-      for (int a = 0; a < 6; ++a) x[a] = col[16 * a * ldx];
-      w16_line(x, cst);
+      for (int j = 0; j < 6; ++j) {
+        x[0][j] = col[16 * j * ldx];
+        x[1][j] = col[(16 * j + 1) * ldx];
+      }
+      w8_line(x, cst);
       if (valid) {
 #pragma unroll
-        for (int k0 = 0; k0 < 6; ++k0)
-          if (o2[k0] >= 0) Y[o2[k0] * nk3 + k3] = x[k0];
+        for (int kc = 0; kc < 2; ++kc)
+#pragma unroll
+          for (int kj = 0; kj < 6; ++kj) {
+            int s = base2 + kj + 48 * kc;
+            s = s >= n ? s - n : s;
+            if (s < nk2) Y[s * nk3 + k3] = x[kc][kj];
+          }
       }
     }
     __syncthreads();
@@ -866,19 +906,19 @@ k_pair_planes_w16(const float2* __restrict__ psi_v, const int32_t* __restrict__ 
   }
 }
 
-cudaError_t launch_planes_w16(const chi0_plan_s* p, const SphereQ& s, const void* psi_v, const int32_t* v_idx,
-                              int v0, int nv, const void* psi_c, const int32_t* c_idx, int c0, int nc, void* D,
-                              cudaStream_t st) {
+cudaError_t launch_planes_w8(const chi0_plan_s* p, const SphereQ& s, const void* psi_v, const int32_t* v_idx,
+                             int v0, int nv, const void* psi_c, const int32_t* c_idx, int c0, int nc, void* D,
+                             cudaStream_t st) {
   constexpr int n = 96;
   const size_t sm = ((size_t)n * (s.nk3 | 1) + (size_t)s.nk2 * s.nk3) * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(k_pair_planes_w16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(k_pair_planes_w8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int cpc = 16;
   while (cpc > 1 && (int64_t)p->n1 * nv * ((nc + cpc - 1) / cpc) < 8 * 152) cpc >>= 1;
   // valence bands fastest: the CTAs running at a time share one plane's conduction rows in L2
   dim3 grid(nv, p->n1, (nc + cpc - 1) / cpc);
-  k_pair_planes_w16<<<grid, W16_WARPS * 32, sm, st>>>((const float2*)psi_v, v_idx, v0, nv, (const float2*)psi_c, c_idx,
-                                                      c0, nc, cpc, s.k2min, s.k3min, s.nk2, s.nk3, (float2*)D);
+  k_pair_planes_w8<<<grid, W8_WARPS * 32, sm, st>>>((const float2*)psi_v, v_idx, v0, nv, (const float2*)psi_c, c_idx,
+                                                    c0, nc, cpc, s.k2min, s.k3min, s.nk2, s.nk3, (float2*)D);
   return cudaGetLastError();
 }
 
@@ -979,7 +1019,7 @@ cudaError_t try_fft_planes(const chi0_plan_s* p, const SphereQ& s, const void* p
   const int nk = std::max(s.nk2, s.nk3);
   if (!(p->n1 == p->n2 && p->n2 == p->n3)) return cudaErrorNotSupported;
   if (p->n3 == 96 && nk <= WL_NKMAX)
-    return launch_planes_w16(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
+    return launch_planes_w8(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st);
   if (nk > NKMAX) return cudaErrorNotSupported;
 #define CHI0_FFT_CASE(P, Q, TV, NCB)                                                                    \
   if (nk <= 12) return launch_fft_planes<P, Q, 12, TV, NCB>(p, s, psi_v, v_idx, v0, nv, psi_c, c_idx, c0, nc, D, st); \
