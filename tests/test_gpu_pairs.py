@@ -35,16 +35,18 @@ def test_pairs_fp32_all_grids(name, nv, nc):
     assert err < 2e-6
 
 
-@pytest.mark.parametrize("lo", [(-14, -20, 3), (5, -30, -31), (-31, 4, -8)])
-def test_pairs_96_shifted_boxes(lo):
-    """The 96^3 pair stage (warp-cooperative 96-point lines) on G lists drawn
-    from boxes of extent 29 that start at other offsets than a centred sphere,
-    so the kept output ranges along i3 and i2 begin anywhere on the grid and wrap
-    past 96, against the oracle."""
+@pytest.mark.parametrize("lo,ext", [((-14, -20, 3), 29), ((5, -30, -31), 29), ((-31, 4, -8), 29),
+                                    ((-16, -9, -23), 32), ((-17, -17, 2), 34)])
+def test_pairs_96_shifted_boxes(lo, ext):
+    """The 96^3 pair stage (cooperative 96-point lines) on G lists drawn from
+    boxes that start at other offsets than a centred sphere, so the kept output
+    ranges along i3 and i2 begin anywhere on the grid and wrap past 96, against
+    the oracle: extent 29, 32 (the largest the line kernel takes) and 34 (the
+    direct row kernel)."""
     from paper_1601_06767_gb300 import Chi0Plan
     prob = make_problem("c5")
-    rng = np.random.default_rng(abs(sum(lo)) + 5)
-    axes = [np.arange(l, l + 29) for l in lo]
+    rng = np.random.default_rng(abs(sum(lo)) + 5 + ext)
+    axes = [np.arange(l, l + ext) for l in lo]
     box = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, 3)
     g = box[rng.choice(box.shape[0], 1500, replace=False)].astype(np.int32)
     cv, cc = prob.coeff_v(0, np.arange(2)), prob.coeff_c(np.arange(3))
@@ -56,7 +58,7 @@ def test_pairs_96_shifted_boxes(lo):
         M = M.cpu().numpy()
     err = rel_fro(M, ref)
     emax = np.max(np.abs(M - ref)) / np.max(np.abs(ref))
-    print(f"\n96^3 box from {lo}: rel err {err:.2e}, max abs err / max |M| {emax:.2e}")
+    print(f"\n96^3 box from {lo}, extent {ext}: rel err {err:.2e}, max abs err / max |M| {emax:.2e}")
     assert err < 2e-6 and emax < 2e-6
 
 
