@@ -75,7 +75,11 @@ typedef struct {
                                 products t0t0+t0t1+t1t0; 4 = two terms, adds t1t1; 6 = three terms
                                 t0+t1+t2, products t_i t_j with i+j <= 2.  0 = 6 for BF16 (three
                                 BF16 terms carry 24 bits), 3 for FP16; ignored for FP64 */
-  int64_t max_pairs;         /* pairs per internal block of chi0_build / chi0_accumulate; 0 = default */
+  int64_t max_pairs;         /* pairs per internal block of chi0_build / chi0_accumulate; 0 = default
+                                (8192 for split precisions).  Split plans add each launch's FP32
+                                chain sums into chi0 once, so longer launches carry more FP32
+                                rounding: at 16384 pairs per launch max|d chi0| / max|chi0| reaches
+                                about 1.3e-6 (relative Frobenius error 4e-7), against 8.7e-7 at 8192 */
   int chain_pairs;           /* pairs accumulated in tensor memory before they are added into FP32
                                 registers (multiple of 32).  The tensor cores round each MMA result
                                 toward zero, so the bias grows with this length; 0 = 32 (default) */

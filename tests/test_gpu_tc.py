@@ -146,6 +146,34 @@ def test_tc_edge_shapes(nG, nv, nc, pair, monkeypatch):
         check_chi(chi, ref, TOL, label=f"edge {prec} herm={herm} nG={nG} {nv}x{nc}")
 
 
+@pytest.mark.parametrize("K", [16384, 16896])
+def test_hermitian_one_product_launch_length(K):
+    """A one-product H2 part is one accumulation chain over the launch's pairs,
+    added together with H1 (the fused epilogue), while the launch has at most
+    16384 pairs (512 stages); past that its chains are 256 pairs long and the
+    parts are added one after the other.  One launch at the limit and one just
+    past it, neighbouring conduction energies (one product), against the
+    oracle.  The Frobenius bar is the usual one; element-wise, launches this long
+    carry the FP32 rounding of sums over 512 chains on top of the chains'
+    round-toward-zero bias (about 4.5e-7 of the diagonal for 32-pair chains), so
+    the bar for max|d chi| / max|chi| is 2e-6 here (1e-6 holds for the default
+    launches of 8192 pairs)."""
+    prob = make_problem("c1", n_G=[203], n_imag=3)
+    rng = np.random.default_rng(K)
+    nv, nG = 16, 203
+    nc = K // nv
+    Ev = np.linspace(-0.05, 0.0, nv)
+    Ec = np.linspace(1.0, 1.02, nc)
+    M = (rng.standard_normal((K, nG)) + 1j * rng.standard_normal((K, nG))) * 0.03
+    dE = (Ev[:, None] - Ec[None, :]).reshape(-1)
+    ref = chi0_from_pairs(M, freq_factor(dE, np.ones_like(dE), prob.omega, prob.delta))
+    with _plan(prob, precision="fp16", max_pairs=K, hermitian=True) as plan:
+        chi = plan.accumulate(0, _dev(M.astype(np.complex64)), nv, nc, _dev(Ev), _dev(Ec))
+        plan.sync_status()
+        chi = chi.cpu().numpy()
+    check_chi(chi, ref, TOL, elem_tol=2e-6, label=f"one-product H2, {K} pairs in one launch")
+
+
 def test_hermitian_automatic_choice():
     """hermitian = automatic: the mode with fewer estimated waves of work items
     over the SMs (T = ceil(N_G / 128): n_freq T^2 items in plain mode, n_freq
