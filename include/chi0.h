@@ -77,12 +77,13 @@ typedef struct {
                                 BF16 terms carry 24 bits), 3 for FP16; ignored for FP64 */
   int64_t max_pairs;         /* pairs per internal block of chi0_build / chi0_accumulate; 0 = default
                                 (8192 for split precisions).  Split plans add each launch's FP32
-                                chain sums into chi0 once, so longer launches carry more FP32
-                                rounding: at 16384 pairs per launch max|d chi0| / max|chi0| reaches
-                                about 1.3e-6 (relative Frobenius error 4e-7), against 8.7e-7 at 8192 */
+                                chain sums into chi0 once; the diagonal sum_p f_p |M_p(G)|^2 (terms
+                                of one phase) is summed apart on the CUDA cores, so the launch length
+                                barely shows: max|d chi0| / max|chi0| 2-3e-8 at 8192 and at 16384 */
   int chain_pairs;           /* pairs accumulated in tensor memory before they are added into FP32
                                 registers (multiple of 32).  The tensor cores round each MMA result
-                                toward zero, so the bias grows with this length; 0 = 32 (default) */
+                                toward zero, which shrinks each chain's sum by about 1.4e-8 per pair
+                                of chain length (the diagonal excepted); 0 = 32 (default) */
   int hermitian;             /* split precisions: contract chi0 = (1 + i t) H1 + i H2 with the Hermitian
                                 parts H1 = sum Re(f_p) M_p M_p^H and H2 = sum g_p M_p M_p^H,
                                 g_p = Im f_p - t Re f_p (f_p the factor of Eq. 1), only tiles on or above

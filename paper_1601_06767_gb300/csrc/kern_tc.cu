@@ -221,15 +221,21 @@ __global__ void k_scales(const unsigned int* __restrict__ amax, const unsigned i
   }
 }
 
-// tile of 64 pairs x 32 sphere points, transposed through shared memory
+// tile of 64 pairs x 32 sphere points, transposed through shared memory.
+// Also the diagonal of the block's sum, diag[w][G] += sum_p f_p(w) |M_p(G)|^2 over
+// the tile's pairs (FP32 over 64 pairs, added to FP64): all its terms have the
+// phase of f, so the tensor cores' round-toward-zero would add up along the
+// whole block there, while the CUDA cores round to nearest.
 template <bool BF16, int NT>
 __global__ void __launch_bounds__(256)
 k_pack(const float2* __restrict__ M, int nG, int64_t K, int nGp, int Kp, const double2* __restrict__ f,
        int n_freq, int herm, const float* __restrict__ scale, const int* __restrict__ h2np,
-       const double* __restrict__ tbar, uint32_t* __restrict__ Bp, uint32_t* __restrict__ Ap) {
+       const double* __restrict__ tbar, uint32_t* __restrict__ Bp, uint32_t* __restrict__ Ap,
+       double2* __restrict__ diag) {
   extern __shared__ __align__(16) unsigned char smem_pack[];
   float2* tile = reinterpret_cast<float2*>(smem_pack);          // [64][33]
   float2* fs = tile + 64 * 33;                                 // [n_freq][64]
+  float2* fo = fs + 64 * n_freq;                               // [n_freq][64] f itself (FP32)
   const int G0 = blockIdx.x * 32;
   const int64_t p0 = (int64_t)blockIdx.y * 64;
   const float sM = scale[0];
@@ -243,18 +249,36 @@ k_pack(const float2* __restrict__ M, int nG, int64_t K, int nGp, int Kp, const d
   for (int e = threadIdx.x; e < n_freq * 64; e += blockDim.x) {
     const int iw = e >> 6, pp = e & 63;
     const int64_t p = p0 + pp;
-    float2 v = make_float2(0.f, 0.f);
+    float2 v = make_float2(0.f, 0.f), v0 = v;
     if (p < K) {
       const double2 d = f[(int64_t)iw * K + p];
       const float sW = scale[1 + iw], sW2 = herm ? scale[1 + n_freq + iw] : sW;
       // Hermitian mode: the W2 weight is g = Im f - t Re f (in FP64, the t of the merge)
       const double im = herm ? d.y - tbar[iw] * d.x : d.y;
       v = make_float2((float)d.x * sW, (float)im * sW2);
+      v0 = make_float2((float)d.x, (float)d.y);
     }
     fs[e] = v;
+    fo[e] = v0;
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (G0 + lane < nG) {
+    for (int iw = warp; iw < n_freq; iw += 8) {
+      float sr[4] = {0.f, 0.f, 0.f, 0.f}, si[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+      for (int pp = 0; pp < 64; ++pp) {
+        const float2 m = tile[pp * 33 + lane];
+        const float a = fmaf(m.x, m.x, m.y * m.y);
+        const float2 fw = fo[iw * 64 + pp];
+        sr[pp & 3] = fmaf(fw.x, a, sr[pp & 3]);
+        si[pp & 3] = fmaf(fw.y, a, si[pp & 3]);
+      }
+      double2* d = diag + (size_t)iw * nGp + G0 + lane;
+      atomicAdd(&d->x, (double)((sr[0] + sr[1]) + (sr[2] + sr[3])));
+      atomicAdd(&d->y, (double)((si[0] + si[1]) + (si[2] + si[3])));
+    }
+  }
   const size_t plane = (size_t)nGp * (Kp / 2);                 // uint32 words per plane
   const int64_t kw = p0 / 2 + lane;                            // word index along K
   for (int g = warp; g < 32; g += 8) {
@@ -452,6 +476,7 @@ struct TcBatch {
   const double* inv[MAXQ];   // [n_parts * n_freq] inverse operand scales
   const int* h2np[MAXQ];     // Hermitian mode: [n_freq] product count of the W2 part (+16 if small)
   const double* tbar[MAXQ];  // Hermitian mode: [n_freq] ratio t of chi0 = (1 + i t) H1 + i H2
+  const double2* diag[MAXQ]; // [n_freq][tiles_n * BN] diagonal of chi0's block sum, from the pack
   int nG[MAXQ];
   int tiles_m[MAXQ];         // tiles along G (rows of chi0)
   int tiles_n[MAXQ];         // tiles along G' (columns)
@@ -567,20 +592,31 @@ __device__ __forceinline__ void red_add_pow2(double* a, float v, int k) {
   atomicAdd(a, f64_of_f32_pow2(v, k));
 }
 
+// chi0[G][G] += the pack's diagonal sum when the row piece Hb..Hb+63 holds column G
+__device__ __forceinline__ void add_diag(double2* __restrict__ chi_w, int nG, int G, int Hb,
+                                         const double2* __restrict__ dg) {
+  if ((unsigned)(G - Hb) < 64u) {
+    const double2 d = dg[G];
+    atomicAdd(&chi_w[(size_t)G * nG + G].x, d.x);
+    atomicAdd(&chi_w[(size_t)G * nG + G].y, d.y);
+  }
+}
+
 // Add one drained part of a tile row (row G, columns Hb..Hb+63; FP32 sums whose
 // scale is 2^-k) into chi0 of one frequency.  Plain mode: chi[G][H] += 2^k (re +
 // i im).  Hermitian mode: part 0 holds H1(G, H), part 1 holds H2(G, H); chi[G][H]
-// += (1 + i t) H1 + i H2 for G <= H and chi[H][G] += (1 + i t) conj(H1) + i
-// conj(H2) for G < H.  Each (1 + i t) product is one FP32 fused multiply-add (one
-// rounding; t is an FP32 number), the power of two and the widening to FP64 are
-// exact, and the FP64 sums are reductions: the epilogue issues no FP64 arithmetic.
+// += (1 + i t) H1 + i H2 and chi[H][G] += (1 + i t) conj(H1) + i conj(H2) for G
+// < H.  Each (1 + i t) product is one FP32 fused multiply-add (one rounding; t
+// is an FP32 number), the power of two and the widening to FP64 are exact, and
+// the FP64 sums are reductions: the epilogue issues no FP64 arithmetic.  The
+// diagonal element is left out: it takes the pack's sum (add_diag).
 __device__ __forceinline__ void merge_row(double2* __restrict__ chi_w, int nG, int G, int Hb, const float (&sre)[64],
                                           const float (&sim)[64], int k, bool herm, int part, float t) {
   double2* row = chi_w + (size_t)G * nG;
   if (!herm) {
 #pragma unroll
     for (int i = 0; i < 64; ++i) {
-      if (Hb + i < nG) {
+      if (Hb + i < nG && Hb + i != G) {
         red_add_pow2(&row[Hb + i].x, sre[i], k);
         red_add_pow2(&row[Hb + i].y, sim[i], k);
       }
@@ -590,23 +626,19 @@ __device__ __forceinline__ void merge_row(double2* __restrict__ chi_w, int nG, i
 #pragma unroll
   for (int i = 0; i < 64; ++i) {
     const int H = Hb + i;
-    if (H < nG && G <= H) {
+    if (H < nG && G < H) {
       const float a = sre[i], b = sim[i];
       double2* m = chi_w + (size_t)H * nG + G;
       if (part == 0) {
         red_add_pow2(&row[H].x, fmaf(-t, b, a), k);
         red_add_pow2(&row[H].y, fmaf(t, a, b), k);
-        if (G < H) {
-          red_add_pow2(&m->x, fmaf(t, b, a), k);
-          red_add_pow2(&m->y, fmaf(t, a, -b), k);
-        }
+        red_add_pow2(&m->x, fmaf(t, b, a), k);
+        red_add_pow2(&m->y, fmaf(t, a, -b), k);
       } else {
         red_add_pow2(&row[H].x, -b, k);
         red_add_pow2(&row[H].y, a, k);
-        if (G < H) {
-          red_add_pow2(&m->x, b, k);
-          red_add_pow2(&m->y, a, k);
-        }
+        red_add_pow2(&m->x, b, k);
+        red_add_pow2(&m->y, a, k);
       }
     }
   }
@@ -618,8 +650,9 @@ __device__ __forceinline__ int exponent_of_pow2(double x) {
 }
 
 // Hermitian mode with a one-product W2 part: add both parts of a tile row at once,
-// chi[G][H] += (1 + i t) H1 + i H2 for G <= H and chi[H][G] += (1 + i t) conj(H1) +
-// i conj(H2) for G < H, both read from tensor memory 16 columns at a time: the W1
+// chi[G][H] += (1 + i t) H1 + i H2 and chi[H][G] += (1 + i t) conj(H1) + i
+// conj(H2) for G < H (the diagonal takes the pack's sum), both read from
+// tensor memory 16 columns at a time: the W1
 // sums (scale 2^-k1) at column address ta1 (Re) and ta1 + 128 (Im), the W2
 // accumulator at ta2, scaled to the W1 units by 2^(k2 - k1) (exact; a ratio
 // outside the FP32 exponent range drops H2: below 2^-126 it is negligible, above
@@ -645,15 +678,13 @@ __device__ __forceinline__ void merge_row_fused(double2* __restrict__ chi_w, int
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const int H = Hb + j + i;
-      if (in && H < nG && G <= H) {
+      if (in && H < nG && G < H) {
         const float a1 = re1[i], b1 = im1[i], a2 = re2[i] * r21, b2 = im2[i] * r21;
+        double2* m = chi_w + (size_t)H * nG + G;
         red_add_pow2(&row[H].x, fmaf(-t, b1, a1) - b2, k1);
         red_add_pow2(&row[H].y, fmaf(t, a1, b1) + a2, k1);
-        if (G < H) {
-          double2* m = chi_w + (size_t)H * nG + G;
-          red_add_pow2(&m->x, fmaf(t, b1, a1) + b2, k1);
-          red_add_pow2(&m->y, fmaf(t, a1, -b1) + a2, k1);
-        }
+        red_add_pow2(&m->x, fmaf(t, b1, a1) + b2, k1);
+        red_add_pow2(&m->y, fmaf(t, a1, -b1) + a2, k1);
       }
     }
   }
@@ -745,6 +776,7 @@ __device__ __forceinline__ bool epilogue_item(const TcBatch& P, BarT* bar, uint3
       const uint32_t tq = tbase + ((uint32_t)(quad * 32) << 16) + half * 64;
       merge_row_fused(chi_w, nG, G, tn * BN + half * 64, tq + b1 * 256, tq + b2 * 256, k,
                       exponent_of_pow2(P.inv[q][P.n_freq + iw]), t, G < nG);
+      if (G < nG) add_diag(chi_w, nG, G, tn * BN + half * 64, P.diag[q] + (size_t)iw * P.tiles_n[q] * BN);
       tc::fence_before();
       __syncwarp();
       if (lane == 0) {
@@ -759,7 +791,10 @@ __device__ __forceinline__ bool epilogue_item(const TcBatch& P, BarT* bar, uint3
       ++gc;
       return true;
     }
-    if (G < nG) merge_row(chi_w, nG, G, tn * BN + half * 64, sre, sim, k, herm, part, t);
+    if (G < nG) {
+      merge_row(chi_w, nG, G, tn * BN + half * 64, sre, sim, k, herm, part, t);
+      if (part == 0) add_diag(chi_w, nG, G, tn * BN + half * 64, P.diag[q] + (size_t)iw * P.tiles_n[q] * BN);
+    }
   }
   return true;
 }
@@ -1197,18 +1232,20 @@ size_t planes_bytes(const chi0_plan_s* p) {
   return ((size_t)b_planes(p) + 2 * (size_t)n_terms(p) * n_parts(p) * p->n_freq) * nGp * Kp * 2;
 }
 
+// amax, ratio range, scales, inverse scales, W2 products, ratios t
+static size_t scal_bytes(const chi0_plan_s* p) { return (256 + 64 * (size_t)(p->n_freq + 1) + 255) / 256 * 256; }
+
 size_t tc_pack_bytes(const chi0_plan_s* p, int64_t max_pairs, int max_nG) {
   const size_t nGp = (size_t)round_up_i(max_nG, 2 * BM);
   const size_t Kp = (size_t)((max_pairs + 63) / 64 * 64);
   const size_t planes = (size_t)b_planes(p) + 2 * (size_t)n_terms(p) * n_parts(p) * p->n_freq;
-  // amax, ratio range, scales, inverse scales, W2 products, ratios t
-  const size_t scal = 256 + 64 * (size_t)(p->n_freq + 1);
-  return planes * nGp * Kp * 2 + scal;
+  // then the diagonal sums [n_freq][nGp]
+  return planes * nGp * Kp * 2 + scal_bytes(p) + (size_t)p->n_freq * nGp * sizeof(double2);
 }
 
 // workspace of one q-point's split planes: B, A, then amax / ratio range /
 // scales / inverse scales / W2 product counts / ratios t (each part sized for
-// two values per frequency)
+// two values per frequency), then the diagonal sums [n_freq][nGp]
 struct PackWs {
   uint16_t* Bp;
   uint16_t* Ap;
@@ -1218,6 +1255,7 @@ struct PackWs {
   double* inv;
   int* h2np;
   double* tbar;
+  double2* diag;
 };
 
 static cudaError_t fill_ratio_min(unsigned int* tr, int n_freq, cudaStream_t s) {
@@ -1237,6 +1275,7 @@ static PackWs pack_ws(const chi0_plan_s* p, void* base, int nGp, int Kp) {
   w.inv = reinterpret_cast<double*>(tail + 24 * nf1);         // 2 n_freq doubles
   w.h2np = reinterpret_cast<int*>(tail + 40 * nf1);           // n_freq ints
   w.tbar = reinterpret_cast<double*>(tail + 48 * nf1);        // n_freq doubles
+  w.diag = reinterpret_cast<double2*>(tail + scal_bytes(p));  // n_freq x nGp
   return w;
 }
 
@@ -1255,12 +1294,14 @@ static cudaError_t pack_one(chi0_plan_s* p, int nG, const float2* M, int64_t K, 
   k_absmax<<<2 * 152, 256, 0, s>>>(M, K * nG, f, K, p->n_freq, w.amax, p->tc_herm ? w.tr : nullptr);
   k_scales<<<1, 128, 0, s>>>(w.amax, w.tr, p->n_freq, p->tc_herm ? 1 : 0, p->n_products, BF16 ? 1 : 0, w.scale,
                              w.inv, w.h2np, w.tbar);
+  e = cudaMemsetAsync(w.diag, 0, sizeof(double2) * p->n_freq * nGp, s);
+  if (e != cudaSuccess) return e;
   dim3 gpk(nGp / 32, Kp / 64);
-  const size_t smp = (size_t)(64 * 33 + 64 * p->n_freq) * sizeof(float2);
+  const size_t smp = (size_t)(64 * 33 + 2 * 64 * p->n_freq) * sizeof(float2);
   e = cudaFuncSetAttribute(k_pack<BF16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
   if (e != cudaSuccess) return e;
   k_pack<BF16, NT><<<gpk, 256, smp, s>>>(M, nG, K, nGp, Kp, f, p->n_freq, p->tc_herm ? 1 : 0, w.scale, w.h2np,
-                                         w.tbar, (uint32_t*)w.Bp, (uint32_t*)w.Ap);
+                                         w.tbar, (uint32_t*)w.Bp, (uint32_t*)w.Ap, w.diag);
   return cudaGetLastError();
 }
 
@@ -1311,6 +1352,7 @@ static cudaError_t run_tc(chi0_plan_s* p, const TcJob* jobs, int n_jobs, int64_t
     P->inv[j] = w.inv;
     P->h2np[j] = w.h2np;
     P->tbar[j] = w.tbar;
+    P->diag[j] = w.diag;
     P->nG[j] = jb.nG;
     const int TM = nGp / (pair ? 2 * BM : BM), TN = nGp / BN;
     P->tiles_m[j] = TM;
