@@ -9,13 +9,13 @@ arithmetic).
 Functions without an independent pin say "parity unpinned" in their
 docstring; every other function is pinned by ``tests/test_oracle_*.py``.
 """
-from .chi0_oracle import (wfn_to_grid, pair_elements, freq_factor, chi0_from_pairs,
+from .chi0_oracle import (wfn_to_grid, pair_elements, freq_factor, chi0_from_pairs, chi0_rows,
                           dos, select_accelerated, accelerated_pairs, chi0_full,
                           chi0_accelerated, full_pairs, chi0_grad, loss_diag,
                           rel_fro, chi0_k_points, grid_energy_of_bands,
                           energy_substitution_estimate)
 
-__all__ = ["wfn_to_grid", "pair_elements", "freq_factor", "chi0_from_pairs", "dos",
+__all__ = ["wfn_to_grid", "pair_elements", "freq_factor", "chi0_from_pairs", "chi0_rows", "dos",
            "select_accelerated", "accelerated_pairs", "chi0_full", "chi0_accelerated",
            "full_pairs", "chi0_grad", "loss_diag", "rel_fro", "chi0_k_points",
            "grid_energy_of_bands", "energy_substitution_estimate"]

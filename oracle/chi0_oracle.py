@@ -100,6 +100,26 @@ def chi0_from_pairs(M: np.ndarray, f: np.ndarray, block: int = 4096) -> np.ndarr
     return chi
 
 
+def chi0_rows(M: np.ndarray, f: np.ndarray, rows, block: int = 4096) -> np.ndarray:
+    """Rows G in `rows` of Eq. 1: chi0_{G,G'}(omega) = sum_p f_p(omega) M_p(G)
+    conj(M_p(G')) for every G' -> [n_freq][len(rows)][N_G], in FP64.
+
+    For checking chi0 of sizes whose full matrix the host cannot form in
+    reasonable time; summed over pair blocks of at most `block` pairs.
+    """
+    M = np.asarray(M)
+    f = np.atleast_2d(np.asarray(f, dtype=np.complex128))
+    rows = np.asarray(rows, dtype=np.int64)
+    out = np.zeros((f.shape[0], rows.size, M.shape[1]), dtype=np.complex128)
+    for p0 in range(0, M.shape[0], block):
+        Mb = np.asarray(M[p0:p0 + block], dtype=np.complex128)
+        Mc = Mb.conj()
+        Mr = Mb[:, rows].T
+        for iw in range(f.shape[0]):
+            out[iw] += (Mr * f[iw, p0:p0 + block][None, :]) @ Mc
+    return out
+
+
 # --------------------------------------------------------------------------
 # Eq. 3 / Eq. 4: accelerated conduction-band summation
 # --------------------------------------------------------------------------

@@ -4,7 +4,7 @@ definiteness properties that Eq. 1 fixes."""
 import numpy as np
 import pytest
 
-from oracle import chi0_from_pairs, freq_factor, rel_fro
+from oracle import chi0_from_pairs, chi0_rows, freq_factor, rel_fro
 
 
 def _rand_M(n_p, n_g, seed=0):
@@ -52,6 +52,27 @@ def test_chi0_matches_direct_loop():
                 for b in range(ng):
                     ref[iw, a, b] += f[iw, p] * M[p, a] * np.conj(M[p, b])
     assert rel_fro(chi, ref) < 1e-14
+
+
+def test_chi0_rows_match_direct_loop():
+    """Rows of Eq. 1 against the quadruple loop, with pair blocks that split
+    the sum unevenly and rows given out of order (one repeated)."""
+    n_p, ng = 13, 7
+    M = _rand_M(n_p, ng, 11)
+    dE = _energies(n_p, 12)
+    f = freq_factor(dE, np.ones_like(dE), np.array([0.0, 0.3j, 0.1]), 1e-3)
+    rows = np.array([6, 0, 3, 3])
+    got = chi0_rows(M, f, rows, block=5)
+    ref = np.zeros((3, rows.size, ng), dtype=np.complex128)
+    for iw in range(3):
+        for i, a in enumerate(rows):
+            for p in range(n_p):
+                for b in range(ng):
+                    ref[iw, i, b] += f[iw, p] * M[p, a] * np.conj(M[p, b])
+    assert np.max(np.abs(got - ref)) < 1e-14 * np.max(np.abs(ref))
+    # complex64 input is widened exactly: the same rows as its complex128 copy
+    M32 = M.astype(np.complex64)
+    assert np.array_equal(chi0_rows(M32, f, rows), chi0_rows(M32.astype(np.complex128), f, rows))
 
 
 def test_rank_one_single_pair():
