@@ -68,7 +68,9 @@ static_assert(EPI_WARP0 * 32 * REG_LOW + EPI_WARPS * 32 * REG_HIGH <= THREADS * 
 static_assert(THREADS * REG_LAUNCH <= 65536 && REG_LAUNCH * THREADS / 4 <= 16384 * 4, "launch registers");
 constexpr int TMEM_COLS = 512;                     // 2 buffers x (Re, Im) x 128 columns
 constexpr uint64_t WAIT_BUDGET_NS = 2000000000ull; // 2 s per wait
-constexpr size_t SMEM_BYTES = (size_t)RING_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int BAR_BYTES = 256;                     // barriers and the tensor-memory base
+constexpr int XBUF_FLOATS = 32 * 8;                // per epilogue warp: the transpose of red_block
+constexpr size_t SMEM_BYTES = (size_t)RING_BYTES + 1024 /*align*/ + BAR_BYTES + EPI_WARPS * XBUF_FLOATS * 4;
 constexpr int MAX_STAGES = 3;
 
 template <int NT> struct Ring {
@@ -356,6 +358,8 @@ struct Barriers {
   uint64_t done;
   uint32_t tmem_base;
 };
+static_assert(sizeof(Barriers) <= BAR_BYTES, "barriers overlap the transpose buffers");
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory above the per-block limit");
 
 // Issue the MMAs of one stage (BK pairs) into the (Re, Im) accumulator pair.
 // The tensor cores round the FP32 accumulator toward zero after every MMA, so
@@ -602,6 +606,33 @@ __device__ __forceinline__ void add_diag(double2* __restrict__ chi_w, int nG, in
   }
 }
 
+// Add a 32-row x 4-column block of complex values into chi0 by coalesced
+// reductions.  The calling lane holds row G0 + lane: v = {re, im} of columns
+// H0..H0+3.  The block passes through the warp's 32 x 8 shared-memory buffer xb
+// (each row's floats XOR-swizzled by (row / 4) mod 8, so that neither the row
+// writes nor the column reads meet a bank conflict), after which one
+// reduction instruction covers 4 rows x 64 contiguous bytes instead of 32 rows
+// of 8 bytes each.  An element (G, H) is added when G, H < nG and G < H
+// (upper) or G != H (the diagonal takes the pack's sum).  Warp-collective.
+__device__ __forceinline__ void red_block(double2* __restrict__ chi_w, int nG, int G0, int H0, const float (&v)[8],
+                                          float* __restrict__ xb, int lane, int k, bool upper) {
+  const int sw = (lane >> 2) & 7;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) xb[lane * 8 + (e ^ sw)] = v[e];
+  __syncwarp();
+  const int e = lane & 7;                        // column e / 2, real (e even) or imaginary part
+  const int H = H0 + (e >> 1);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int r = 4 * j + (lane >> 3);           // row r was written by lane r, swizzled by j
+    const float x = xb[r * 8 + (e ^ j)];
+    const int G = G0 + r;
+    if (H < nG && G < nG && (upper ? G < H : G != H))
+      red_add_pow2(reinterpret_cast<double*>(chi_w + (size_t)G * nG + H) + (e & 1), x, k);
+  }
+  __syncwarp();
+}
+
 // Add one drained part of a tile row (row G, columns Hb..Hb+63; FP32 sums whose
 // scale is 2^-k) into chi0 of one frequency.  Plain mode: chi[G][H] += 2^k (re +
 // i im).  Hermitian mode: part 0 holds H1(G, H), part 1 holds H2(G, H); chi[G][H]
@@ -609,7 +640,11 @@ __device__ __forceinline__ void add_diag(double2* __restrict__ chi_w, int nG, in
 // < H.  Each (1 + i t) product is one FP32 fused multiply-add (one rounding; t
 // is an FP32 number), the power of two and the widening to FP64 are exact, and
 // the FP64 sums are reductions: the epilogue issues no FP64 arithmetic.  The
-// diagonal element is left out: it takes the pack's sum (add_diag).
+// diagonal element is left out: it takes the pack's sum (add_diag).  The
+// lanes' reductions into chi[G][H] fall on 32 rows each; this merge runs while
+// the next chains accumulate (the part's buffers are released), and going
+// through red_block lengthened it past that overlap (a 64-atom BF16 launch took
+// 11.66 ms with it, 10.8 ms without).
 __device__ __forceinline__ void merge_row(double2* __restrict__ chi_w, int nG, int G, int Hb, const float (&sre)[64],
                                           const float (&sim)[64], int k, bool herm, int part, float t) {
   double2* row = chi_w + (size_t)G * nG;
@@ -652,17 +687,20 @@ __device__ __forceinline__ int exponent_of_pow2(double x) {
 // Hermitian mode with a one-product W2 part: add both parts of a tile row at once,
 // chi[G][H] += (1 + i t) H1 + i H2 and chi[H][G] += (1 + i t) conj(H1) + i
 // conj(H2) for G < H (the diagonal takes the pack's sum), both read from
-// tensor memory 16 columns at a time: the W1
-// sums (scale 2^-k1) at column address ta1 (Re) and ta1 + 128 (Im), the W2
-// accumulator at ta2, scaled to the W1 units by 2^(k2 - k1) (exact; a ratio
-// outside the FP32 exponent range drops H2: below 2^-126 it is negligible, above
-// 2^127 the W2 weights were zero).  Every lane of the warp runs the loads; `in`
-// masks the row.
+// tensor memory 16 columns at a time: the W1 sums (scale 2^-k1) at column
+// address ta1 (Re) and ta1 + 128 (Im), the W2 accumulator at ta2, scaled to the
+// W1 units by 2^(k2 - k1) (exact; a ratio outside the FP32 exponent range drops
+// H2: below 2^-126 it is negligible, above 2^127 the W2 weights were zero).
+// Both tensor-memory buffers stay held while this runs, so the MMAs wait for it:
+// the elements (G, H) go through red_block (coalesced), the mirrored ones (H, G)
+// directly (consecutive lanes, consecutive addresses).  Warp-collective (the
+// loads and red_block): every lane calls it, rows G >= nG add nothing.
 __device__ __forceinline__ void merge_row_fused(double2* __restrict__ chi_w, int nG, int G, int Hb, uint32_t ta1,
-                                                uint32_t ta2, int k1, int k2, float t, bool in) {
-  double2* row = chi_w + (size_t)G * nG;
+                                                uint32_t ta2, int k1, int k2, float t, float* __restrict__ xb,
+                                                int lane) {
   const int d = k2 - k1;
   const float r21 = d >= -126 && d <= 127 ? __int_as_float((d + 127) << 23) : 0.f;
+  const bool in = G < nG;
 #pragma unroll 1
   for (int j = 0; j < 64; j += 16) {
     float re1[16], im1[16], re2[16], im2[16];
@@ -676,13 +714,22 @@ __device__ __forceinline__ void merge_row_fused(double2* __restrict__ chi_w, int
     tc::reg_after_wait(re2);
     tc::reg_after_wait(im2);
 #pragma unroll
+    for (int c = 0; c < 16; c += 4) {
+      float v[8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float a1 = re1[c + i], b1 = im1[c + i], a2 = re2[c + i] * r21, b2 = im2[c + i] * r21;
+        v[2 * i] = fmaf(-t, b1, a1) - b2;
+        v[2 * i + 1] = fmaf(t, a1, b1) + a2;
+      }
+      red_block(chi_w, nG, G - lane, Hb + j + c, v, xb, lane, k1, true);
+    }
+#pragma unroll
     for (int i = 0; i < 16; ++i) {
       const int H = Hb + j + i;
       if (in && H < nG && G < H) {
         const float a1 = re1[i], b1 = im1[i], a2 = re2[i] * r21, b2 = im2[i] * r21;
         double2* m = chi_w + (size_t)H * nG + G;
-        red_add_pow2(&row[H].x, fmaf(-t, b1, a1) - b2, k1);
-        red_add_pow2(&row[H].y, fmaf(t, a1, b1) + a2, k1);
         red_add_pow2(&m->x, fmaf(t, b1, a1) + b2, k1);
         red_add_pow2(&m->y, fmaf(t, a1, -b1) + a2, k1);
       }
@@ -754,7 +801,8 @@ __device__ __forceinline__ bool drain_part(BarT* bar, uint32_t tbase, int quad, 
 // Returns false when a bounded wait ran out.
 template <int NT, bool PAIR, class BarT>
 __device__ __forceinline__ bool epilogue_item(const TcBatch& P, BarT* bar, uint32_t tbase, int quad, int half,
-                                              int lane, int q, int iw, int G, int tn, int64_t& gc, int* status) {
+                                              int lane, int q, int iw, int G, int tn, int64_t& gc, int* status,
+                                              float* xb) {
   // (everything else is read from the launch parameters after the drain, where the
   // sums no longer fill the registers)
   const bool fused = h2_fused(P, q, iw);
@@ -775,7 +823,7 @@ __device__ __forceinline__ bool epilogue_item(const TcBatch& P, BarT* bar, uint3
       tc::fence_after();
       const uint32_t tq = tbase + ((uint32_t)(quad * 32) << 16) + half * 64;
       merge_row_fused(chi_w, nG, G, tn * BN + half * 64, tq + b1 * 256, tq + b2 * 256, k,
-                      exponent_of_pow2(P.inv[q][P.n_freq + iw]), t, G < nG);
+                      exponent_of_pow2(P.inv[q][P.n_freq + iw]), t, xb, lane);
       if (G < nG) add_diag(chi_w, nG, G, tn * BN + half * 64, P.diag[q] + (size_t)iw * P.tiles_n[q] * BN);
       tc::fence_before();
       __syncwarp();
@@ -944,12 +992,13 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
     // ---------------- epilogue: drain chains, then FP64 reductions per item ----------------
     const int ew = warp - EPI_WARP0, quad = warp & 3, half = ew >> 2;
     const int row = quad * 32 + lane;
+    float* xb = reinterpret_cast<float*>(tiles + RING_BYTES + BAR_BYTES) + ew * XBUF_FLOATS;
     int64_t gc = 0;
     bool ok = true;
     for (int64_t item = blockIdx.x; item < P.total_items && ok; item += gridDim.x) {
       int q, iw, tm, tn;
       decode_item(P, item, q, iw, tm, tn);
-      ok = epilogue_item<NT, false>(P, bar, tbase, quad, half, lane, q, iw, tm * BM + row, tn, gc, status);
+      ok = epilogue_item<NT, false>(P, bar, tbase, quad, half, lane, q, iw, tm * BM + row, tn, gc, status, xb);
     }
   }
   tc::fence_before();
@@ -968,7 +1017,8 @@ k_contract_tc(const __grid_constant__ TcBatch P, int* __restrict__ status) {
 // release the accumulators on the first CTA's "tempty" barriers.
 // ---------------------------------------------------------------------------
 constexpr int RING2_BYTES = 216 * 1024;
-constexpr size_t SMEM2_BYTES = (size_t)RING2_BYTES + 1024 + 256;
+constexpr size_t SMEM2_BYTES = (size_t)RING2_BYTES + 1024 + BAR_BYTES + EPI_WARPS * XBUF_FLOATS * 4;
+static_assert(SMEM2_BYTES <= 227 * 1024, "CTA-pair shared memory above the per-block limit");
 
 template <int NT> struct Ring2 {
   static constexpr int PLANES = 2 * NT;
@@ -991,6 +1041,7 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
     uint64_t full[4], empty[4], tfull[2], tempty[2], done;
     uint32_t tmem_base;
   };
+  static_assert(sizeof(Bars) <= BAR_BYTES, "barriers overlap the transpose buffers");
   Bars* bar = reinterpret_cast<Bars*>(tiles + RING2_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = tc::cluster_rank();
@@ -1133,12 +1184,14 @@ k_contract_tc2(const __grid_constant__ TcBatch P, int* __restrict__ status) {
     // ---------------- epilogue (both CTAs, own 128 rows) ----------------
     const int ew = warp - EPI_WARP0, quad = warp & 3, half = ew >> 2;
     const int row = quad * 32 + lane;
+    float* xb = reinterpret_cast<float*>(tiles + RING2_BYTES + BAR_BYTES) + ew * XBUF_FLOATS;
     int64_t gc = 0;
     bool ok = true;
     for (int64_t item = pair; item < P.total_items && ok; item += npairs) {
       int q, iw, tm, tn;
       decode_item(P, item, q, iw, tm, tn);
-      ok = epilogue_item<NT, true>(P, bar, tbase, quad, half, lane, q, iw, tm * 2 * BM + (int)rank * BM + row, tn, gc, status);
+      ok = epilogue_item<NT, true>(P, bar, tbase, quad, half, lane, q, iw, tm * 2 * BM + (int)rank * BM + row, tn, gc,
+                                   status, xb);
     }
   }
   tc::fence_before();
