@@ -24,8 +24,9 @@
 //   chi0 = (1 + i t) H1 + i H2,  H1 = sum Re(f) M M^H,  H2 = sum g M M^H,
 // H1 and H2 both Hermitian.  An item contracts W1 = Re(f) M and W2 = g M (two
 // parts, each with its own power-of-two scale) for one tile on or above the
-// diagonal, adds the elements with G <= G' and writes the conjugate transpose
-// of those with G < G' into the lower triangle.  t is the midrange of
+// diagonal, adds the elements with G < G' and writes their conjugate transpose
+// into the lower triangle (in both modes the diagonal G = G' is the pack's
+// sum, not the tensor cores').  t is the midrange of
 // Im f_p / Re f_p over the block (0 where that does not shrink the weights),
 // so max|g| <= rho max|Re f| with rho = half the range of the ratio: about
 // delta / |E_v - E_c| spread over the block's energies, 1e-4 for a block of
